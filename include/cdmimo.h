@@ -1,0 +1,185 @@
+/*
+ * cdmimo — GB300 (sm_103a) library for decentralized coordinate-descent (CD) data detection and
+ * precoding in massive MU-MIMO, after K. Li, O. Castaneda, C. Jeon, J. R. Cavallaro, C. Studer,
+ * "Decentralized Coordinate-Descent Data Detection and Precoding for Massive MU-MIMO"
+ * (arXiv 1902.08653).
+ *
+ * C ABI: plain pointers, sizes and a CUDA stream passed as void*.  Every device buffer is owned by
+ * the caller; the hot-path entry points never allocate, free or synchronize: they validate their
+ * arguments on the host, enqueue kernels on the given stream and return.  Status codes are
+ * negative on error (cdmimo_status_string() names them); no entry point aborts the process.
+ *
+ * Common layouts (row-major; "c64" = interleaved (re, im) float32 pairs, 8 bytes per entry;
+ * "c16" = interleaved (re, im) 16-bit pairs, fp16 or bf16, 4 bytes per entry):
+ *   H    [n_sc][U][B]      uplink channel.  Row u is column h_u of the paper's B x U matrix H^ul,
+ *                          so cluster c's block h_{u,c} = H[f][u][o_c .. o_c+B_c-1] is contiguous.
+ *                          The downlink uses the same array: H^dl_c = (H^ul_c)^H (Sec. II-B).
+ *   Y    [n_sc][n_sym][B]  uplink receive vectors y; H is fixed over the n_sym OFDM symbols.
+ *   S    [n_sc][n_sym][U]  downlink symbol vectors s (c64).
+ *   N0   [n_sc]            float32 noise variance per receive antenna, per subcarrier.
+ *   Xhat [n_sc][n_sym][U]  c64 fused uplink estimate.
+ *   Xc   [n_sc][C][n_sym][U] c64 per-cluster uplink estimates.
+ *   Xdl  [n_sc][n_sym][B]  c64 stacked downlink beamformer [x_1; ...; x_C].
+ * Clusters are contiguous antenna ranges in order: o_0 = 0, o_{c+1} = o_c + B_c, sum B_c = B
+ * (Sec. II-A).
+ */
+#ifndef CDMIMO_H
+#define CDMIMO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Status codes.                                                                                   */
+/* ---------------------------------------------------------------------------------------------- */
+typedef enum {
+    CDMIMO_OK = 0,
+    CDMIMO_ERR_INVALID_ARG = -1,   /* null pointer, negative size or count, bad enum, misalignment */
+    CDMIMO_ERR_BAD_PARTITION = -2, /* some B_c <= 0, or sum B_c != B, or C > CDMIMO_MAX_CLUSTERS */
+    CDMIMO_ERR_UNSUPPORTED = -3,   /* shape beyond what the kernels' on-chip tiles can hold */
+    CDMIMO_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed */
+    CDMIMO_ERR_TIMEOUT = -5,       /* a bounded device-side wait expired (see cdmimo_device_status) */
+    CDMIMO_ERR_WORKSPACE = -6      /* workspace pointer missing, misaligned or too small */
+} cdmimo_status;
+
+/* Bits of the device-side status word (cdmimo_device_status). */
+#define CDMIMO_DEV_TIMEOUT 0x1   /* a bounded wait on an async copy or work queue expired */
+#define CDMIMO_DEV_BAD_N0 0x2    /* some N0[f] was negative or NaN: that subcarrier's output is NaN */
+
+#define CDMIMO_MAX_CLUSTERS 64
+#define CDMIMO_MAX_USERS 64
+
+typedef enum { CDMIMO_C64 = 0, CDMIMO_C16F = 1, CDMIMO_C16BF = 2 } cdmimo_dtype;
+
+/*
+ * Fusion rule of the uplink (Sec. III: xhat = sum_c lambda_c xhat_c, lambda_c = sigma_c^{-2} /
+ * sum_c' sigma_c'^{-2}, sigma_c^2 the post-equalization noise variance of cluster c).
+ *   EQUAL   lambda_c = 1 / C.
+ *   COLNORM sigma_c^2 = (N0/U) sum_u (||h_{u,c}||^2 + N0/Ex)^{-1}; the paper defines sigma_c^2 only
+ *           in words, this is the library's reading.  The factor N0/U cancels in lambda.
+ *   LEARNED lambda = softmax_c of a small MLP on per-cluster statistics (see cdmimo_learned).
+ */
+typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARNED = 2 } cdmimo_fuse_rule;
+
+/*
+ * Problem description shared by detection and precoding.
+ *   n_sc, n_sym, B, U, C  dimensions (n_sc >= 0, others >= 1; C <= 64, U <= 64).
+ *   cluster_size  HOST array [C] of B_c (each >= 1, sum == B).  Read during the call only.
+ *   K             sweeps T_max of the CD loops, K >= 0 (K = 0 gives a zero estimate / beamformer).
+ *   Ex            per-user transmit energy, > 0 (the regularizer is N0/Ex, Eq. (1)).
+ *   fuse          cdmimo_fuse_rule (uplink only).
+ *   rho           downlink total power constraint rho (rho^2 = total power); each cluster gets
+ *                 rho_c = rho / sqrt(C) (Sec. IV-B).
+ *   in_dtype      storage of H and Y (detection) or H (precoding): CDMIMO_C64, or CDMIMO_C16F /
+ *                 CDMIMO_C16BF with per-subcarrier float32 scales: the true values are
+ *                 H[f] = h_scale[f] * stored and Y[f] = y_scale[f] * stored.  All arithmetic is FP32.
+ *   h_scale, y_scale  DEVICE arrays [n_sc] (16-bit dtypes only, else ignored; may be NULL).
+ *   learned       DEVICE pointer to a cdmimo_learned block (fuse == LEARNED, or nonzero
+ *                 learned sweeps), else NULL: plain CD.
+ */
+typedef struct {
+    int n_sc, n_sym, B, U, C;
+    const int* cluster_size;
+    int K;
+    float Ex;
+    int fuse;
+    float rho;
+    int in_dtype;
+    const float* h_scale;
+    const float* y_scale;
+    const void* learned;
+} cdmimo_params;
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Hot path.                                                                                       */
+/* ---------------------------------------------------------------------------------------------- */
+
+/*
+ * Uplink detection: Algorithm 1 (decentralized L-MMSE detection using CD) for every subcarrier,
+ * cluster and OFDM symbol, followed by the feedforward fusion of Sec. III, in one launch.
+ *   Per cluster: m_{u,c} = (||h_{u,c}||^2 + N0/Ex)^{-1}, n_{u,c} = m_{u,c} ||h_{u,c}||^2;
+ *   r = y_c, x_c = 0; for t = 1..K, u = 1..U: x_u <- m h_{u,c}^H r + n x_u, r <- r - h_{u,c} dx.
+ *   A column with ||h||^2 + N0/Ex == 0 is skipped (its estimate stays 0).
+ * H, Y     DEVICE, layout above, dtype p->in_dtype; 16-byte aligned for c64 (8 for c16).
+ * N0       DEVICE float [n_sc], each >= 0 (violations set CDMIMO_DEV_BAD_N0 and give NaN output).
+ * Xhat     DEVICE c64 [n_sc][n_sym][U] output, 8-byte aligned.
+ * Xc_opt   DEVICE c64 [n_sc][C][n_sym][U] per-cluster estimates, or NULL.
+ * lambda_opt DEVICE float [n_sc][C] fusion weights, or NULL.
+ * workspace, ws_bytes  DEVICE scratch of at least cdmimo_workspace_size(p, CDMIMO_OP_DETECT) bytes
+ *          (currently 0 for every supported shape; NULL is accepted when 0 is needed).
+ * stream   cudaStream_t (NULL = legacy default stream).
+ */
+int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
+                  void* Xc_opt, float* lambda_opt, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Downlink precoding: Algorithm 2 (decentralized ZF precoding using CD, Eq. (4)) plus the
+ * per-cluster power normalization of Sec. IV-B, for every subcarrier, cluster and symbol.
+ *   p_{u,c} = ||h_{u,c}||^{-1} (0 for a zero column); x_c = 0;
+ *   for t = 1..K, u = 1..U: x_c <- x_c - (hbar_{u,c}^H x_c - sbar_{u,c}) hbar_{u,c};
+ *   x_c <- rho_c x_c / ||x_c|| (x_c = 0 stays 0).  Output Xdl = [x_1; ...; x_C].
+ * H        DEVICE, dtype p->in_dtype (16-bit storage needs no scale: the normalization removes it).
+ * S        DEVICE c64 [n_sc][n_sym][U], 8-byte aligned.   Xdl DEVICE c64 [n_sc][n_sym][B].
+ */
+int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* Xdl, void* workspace,
+                   size_t ws_bytes, void* stream);
+
+/*
+ * Standalone fusion (Sec. III): Xhat[f][n][u] = sum_c lambda[f][c] Xc[f][c][n][u].
+ * If weights_are_lambda != 0, w is lambda itself; otherwise w holds sigma_c^2 and
+ * lambda_c = sigma_c^{-2} / sum_c' sigma_c'^{-2} (a zero sigma^2 gives that cluster all the weight;
+ * if several are zero they share it equally).  This is the reduction that a cluster-per-GPU
+ * deployment performs across devices.
+ * Xc DEVICE c64 [n_sc][C][n_sym][U]; w DEVICE float [n_sc][C]; Xhat DEVICE c64 [n_sc][n_sym][U].
+ */
+int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* w, int weights_are_lambda,
+                void* Xhat, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Host-buffer variants (end-to-end calls).                                                        */
+/* ---------------------------------------------------------------------------------------------- */
+
+/*
+ * Same as cdmimo_detect / cdmimo_precode, but H, Y (or S), N0 and the outputs are HOST buffers
+ * (pinned memory makes the copies asynchronous).  The call enqueues on `stream` the host-to-device
+ * copies into `dev_ws`, the kernel, and the device-to-host copy of the output, then returns;
+ * the caller synchronizes the stream before reading the output.  dev_ws is DEVICE scratch of at
+ * least cdmimo_host_workspace_size(p, op) bytes, 256-byte aligned.
+ */
+int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y_host, const float* N0_host,
+                       void* Xhat_host, void* dev_ws, size_t ws_bytes, void* stream);
+int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* S_host, void* Xdl_host,
+                        void* dev_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Queries.                                                                                        */
+/* ---------------------------------------------------------------------------------------------- */
+#define CDMIMO_OP_DETECT 0
+#define CDMIMO_OP_PRECODE 1
+
+/* Device scratch bytes that cdmimo_detect / cdmimo_precode need for p (0 when none), or 0 with an
+ * invalid p (the call itself then reports the error). */
+size_t cdmimo_workspace_size(const cdmimo_params* p, int op);
+
+/* Device staging bytes that cdmimo_detect_host / cdmimo_precode_host need for p. */
+size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
+
+/* Static name of a status code. */
+const char* cdmimo_status_string(int status);
+
+/* Device-side status word (CDMIMO_DEV_* bits) accumulated by kernels on the current device since
+ * the last clear; synchronizes the device.  clear != 0 resets it to 0.  Returns a negative
+ * cdmimo_status if the read itself fails. */
+int cdmimo_device_status(int clear);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+int cdmimo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDMIMO_H */

@@ -1,0 +1,238 @@
+"""Python binding of the cdmimo C ABI (argument marshalling only).
+
+Every function takes torch tensors as plain device (or pinned host) buffers, checks their dtype,
+shape and contiguity, and passes raw pointers and the current CUDA stream to the C entry point of
+the same name; all computation happens in the library's CUDA kernels.  There is no CPU fallback:
+if libcdmimo.so is missing or fails to load, every call raises.
+
+Tensor conventions (see include/cdmimo.h for the exact layouts):
+  complex entries are torch.complex64, or 16-bit storage given as a [..., 2] tensor of
+  torch.float16 / torch.bfloat16 (re, im pairs) with per-subcarrier float32 scales.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_BAD_PARTITION = -2
+ERR_UNSUPPORTED = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_WORKSPACE = -6
+
+DEV_TIMEOUT = 0x1
+DEV_BAD_N0 = 0x2
+
+C64, C16F, C16BF = 0, 1, 2
+FUSE = {"equal": 0, "colnorm": 1, "learned": 2}
+OP_DETECT, OP_PRECODE = 0, 1
+
+
+class CdmimoError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} failed: {status_string(status)} ({status})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_sc", ctypes.c_int), ("n_sym", ctypes.c_int), ("B", ctypes.c_int), ("U", ctypes.c_int),
+                ("C", ctypes.c_int), ("cluster_size", ctypes.POINTER(ctypes.c_int)), ("K", ctypes.c_int),
+                ("Ex", ctypes.c_float), ("fuse", ctypes.c_int), ("rho", ctypes.c_float), ("in_dtype", ctypes.c_int),
+                ("h_scale", ctypes.c_void_p), ("y_scale", ctypes.c_void_p), ("learned", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcdmimo.so (building it first if the sources are newer).  Raises if unavailable."""
+    global _lib
+    if _lib is None:
+        path = _build.OUT
+        if not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libcdmimo.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(path)
+        P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+        PP = ctypes.POINTER(Params)
+        sig = {
+            "cdmimo_detect": ([PP, P, P, P, P, P, P, P, S, P], I),
+            "cdmimo_precode": ([PP, P, P, P, P, S, P], I),
+            "cdmimo_fuse": ([I, I, I, I, P, P, I, P, P], I),
+            "cdmimo_detect_host": ([PP, P, P, P, P, P, S, P], I),
+            "cdmimo_precode_host": ([PP, P, P, P, P, S, P], I),
+            "cdmimo_workspace_size": ([PP, I], S),
+            "cdmimo_host_workspace_size": ([PP, I], S),
+            "cdmimo_status_string": ([I], ctypes.c_char_p),
+            "cdmimo_device_status": ([I], I),
+            "cdmimo_version": ([], I),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().cdmimo_status_string(int(status)).decode()
+
+
+def device_status(clear: bool = False) -> int:
+    return lib().cdmimo_device_status(1 if clear else 0)
+
+
+def _check(fn, rc):
+    if rc != OK:
+        raise CdmimoError(fn, rc)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dtype_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.float16 and t.shape[-1] == 2:
+        return C16F
+    if t.dtype == torch.bfloat16 and t.shape[-1] == 2:
+        return C16BF
+    raise TypeError(f"unsupported storage {t.dtype} {tuple(t.shape)}: use complex64 or [...,2] float16/bfloat16")
+
+
+def _need(t, name, dev=True):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dev and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not dev and t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    return t
+
+
+def make_params(n_sc, n_sym, B, U, cluster_size, K, *, Ex=1.0, fuse="colnorm", rho=1.0, in_dtype=C64,
+                h_scale=None, y_scale=None, learned=None):
+    """Build the C parameter block.  Returns (Params, keepalive) — keep both alive during the call."""
+    cs = (ctypes.c_int * len(cluster_size))(*[int(v) for v in cluster_size])
+    p = Params(int(n_sc), int(n_sym), int(B), int(U), len(cluster_size), ctypes.cast(cs, ctypes.POINTER(ctypes.c_int)),
+               int(K), float(Ex), FUSE[fuse] if isinstance(fuse, str) else int(fuse), float(rho), int(in_dtype),
+               h_scale.data_ptr() if h_scale is not None else None,
+               y_scale.data_ptr() if y_scale is not None else None,
+               learned.data_ptr() if learned is not None else None)
+    return p, cs
+
+
+def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y_scale=None, learned=None,
+           out=None, Xc=None, lam=None, workspace=None, stream=None):
+    """cdmimo_detect: Algorithm 1 + fusion.  Returns Xhat [n_sc, n_sym, U] complex64."""
+    _need(H, "H")
+    _need(Y, "Y")
+    _need(N0, "N0")
+    dt = _dtype_of(H)
+    if _dtype_of(Y) != dt:
+        raise TypeError("H and Y must use the same storage dtype")
+    n_sc, U, B = H.shape[:3]
+    n_sym = Y.shape[1]
+    if N0.dtype != torch.float32:
+        raise TypeError("N0 must be float32")
+    if out is None:
+        out = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=H.device)
+    _need(out, "out")
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse=fuse, in_dtype=dt, h_scale=h_scale,
+                          y_scale=y_scale, learned=learned)
+    ws = workspace.data_ptr() if workspace is not None else None
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    rc = lib().cdmimo_detect(ctypes.byref(p), _ptr(H), _ptr(Y), _ptr(N0), _ptr(out), _ptr(Xc), _ptr(lam),
+                             ws, wsb, _stream(stream))
+    _check("cdmimo_detect", rc)
+    return out
+
+
+def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=None):
+    """cdmimo_precode: Algorithm 2 + per-cluster normalization.  Returns Xdl [n_sc, n_sym, B] complex64."""
+    _need(H, "H")
+    _need(S, "S")
+    dt = _dtype_of(H)
+    if S.dtype != torch.complex64:
+        raise TypeError("S must be complex64")
+    n_sc, U, B = H.shape[:3]
+    n_sym = S.shape[1]
+    if out is None:
+        out = torch.empty((n_sc, n_sym, B), dtype=torch.complex64, device=H.device)
+    _need(out, "out")
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, rho=rho, in_dtype=dt)
+    ws = workspace.data_ptr() if workspace is not None else None
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    rc = lib().cdmimo_precode(ctypes.byref(p), _ptr(H), _ptr(S), _ptr(out), ws, wsb, _stream(stream))
+    _check("cdmimo_precode", rc)
+    return out
+
+
+def fuse(Xc, w, *, weights_are_lambda=False, out=None, stream=None):
+    """cdmimo_fuse: Xhat = sum_c lambda_c Xc[:, c] with lambda given, or derived from sigma_c^2."""
+    _need(Xc, "Xc")
+    _need(w, "w")
+    n_sc, C, n_sym, U = Xc.shape
+    if out is None:
+        out = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=Xc.device)
+    rc = lib().cdmimo_fuse(n_sc, n_sym, U, C, _ptr(Xc), _ptr(w), 1 if weights_are_lambda else 0, _ptr(out),
+                           _stream(stream))
+    _check("cdmimo_fuse", rc)
+    return out
+
+
+def host_workspace_size(op, n_sc, n_sym, B, U, cluster_size, K, in_dtype=C64):
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, in_dtype=in_dtype)
+    return int(lib().cdmimo_host_workspace_size(ctypes.byref(p), op))
+
+
+def detect_host(H, Y, N0, cluster_size, K, Xhat, dev_ws, *, Ex=1.0, fuse="colnorm", h_scale=None, y_scale=None,
+                stream=None):
+    """cdmimo_detect_host: host (pinned) inputs and output; the copies are enqueued with the kernel.
+    The caller synchronizes the stream before reading Xhat."""
+    for t, nm in ((H, "H"), (Y, "Y"), (N0, "N0"), (Xhat, "Xhat")):
+        _need(t, nm, dev=False)
+    _need(dev_ws, "dev_ws")
+    dt = _dtype_of(H)
+    n_sc, U, B = H.shape[:3]
+    n_sym = Y.shape[1]
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse=fuse, in_dtype=dt, h_scale=h_scale,
+                          y_scale=y_scale)
+    rc = lib().cdmimo_detect_host(ctypes.byref(p), _ptr(H), _ptr(Y), _ptr(N0), _ptr(Xhat), _ptr(dev_ws),
+                                  dev_ws.numel() * dev_ws.element_size(), _stream(stream))
+    _check("cdmimo_detect_host", rc)
+    return Xhat
+
+
+def precode_host(H, S, cluster_size, K, Xdl, dev_ws, *, rho=1.0, stream=None):
+    """cdmimo_precode_host: host (pinned) inputs and output."""
+    for t, nm in ((H, "H"), (S, "S"), (Xdl, "Xdl")):
+        _need(t, nm, dev=False)
+    _need(dev_ws, "dev_ws")
+    dt = _dtype_of(H)
+    n_sc, U, B = H.shape[:3]
+    n_sym = S.shape[1]
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, rho=rho, in_dtype=dt)
+    rc = lib().cdmimo_precode_host(ctypes.byref(p), _ptr(H), _ptr(S), _ptr(Xdl), _ptr(dev_ws),
+                                   dev_ws.numel() * dev_ws.element_size(), _stream(stream))
+    _check("cdmimo_precode_host", rc)
+    return Xdl

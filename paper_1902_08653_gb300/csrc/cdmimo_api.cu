@@ -1,0 +1,401 @@
+// C-ABI entry points of the cdmimo library: argument validation, launch planning and kernel
+// dispatch.  Every hot-path call enqueues on the caller's stream and returns; nothing here
+// allocates device memory or synchronizes (except cdmimo_device_status, which is documented to).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "cd_kernels.cuh"
+#include "cdmimo.h"
+#include "plan.h"
+
+using namespace cdmimo;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kMaxThreads = 512;  // __launch_bounds__ of the CD kernels
+
+int device_smem_optin()
+{
+    static int cache[kMaxDevices] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 48 * 1024;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+            v = 48 * 1024;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+int pow2ceil(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+unsigned align16(unsigned v) { return (v + 15u) & ~15u; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int elem_bytes(int dtype) { return dtype == CDMIMO_C64 ? 8 : 4; }
+
+// Structural validation of the problem description (no device pointers involved).
+int validate(const cdmimo_params* p)
+{
+    if (!p) return CDMIMO_ERR_INVALID_ARG;
+    if (p->n_sc < 0 || p->n_sym < 1 || p->B < 1 || p->U < 1 || p->C < 1 || p->K < 0) return CDMIMO_ERR_INVALID_ARG;
+    if (!(p->Ex > 0.f)) return CDMIMO_ERR_INVALID_ARG;
+    if (p->in_dtype != CDMIMO_C64 && p->in_dtype != CDMIMO_C16F && p->in_dtype != CDMIMO_C16BF)
+        return CDMIMO_ERR_INVALID_ARG;
+    if (p->fuse != CDMIMO_FUSE_EQUAL && p->fuse != CDMIMO_FUSE_COLNORM && p->fuse != CDMIMO_FUSE_LEARNED)
+        return CDMIMO_ERR_INVALID_ARG;
+    if (p->U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
+    if (!p->cluster_size || p->C > CDMIMO_MAX_CLUSTERS) return CDMIMO_ERR_BAD_PARTITION;
+    long sum = 0;
+    for (int c = 0; c < p->C; ++c) {
+        if (p->cluster_size[c] < 1) return CDMIMO_ERR_BAD_PARTITION;
+        sum += p->cluster_size[c];
+    }
+    if (sum != p->B) return CDMIMO_ERR_BAD_PARTITION;
+    return CDMIMO_OK;
+}
+
+// Build the tiling for antennas-per-lane P.  Returns UNSUPPORTED if the CTA would need more than
+// 1024 threads or more shared memory than the device grants.
+int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan* pl)
+{
+    std::memset(pl, 0, sizeof(*pl));
+    pl->n_sc = p->n_sc;
+    pl->n_sym = p->n_sym;
+    pl->B = p->B;
+    pl->U = p->U;
+    pl->C = p->C;
+    pl->K = p->K;
+    pl->P = P;
+    pl->fuse = p->fuse;
+    pl->inv_Ex = 1.f / p->Ex;
+    pl->rho_c = (float)(p->rho / std::sqrt((double)p->C));
+    pl->coef_sweeps = 1;
+    int off = 0, soff = 0;
+    bool unpadded = true;
+    for (int c = 0; c < p->C; ++c) {
+        ClusterTile& ct = pl->cl[c];
+        ct.off = off;
+        ct.size = p->cluster_size[c];
+        ct.A = pow2ceil((ct.size + P - 1) / P);
+        if (ct.A > 32) return CDMIMO_ERR_UNSUPPORTED;
+        ct.soff = soff;
+        if (ct.A * P != ct.size) unpadded = false;
+        off += ct.size;
+        soff += ct.A * P;
+    }
+    pl->Ltot = soff;
+    // Lanes: clusters in order of decreasing A so every tile's lane group is A-aligned in its warp.
+    int order[CDMIMO_MAX_CLUSTERS];
+    for (int c = 0; c < p->C; ++c) order[c] = c;
+    std::stable_sort(order, order + p->C, [&](int a, int b) { return pl->cl[a].A > pl->cl[b].A; });
+    int lane = 0;
+    for (int k = 0; k < p->C; ++k) {
+        ClusterTile& ct = pl->cl[order[k]];
+        ct.lane0 = lane;
+        lane += p->n_sym * ct.A;
+    }
+    pl->n_lanes = lane;
+    pl->n_tiles = p->C * p->n_sym;
+    if (pl->n_lanes > kMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
+
+    const unsigned U = p->U, C = p->C;
+    unsigned o = align16(U * pl->Ltot * 8u);
+    if (detect) {
+        pl->off_X = o;
+        o = align16(o + U * ((unsigned)pl->n_tiles | 1u) * 8u);
+        pl->off_coef = o;
+        o = align16(o + pl->coef_sweeps * C * U * 8u);
+        pl->off_lam = o;
+        o = align16(o + C * 4u);
+    } else {
+        pl->off_coef = o;
+        o = align16(o + C * U * 4u);
+        pl->off_S = o;
+        o = align16(o + (unsigned)p->n_sym * U * 8u);
+    }
+    pl->off_e = o;
+    o = align16(o + C * U * 4u);
+    pl->off_tab = o;
+    o = align16(o + C * (unsigned)sizeof(ClusterTile));
+    pl->off_bar = o;
+    o = align16(o + 8u);
+    pl->smem_bytes = o;
+    if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+
+    const size_t hbytes = (size_t)U * p->B * 8u;
+    pl->bulk = (p->in_dtype == CDMIMO_C64 && unpadded && (hbytes % 16) == 0 && aligned(H, 16)) ? 1 : 0;
+    return CDMIMO_OK;
+}
+
+// Antennas per lane: 16 by default (two lanes per tile at B_c = 32), 8 for tiny clusters, 32 when
+// 16 would need more than 1024 threads per CTA.
+int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
+{
+    int maxBc = 0;
+    for (int c = 0; c < p->C; ++c) maxBc = std::max(maxBc, p->cluster_size[c]);
+    const int first = maxBc <= 8 ? 8 : 16;
+    int rc = CDMIMO_ERR_UNSUPPORTED;
+    for (int P = first; P <= 32; P *= 2) {
+        rc = build_plan(p, P, detect, H, pl);
+        if (rc == CDMIMO_OK) return rc;
+    }
+    return rc;
+}
+
+int threads_for(const CdPlan& pl) { return std::max(64, (pl.n_lanes + 31) / 32 * 32); }
+
+template <typename Kern>
+int prepare_kernel(Kern k, unsigned smem)
+{
+    if (smem > 48u * 1024u) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return CDMIMO_ERR_CUDA;
+    }
+    return CDMIMO_OK;
+}
+
+template <int P, int IN>
+int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
+{
+    auto k = cd_detect_kernel<P, IN>;
+    if (int rc = prepare_kernel(k, pl.smem_bytes)) return rc;
+    k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+template <int P, int IN>
+int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
+{
+    auto k = cd_precode_kernel<P, IN>;
+    if (int rc = prepare_kernel(k, pl.smem_bytes)) return rc;
+    k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+template <int IN>
+int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
+{
+    switch (pl.P) {
+    case 8: return launch_detect_t<8, IN>(pl, io, s);
+    case 16: return launch_detect_t<16, IN>(pl, io, s);
+    case 32: return launch_detect_t<32, IN>(pl, io, s);
+    }
+    return CDMIMO_ERR_UNSUPPORTED;
+}
+
+template <int IN>
+int dispatch_precode(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
+{
+    switch (pl.P) {
+    case 8: return launch_precode_t<8, IN>(pl, io, s);
+    case 16: return launch_precode_t<16, IN>(pl, io, s);
+    case 32: return launch_precode_t<32, IN>(pl, io, s);
+    }
+    return CDMIMO_ERR_UNSUPPORTED;
+}
+
+int check_detect_ptrs(const cdmimo_params* p, const void* H, const void* Y, const float* N0, const void* Xhat)
+{
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H || !Y || !N0 || !Xhat) return CDMIMO_ERR_INVALID_ARG;
+    const size_t ea = p->in_dtype == CDMIMO_C64 ? 8 : 4;
+    if (!aligned(H, ea) || !aligned(Y, ea) || !aligned(N0, 4) || !aligned(Xhat, 8)) return CDMIMO_ERR_INVALID_ARG;
+    if (p->in_dtype != CDMIMO_C64 && (!p->h_scale || !p->y_scale)) return CDMIMO_ERR_INVALID_ARG;
+    return CDMIMO_OK;
+}
+
+int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc,
+                float* lam, cudaStream_t s)
+{
+    if (int rc = validate(p)) return rc;
+    if (int rc = check_detect_ptrs(p, H, Y, N0, Xhat)) return rc;
+    if ((Xc && !aligned(Xc, 8)) || (lam && !aligned(lam, 4))) return CDMIMO_ERR_INVALID_ARG;
+    if (p->fuse == CDMIMO_FUSE_LEARNED) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    CdPlan pl;
+    if (int rc = plan_auto(p, true, H, &pl)) return rc;
+    DetectIO io{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), reinterpret_cast<float2*>(Xc),
+                lam, p->learned};
+    switch (p->in_dtype) {
+    case CDMIMO_C64: return dispatch_detect<CDMIMO_C64>(pl, io, s);
+    case CDMIMO_C16F: return dispatch_detect<CDMIMO_C16F>(pl, io, s);
+    case CDMIMO_C16BF: return dispatch_detect<CDMIMO_C16BF>(pl, io, s);
+    }
+    return CDMIMO_ERR_INVALID_ARG;
+}
+
+int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl, cudaStream_t s)
+{
+    if (int rc = validate(p)) return rc;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H || !S || !Xdl) return CDMIMO_ERR_INVALID_ARG;
+    const size_t ea = p->in_dtype == CDMIMO_C64 ? 8 : 4;
+    if (!aligned(H, ea) || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
+    CdPlan pl;
+    if (int rc = plan_auto(p, false, H, &pl)) return rc;
+    PrecodeIO io{H, reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
+    switch (p->in_dtype) {
+    case CDMIMO_C64: return dispatch_precode<CDMIMO_C64>(pl, io, s);
+    case CDMIMO_C16F: return dispatch_precode<CDMIMO_C16F>(pl, io, s);
+    case CDMIMO_C16BF: return dispatch_precode<CDMIMO_C16BF>(pl, io, s);
+    }
+    return CDMIMO_ERR_INVALID_ARG;
+}
+
+size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc_opt,
+                  float* lambda_opt, void* workspace, size_t ws_bytes, void* stream)
+{
+    (void)workspace;
+    (void)ws_bytes;
+    return detect_impl(p, H, Y, N0, Xhat, Xc_opt, lambda_opt, static_cast<cudaStream_t>(stream));
+}
+
+int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* Xdl, void* workspace, size_t ws_bytes,
+                   void* stream)
+{
+    (void)workspace;
+    (void)ws_bytes;
+    return precode_impl(p, H, S, Xdl, static_cast<cudaStream_t>(stream));
+}
+
+int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* w, int weights_are_lambda, void* Xhat,
+                void* stream)
+{
+    if (n_sc < 0 || n_sym < 1 || U < 1 || C < 1) return CDMIMO_ERR_INVALID_ARG;
+    if (n_sc == 0) return CDMIMO_OK;
+    if (!Xc || !w || !Xhat || !aligned(Xc, 8) || !aligned(Xhat, 8) || !aligned(w, 4)) return CDMIMO_ERR_INVALID_ARG;
+    const size_t total = (size_t)n_sc * n_sym * U;
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((total + threads - 1) / threads, 152 * 16);
+    fuse_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_sc, n_sym, U, C, reinterpret_cast<const float2*>(Xc), w, weights_are_lambda, reinterpret_cast<float2*>(Xhat));
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+size_t cdmimo_workspace_size(const cdmimo_params* p, int op)
+{
+    (void)op;
+    (void)p;
+    return 0;
+}
+
+size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op)
+{
+    if (validate(p) != CDMIMO_OK) return 0;
+    const size_t eb = elem_bytes(p->in_dtype);
+    const size_t hb = round256((size_t)p->n_sc * p->U * p->B * eb);
+    if (op == CDMIMO_OP_DETECT) {
+        size_t v = hb + round256((size_t)p->n_sc * p->n_sym * p->B * eb) + round256((size_t)p->n_sc * 4) +
+                   round256((size_t)p->n_sc * p->n_sym * p->U * 8);
+        if (p->in_dtype != CDMIMO_C64) v += 2 * round256((size_t)p->n_sc * 4);
+        return v;
+    }
+    if (op == CDMIMO_OP_PRECODE)
+        return hb + round256((size_t)p->n_sc * p->n_sym * p->U * 8) + round256((size_t)p->n_sc * p->n_sym * p->B * 8);
+    return 0;
+}
+
+int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y_host, const float* N0_host,
+                       void* Xhat_host, void* dev_ws, size_t ws_bytes, void* stream)
+{
+    if (int rc = validate(p)) return rc;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H_host || !Y_host || !N0_host || !Xhat_host) return CDMIMO_ERR_INVALID_ARG;
+    if (p->in_dtype != CDMIMO_C64 && (!p->h_scale || !p->y_scale)) return CDMIMO_ERR_INVALID_ARG;
+    const size_t need = cdmimo_host_workspace_size(p, CDMIMO_OP_DETECT);
+    if (!dev_ws || !aligned(dev_ws, 256) || ws_bytes < need) return CDMIMO_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t eb = elem_bytes(p->in_dtype);
+    const size_t hb = (size_t)p->n_sc * p->U * p->B * eb, yb = (size_t)p->n_sc * p->n_sym * p->B * eb;
+    const size_t nb = (size_t)p->n_sc * 4, xb = (size_t)p->n_sc * p->n_sym * p->U * 8;
+    char* w = static_cast<char*>(dev_ws);
+    char* dH = w;
+    char* dY = dH + round256(hb);
+    char* dN = dY + round256(yb);
+    char* dX = dN + round256(nb);
+    cdmimo_params q = *p;
+    if (cudaMemcpyAsync(dH, H_host, hb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (cudaMemcpyAsync(dY, Y_host, yb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (cudaMemcpyAsync(dN, N0_host, nb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (p->in_dtype != CDMIMO_C64) {
+        char* dhs = dX + round256(xb);
+        char* dys = dhs + round256(nb);
+        if (cudaMemcpyAsync(dhs, p->h_scale, nb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+        if (cudaMemcpyAsync(dys, p->y_scale, nb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+        q.h_scale = reinterpret_cast<const float*>(dhs);
+        q.y_scale = reinterpret_cast<const float*>(dys);
+    }
+    if (int rc = detect_impl(&q, dH, dY, reinterpret_cast<const float*>(dN), dX, nullptr, nullptr, s)) return rc;
+    if (cudaMemcpyAsync(Xhat_host, dX, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    return CDMIMO_OK;
+}
+
+int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* S_host, void* Xdl_host, void* dev_ws,
+                        size_t ws_bytes, void* stream)
+{
+    if (int rc = validate(p)) return rc;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H_host || !S_host || !Xdl_host) return CDMIMO_ERR_INVALID_ARG;
+    const size_t need = cdmimo_host_workspace_size(p, CDMIMO_OP_PRECODE);
+    if (!dev_ws || !aligned(dev_ws, 256) || ws_bytes < need) return CDMIMO_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t hb = (size_t)p->n_sc * p->U * p->B * elem_bytes(p->in_dtype);
+    const size_t sb = (size_t)p->n_sc * p->n_sym * p->U * 8, xb = (size_t)p->n_sc * p->n_sym * p->B * 8;
+    char* dH = static_cast<char*>(dev_ws);
+    char* dS = dH + round256(hb);
+    char* dX = dS + round256(sb);
+    if (cudaMemcpyAsync(dH, H_host, hb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (cudaMemcpyAsync(dS, S_host, sb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (int rc = precode_impl(p, dH, dS, dX, s)) return rc;
+    if (cudaMemcpyAsync(Xdl_host, dX, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    return CDMIMO_OK;
+}
+
+const char* cdmimo_status_string(int status)
+{
+    switch (status) {
+    case CDMIMO_OK: return "CDMIMO_OK";
+    case CDMIMO_ERR_INVALID_ARG: return "CDMIMO_ERR_INVALID_ARG";
+    case CDMIMO_ERR_BAD_PARTITION: return "CDMIMO_ERR_BAD_PARTITION";
+    case CDMIMO_ERR_UNSUPPORTED: return "CDMIMO_ERR_UNSUPPORTED";
+    case CDMIMO_ERR_CUDA: return "CDMIMO_ERR_CUDA";
+    case CDMIMO_ERR_TIMEOUT: return "CDMIMO_ERR_TIMEOUT";
+    case CDMIMO_ERR_WORKSPACE: return "CDMIMO_ERR_WORKSPACE";
+    }
+    return "CDMIMO_UNKNOWN_STATUS";
+}
+
+int cdmimo_device_status(int clear)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return CDMIMO_ERR_CUDA;
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_dev_status, sizeof(v)) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (clear) {
+        const unsigned z = 0;
+        if (cudaMemcpyToSymbol(g_dev_status, &z, sizeof(z)) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    }
+    return (int)v;
+}
+
+int cdmimo_version(void) { return 0x000100; }
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""The C-ABI library loads, exports every declared entry point, and validates arguments on the
+host (CPU only: no call here reaches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1902_08653_gb300 import cdmimo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(cdmimo_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cdmimo_detect", "cdmimo_precode", "cdmimo_fuse", "cdmimo_workspace_size",
+                     "cdmimo_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = cdmimo.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    for code, name in [(0, "CDMIMO_OK"), (-1, "CDMIMO_ERR_INVALID_ARG"), (-2, "CDMIMO_ERR_BAD_PARTITION"),
+                       (-3, "CDMIMO_ERR_UNSUPPORTED"), (-4, "CDMIMO_ERR_CUDA"), (-5, "CDMIMO_ERR_TIMEOUT"),
+                       (-6, "CDMIMO_ERR_WORKSPACE")]:
+        assert cdmimo.status_string(code) == name
+    assert cdmimo.status_string(12345) == "CDMIMO_UNKNOWN_STATUS"
+    assert cdmimo.lib().cdmimo_version() >= 0x000100
+
+
+def _detect_rc(**kw):
+    args = dict(n_sc=4, n_sym=2, B=32, U=4, cluster_size=[16, 16], K=3)
+    args.update(kw)
+    p, keep = cdmimo.make_params(args["n_sc"], args["n_sym"], args["B"], args["U"], args["cluster_size"], args["K"],
+                                 Ex=args.get("Ex", 1.0), fuse=args.get("fuse", "colnorm"),
+                                 in_dtype=args.get("in_dtype", 0))
+    fake = ctypes.c_void_p(0x10000)  # never dereferenced: validation fails before any launch
+    ptrs = [args.get(k, fake) for k in ("H", "Y", "N0", "Xhat")]
+    return cdmimo.lib().cdmimo_detect(ctypes.byref(p), *ptrs, None, None, None, 0, None)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(cluster_size=[16, 15]), cdmimo.ERR_BAD_PARTITION),
+    (dict(cluster_size=[32, 0]), cdmimo.ERR_BAD_PARTITION),
+    (dict(cluster_size=[40, -8]), cdmimo.ERR_BAD_PARTITION),
+    (dict(K=-1), cdmimo.ERR_INVALID_ARG),
+    (dict(n_sym=0), cdmimo.ERR_INVALID_ARG),
+    (dict(n_sc=-1), cdmimo.ERR_INVALID_ARG),
+    (dict(U=0), cdmimo.ERR_INVALID_ARG),
+    (dict(U=65), cdmimo.ERR_UNSUPPORTED),
+    (dict(Ex=0.0), cdmimo.ERR_INVALID_ARG),
+    (dict(Ex=float("nan")), cdmimo.ERR_INVALID_ARG),
+    (dict(fuse=7), cdmimo.ERR_INVALID_ARG),
+    (dict(in_dtype=9), cdmimo.ERR_INVALID_ARG),
+    (dict(H=None), cdmimo.ERR_INVALID_ARG),
+    (dict(Xhat=None), cdmimo.ERR_INVALID_ARG),
+    (dict(Y=ctypes.c_void_p(0x10004)), cdmimo.ERR_INVALID_ARG),   # misaligned complex64
+    (dict(in_dtype=1), cdmimo.ERR_INVALID_ARG),                   # 16-bit storage without scales
+])
+def test_detect_validation(kw, code):
+    assert _detect_rc(**kw) == code
+
+
+def test_empty_batch_is_a_no_op():
+    assert _detect_rc(n_sc=0, H=None, Y=None, N0=None, Xhat=None) == cdmimo.OK
+
+
+def test_precode_and_fuse_validation():
+    L = cdmimo.lib()
+    p, keep = cdmimo.make_params(2, 1, 32, 4, [16, 17], 3)
+    fake = ctypes.c_void_p(0x10000)
+    assert L.cdmimo_precode(ctypes.byref(p), fake, fake, fake, None, 0, None) == cdmimo.ERR_BAD_PARTITION
+    p, keep = cdmimo.make_params(2, 1, 32, 4, [16, 16], 3)
+    assert L.cdmimo_precode(ctypes.byref(p), None, fake, fake, None, 0, None) == cdmimo.ERR_INVALID_ARG
+    assert L.cdmimo_fuse(2, 1, 4, 0, fake, fake, 0, fake, None) == cdmimo.ERR_INVALID_ARG
+    assert L.cdmimo_fuse(2, 1, 4, 2, None, fake, 0, fake, None) == cdmimo.ERR_INVALID_ARG
+    assert L.cdmimo_fuse(0, 1, 4, 2, None, None, 0, None, None) == cdmimo.OK
+
+
+def test_host_workspace_sizes():
+    L = cdmimo.lib()
+    p, keep = cdmimo.make_params(1200, 14, 256, 16, [32] * 8, 3)
+    need = L.cdmimo_host_workspace_size(ctypes.byref(p), cdmimo.OP_DETECT)
+    assert need >= 1200 * 16 * 256 * 8 + 1200 * 14 * 256 * 8 + 1200 * 4 + 1200 * 14 * 16 * 8
+    assert need % 256 == 0
+    assert L.cdmimo_workspace_size(ctypes.byref(p), cdmimo.OP_DETECT) == 0
+    assert L.cdmimo_detect_host(ctypes.byref(p), ctypes.c_void_p(1), ctypes.c_void_p(1), ctypes.c_void_p(1),
+                                ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None) == cdmimo.ERR_WORKSPACE
