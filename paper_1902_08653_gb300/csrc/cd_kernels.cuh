@@ -1,5 +1,9 @@
 // CD detection / precoding / fusion kernels for sm_103a (plain FP32 arithmetic, FP32 or 16-bit
-// storage).  The tiling is described in plan.h.
+// storage).  The tiling and the shared-memory layout are described in plan.h.
+//
+// Template parameters: P antennas per lane; IN storage type of H (and Y); AT lanes per tile when
+// every cluster has the same A (so shuffle counts and shared-memory offsets are compile-time
+// constants), or 0 for mixed cluster sizes (per-lane A at run time).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -9,8 +13,6 @@
 
 namespace cdmimo {
 
-constexpr uint32_t kBulkChunk = 16384;  // bytes per cp.async.bulk instruction
-
 // ---------------------------------------------------------------------------------------------
 // storage element types
 // ---------------------------------------------------------------------------------------------
@@ -18,7 +20,6 @@ template <int IN>
 struct Elem;
 template <>
 struct Elem<CDMIMO_C64> {
-    static constexpr int bytes = 8;
     static __device__ __forceinline__ float2 load(const void* base, size_t i)
     {
         return __ldg(reinterpret_cast<const float2*>(base) + i);
@@ -26,7 +27,6 @@ struct Elem<CDMIMO_C64> {
 };
 template <>
 struct Elem<CDMIMO_C16F> {
-    static constexpr int bytes = 4;
     static __device__ __forceinline__ float2 load(const void* base, size_t i)
     {
         return __half22float2(__ldg(reinterpret_cast<const __half2*>(base) + i));
@@ -34,7 +34,6 @@ struct Elem<CDMIMO_C16F> {
 };
 template <>
 struct Elem<CDMIMO_C16BF> {
-    static constexpr int bytes = 4;
     static __device__ __forceinline__ float2 load(const void* base, size_t i)
     {
         return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(base) + i));
@@ -52,7 +51,7 @@ __device__ __forceinline__ float warp_sum(float v)
 // per-CTA pieces shared by detection and precoding
 // ---------------------------------------------------------------------------------------------
 struct LaneTile {
-    bool active;    // this thread runs a CD tile
+    bool active;     // this thread runs a CD tile
     int c, A, n, a;  // cluster, lanes per tile, symbol, lane within tile
     int Awarp;       // max A over the active lanes of this warp (uniform shuffle trip count)
     unsigned mask;   // active lanes of this warp
@@ -82,53 +81,70 @@ __device__ __forceinline__ LaneTile map_lane(const CdPlan& pl, const ClusterTile
     return t;
 }
 
-// Stage the channel rows of subcarrier f into shared memory.  Bulk path: one elected thread
-// issues cp.async.bulk copies of the contiguous U x B block and arms the mbarrier; the caller
-// waits on it.  Otherwise every warp copies (u, c) row segments with conversion and zero padding.
-template <int P, int IN>
-__device__ __forceinline__ void stage_H(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
-                                        float2* Hs, uint64_t* bar)
+// Zero the padding columns [B_c, L_c) of every channel row (done once: staging never writes them).
+__device__ __forceinline__ void zero_padding(const CdPlan& pl, const ClusterTile* tab, float2* Hs)
 {
-    if (pl.bulk) {
-        if (threadIdx.x == 0) {
-            fence_proxy_async_smem();
-            const uint32_t bytes = (uint32_t)pl.U * pl.B * 8u;
-            mbar_arrive_expect_tx(bar, bytes);
-            const char* src = reinterpret_cast<const char*>(H) + (size_t)f * bytes;
-            for (uint32_t o = 0; o < bytes; o += kBulkChunk)
-                bulk_g2s(reinterpret_cast<char*>(Hs) + o, src + o, min(kBulkChunk, bytes - o), bar);
-        }
-        return;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int row = warp; row < pl.U * pl.C; row += nwarps) {
-        const int u = row / pl.C, c = row - u * pl.C;
+    if (!pl.padded) return;
+    for (int c = 0; c < pl.C; ++c) {
         const ClusterTile ct = tab[c];
-        const int L = ct.A * P;
-        const size_t g0 = ((size_t)f * pl.U + u) * pl.B + ct.off;
-        float2* dst = Hs + (size_t)u * pl.Ltot + ct.soff;
-        for (int j = lane; j < L; j += 32)
-            dst[j] = j < ct.size ? Elem<IN>::load(H, g0 + j) : make_float2(0.f, 0.f);
+        const int w = ct.L - ct.size;
+        for (int i = threadIdx.x; i < pl.U * w; i += blockDim.x) {
+            const int u = i / w, j = ct.size + (i - u * w);
+            Hs[ct.soff + u * ct.L + j] = make_float2(0.f, 0.f);
+        }
     }
 }
 
-// Column energies e[c][u] = ||h_{u,c}||^2 from the staged rows: one warp per (u, c) segment.
-template <int P>
+// Stage the channel of subcarrier f into the per-cluster shared-memory blocks.  Bulk path: warp 0
+// arms the mbarrier with the total byte count, then its lanes issue one cp.async.bulk per (cluster,
+// user) row; the caller waits on the barrier.  Otherwise every warp copies rows with conversion.
+template <int IN>
+__device__ __forceinline__ void stage_H(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
+                                        float2* Hs, uint64_t* bar)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int rows = pl.U * pl.C;
+    if (pl.bulk) {
+        if (warp == 0) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, (uint32_t)pl.U * pl.B * 8u);
+            }
+            __syncwarp();
+            const float2* Hf = reinterpret_cast<const float2*>(H) + (size_t)f * pl.U * pl.B;
+            for (int row = lane; row < rows; row += 32) {
+                const int c = row / pl.U, u = row - c * pl.U;
+                const ClusterTile ct = tab[c];
+                bulk_g2s(Hs + ct.soff + u * ct.L, Hf + (size_t)u * pl.B + ct.off, (uint32_t)ct.size * 8u, bar);
+            }
+        }
+        return;
+    }
+    for (int row = warp; row < rows; row += nwarps) {
+        const int c = row / pl.U, u = row - c * pl.U;
+        const ClusterTile ct = tab[c];
+        const size_t g0 = ((size_t)f * pl.U + u) * pl.B + ct.off;
+        float2* dst = Hs + ct.soff + u * ct.L;
+        for (int j = lane; j < ct.size; j += 32) dst[j] = Elem<IN>::load(H, g0 + j);
+    }
+}
+
+// Column energies esum[u*C + c] = ||h_{u,c}||^2 from the staged rows: one warp per (c, u) row.
 __device__ __forceinline__ void column_energies(const CdPlan& pl, const ClusterTile* tab, const float2* Hs,
                                                 float* esum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int row = warp; row < pl.U * pl.C; row += nwarps) {
-        const int u = row / pl.C, c = row - u * pl.C;
+        const int c = row / pl.U, u = row - c * pl.U;
         const ClusterTile ct = tab[c];
-        const float2* hr = Hs + (size_t)u * pl.Ltot + ct.soff;
+        const float2* hr = Hs + ct.soff + u * ct.L;
         float s = 0.f;
-        for (int j = lane; j < ct.A * P; j += 32) {
+        for (int j = lane; j < ct.size; j += 32) {
             const float2 h = hr[j];
             s = fmaf(h.x, h.x, fmaf(h.y, h.y, s));
         }
         s = warp_sum(s);
-        if (lane == 0) esum[c * pl.U + u] = s;
+        if (lane == 0) esum[u * pl.C + c] = s;
     }
 }
 
@@ -155,30 +171,56 @@ __device__ __forceinline__ void load_h_pairs(const float2* hr, int A, float2 (&h
     }
 }
 
-// g = sum_j conj(h_j) v_j over the lane's antennas, then over the A lanes of the tile.
-// The xor butterfly leaves bitwise-identical sums on every lane of the tile.
-template <int P>
+// Sum of values over the A lanes of a tile (xor butterfly: bitwise-identical on every lane).
+template <int AT>
+__device__ __forceinline__ float tile_sum(float v, const LaneTile& lt)
+{
+    if (AT > 0) {
+#pragma unroll
+        for (int off = 1; off < AT; off <<= 1) v += __shfl_xor_sync(lt.mask, v, off);
+        return v;
+    }
+    for (int off = 1; off < lt.Awarp; off <<= 1) {
+        const float o = __shfl_xor_sync(lt.mask, v, off);
+        if (off < lt.A) v += o;
+    }
+    return v;
+}
+
+// g = sum_j conj(h_j) v_j over the lane's antennas (four independent accumulator pairs), then over
+// the A lanes of the tile.
+template <int P, int AT>
 __device__ __forceinline__ float2 tile_correlate(const float2 (&h)[P], const float2 (&v)[P], const LaneTile& lt)
 {
-    float gr0 = 0.f, gi0 = 0.f, gr1 = 0.f, gi1 = 0.f;
+    float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < P; j += 2) {
-        gr0 = fmaf(h[j].x, v[j].x, gr0);
-        gi0 = fmaf(h[j].x, v[j].y, gi0);
-        gr1 = fmaf(h[j + 1].x, v[j + 1].x, gr1);
-        gi1 = fmaf(h[j + 1].x, v[j + 1].y, gi1);
-        gr0 = fmaf(h[j].y, v[j].y, gr0);
-        gi0 = fmaf(-h[j].y, v[j].x, gi0);
-        gr1 = fmaf(h[j + 1].y, v[j + 1].y, gr1);
-        gi1 = fmaf(-h[j + 1].y, v[j + 1].x, gi1);
+    for (int j = 0; j < P; ++j) {
+        const int q = j & 3;
+        ar[q] = fmaf(h[j].x, v[j].x, ar[q]);
+        ai[q] = fmaf(h[j].x, v[j].y, ai[q]);
     }
-    float gr = gr0 + gr1, gi = gi0 + gi1;
-    for (int off = 1; off < lt.Awarp; off <<= 1) {
-        const float orr = __shfl_xor_sync(lt.mask, gr, off);
-        const float oi = __shfl_xor_sync(lt.mask, gi, off);
-        if (off < lt.A) {
-            gr += orr;
-            gi += oi;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int q = j & 3;
+        ar[q] = fmaf(h[j].y, v[j].y, ar[q]);
+        ai[q] = fmaf(-h[j].y, v[j].x, ai[q]);
+    }
+    float gr = (ar[0] + ar[1]) + (ar[2] + ar[3]);
+    float gi = (ai[0] + ai[1]) + (ai[2] + ai[3]);
+    if (AT > 0) {
+#pragma unroll
+        for (int off = 1; off < AT; off <<= 1) {
+            gr += __shfl_xor_sync(lt.mask, gr, off);
+            gi += __shfl_xor_sync(lt.mask, gi, off);
+        }
+    } else {
+        for (int off = 1; off < lt.Awarp; off <<= 1) {
+            const float orr = __shfl_xor_sync(lt.mask, gr, off);
+            const float oi = __shfl_xor_sync(lt.mask, gi, off);
+            if (off < lt.A) {
+                gr += orr;
+                gi += oi;
+            }
         }
     }
     return make_float2(gr, gi);
@@ -199,17 +241,22 @@ __device__ __forceinline__ void axpy_update(const float2 (&h)[P], float2 d, floa
 
 __device__ __forceinline__ uint32_t x_stride(const CdPlan& pl) { return (uint32_t)pl.n_tiles | 1u; }
 
+// Register budget: the compile-time-A variants are capped at 96 registers so that three CTAs of
+// seven warps (the 224-thread tiling of B_c = 32, C = 8, 14 symbols) fit on an SM; the generic
+// variant allows 512 threads per CTA.
+#define CDMIMO_CD_SPECIALIZED_REGS 96
+
 // ---------------------------------------------------------------------------------------------
 // Uplink: Algorithm 1 + fusion (Sec. III), one CTA per subcarrier (grid-stride).
 // ---------------------------------------------------------------------------------------------
-template <int P, int IN>
-__global__ void __launch_bounds__(512) cd_detect_kernel(const CdPlan pl, const DetectIO io)
+template <int P, int IN, int AT>
+__global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_detect_kernel(const CdPlan pl, const DetectIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float2* Hs = reinterpret_cast<float2*>(smem);
     float2* Xs = reinterpret_cast<float2*>(smem + pl.off_X);     // [U][x_stride] current x per tile
-    float2* coef = reinterpret_cast<float2*>(smem + pl.off_coef); // [C][U] (m, n) of Algorithm 1
-    float* esum = reinterpret_cast<float*>(smem + pl.off_e);      // [C][U] ||h_{u,c}||^2
+    float2* coef = reinterpret_cast<float2*>(smem + pl.off_coef); // [U][C] (m, n) of Algorithm 1
+    float* esum = reinterpret_cast<float*>(smem + pl.off_e);      // [U][C] ||h_{u,c}||^2
     float* lam = reinterpret_cast<float*>(smem + pl.off_lam);     // [C] fusion weights
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
@@ -224,17 +271,20 @@ __global__ void __launch_bounds__(512) cd_detect_kernel(const CdPlan pl, const D
         fence_proxy_async_smem();
     }
     __syncthreads();
+    zero_padding(pl, tab, Hs);
     const LaneTile lt = map_lane(pl, tab);
     const ClusterTile ct = tab[lt.c];
+    const int A = AT > 0 ? AT : lt.A;
+    const int L = AT > 0 ? AT * P : ct.L;
     const int tile = lt.c * n_sym + lt.n;
 
     uint32_t phase = 0;
     for (int f = blockIdx.x; f < pl.n_sc; f += gridDim.x, phase ^= 1u) {
-        stage_H<P, IN>(pl, tab, io.H, f, Hs, bar);
+        stage_H<IN>(pl, tab, io.H, f, Hs, bar);
 
         // r = y_c (registers), overlapping the channel copy.
         float2 r[P];
-        if (lt.active) load_lane_vec<P, IN>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.A, lt.a, r);
+        if (lt.active) load_lane_vec<P, IN>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, A, lt.a, r);
 
         float alpha = __ldg(io.N0 + f) * pl.inv_Ex;
         float out_scale = 1.f;
@@ -254,7 +304,7 @@ __global__ void __launch_bounds__(512) cd_detect_kernel(const CdPlan pl, const D
         if (__syncthreads_or(!ok)) return;
 
         // Preprocessing (decentralized): column energies, then m and n.
-        column_energies<P>(pl, tab, Hs, esum);
+        column_energies(pl, tab, Hs, esum);
         __syncthreads();
         for (int i = tid; i < C * U; i += blockDim.x) {
             const float e = esum[i];
@@ -272,7 +322,7 @@ __global__ void __launch_bounds__(512) cd_detect_kernel(const CdPlan pl, const D
                 if (c < C) {
                     float s = 0.f;
                     for (int u = 0; u < U; ++u) {
-                        const float den = esum[c * U + u] + alpha;
+                        const float den = esum[u * C + c] + alpha;
                         s += den > 0.f ? 1.f / den : __int_as_float(0x7f800000);
                     }
                     w[k] = 1.f / s;
@@ -295,13 +345,14 @@ __global__ void __launch_bounds__(512) cd_detect_kernel(const CdPlan pl, const D
         if (lt.active) {
             const float2* hb = Hs + ct.soff + 2 * lt.a;
             float2* xs = Xs + tile;
-            const float2* cf = coef + lt.c * U;
+            const float2* cf = coef + lt.c;
             for (int t = 0; t < pl.K; ++t) {
+#pragma unroll 1
                 for (int u = 0; u < U; ++u) {
                     float2 h[P];
-                    load_h_pairs<P>(hb + (size_t)u * pl.Ltot, lt.A, h);
-                    const float2 g = tile_correlate<P>(h, r, lt);
-                    const float2 k = cf[u];
+                    load_h_pairs<P>(hb + u * L, A, h);
+                    const float2 g = tile_correlate<P, AT>(h, r, lt);
+                    const float2 k = cf[u * C];
                     const float2 xo = xs[u * xs_stride];
                     const float2 xn = make_float2(fmaf(k.x, g.x, k.y * xo.x), fmaf(k.x, g.y, k.y * xo.y));
                     xs[u * xs_stride] = xn;
@@ -333,12 +384,12 @@ __global__ void __launch_bounds__(512) cd_detect_kernel(const CdPlan pl, const D
 // The update x -= (hbar^H x - sbar) hbar is applied as x -= p^2 (h^H x - s) h, so hbar is never
 // formed: hbar = p h and sbar = p s give the same product.
 // ---------------------------------------------------------------------------------------------
-template <int P, int IN>
-__global__ void __launch_bounds__(512) cd_precode_kernel(const CdPlan pl, const PrecodeIO io)
+template <int P, int IN, int AT>
+__global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precode_kernel(const CdPlan pl, const PrecodeIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float2* Hs = reinterpret_cast<float2*>(smem);
-    float* p2 = reinterpret_cast<float*>(smem + pl.off_coef);  // [C][U] p_{u,c}^2
+    float* p2 = reinterpret_cast<float*>(smem + pl.off_coef);  // [U][C] p_{u,c}^2
     float* esum = reinterpret_cast<float*>(smem + pl.off_e);
     float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);   // [n_sym][U]
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
@@ -352,19 +403,22 @@ __global__ void __launch_bounds__(512) cd_precode_kernel(const CdPlan pl, const 
         fence_proxy_async_smem();
     }
     __syncthreads();
+    zero_padding(pl, tab, Hs);
     const LaneTile lt = map_lane(pl, tab);
     const ClusterTile ct = tab[lt.c];
+    const int A = AT > 0 ? AT : lt.A;
+    const int L = AT > 0 ? AT * P : ct.L;
 
     uint32_t phase = 0;
     for (int f = blockIdx.x; f < pl.n_sc; f += gridDim.x, phase ^= 1u) {
-        stage_H<P, IN>(pl, tab, io.H, f, Hs, bar);
+        stage_H<IN>(pl, tab, io.H, f, Hs, bar);
         for (int i = tid; i < n_sym * U; i += blockDim.x) Ss[i] = __ldg(io.S + (size_t)f * n_sym * U + i);
 
         bool ok = true;
         if (pl.bulk) ok = mbar_wait_bounded(bar, phase);
         if (__syncthreads_or(!ok)) return;
 
-        column_energies<P>(pl, tab, Hs, esum);
+        column_energies(pl, tab, Hs, esum);
         __syncthreads();
         for (int i = tid; i < C * U; i += blockDim.x) {
             const float e = esum[i];
@@ -377,14 +431,15 @@ __global__ void __launch_bounds__(512) cd_precode_kernel(const CdPlan pl, const 
 #pragma unroll
             for (int j = 0; j < P; ++j) x[j] = make_float2(0.f, 0.f);
             const float2* hb = Hs + ct.soff + 2 * lt.a;
-            const float* pc = p2 + lt.c * U;
+            const float* pc = p2 + lt.c;
             const float2* s = Ss + lt.n * U;
             for (int t = 0; t < pl.K; ++t) {
+#pragma unroll 1
                 for (int u = 0; u < U; ++u) {
                     float2 h[P];
-                    load_h_pairs<P>(hb + (size_t)u * pl.Ltot, lt.A, h);
-                    const float2 g = tile_correlate<P>(h, x, lt);
-                    const float q = pc[u];
+                    load_h_pairs<P>(hb + u * L, A, h);
+                    const float2 g = tile_correlate<P, AT>(h, x, lt);
+                    const float q = pc[u * C];
                     const float2 su = s[u];
                     axpy_update<P>(h, make_float2(q * (g.x - su.x), q * (g.y - su.y)), x);
                 }
@@ -393,15 +448,12 @@ __global__ void __launch_bounds__(512) cd_precode_kernel(const CdPlan pl, const 
             float nr = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) nr = fmaf(x[j].x, x[j].x, fmaf(x[j].y, x[j].y, nr));
-            for (int off = 1; off < lt.Awarp; off <<= 1) {
-                const float o = __shfl_xor_sync(lt.mask, nr, off);
-                if (off < lt.A) nr += o;
-            }
+            nr = tile_sum<AT>(nr, lt);
             const float sc = nr > 0.f ? pl.rho_c * rsqrtf(nr) : 0.f;
             float2* out = io.Xdl + ((size_t)f * n_sym + lt.n) * pl.B + ct.off;
 #pragma unroll
             for (int i = 0; i < P / 2; ++i) {
-                const int col = 2 * (i * lt.A + lt.a);
+                const int col = 2 * (i * A + lt.a);
                 if (col < ct.size) out[col] = make_float2(x[2 * i].x * sc, x[2 * i].y * sc);
                 if (col + 1 < ct.size) out[col + 1] = make_float2(x[2 * i + 1].x * sc, x[2 * i + 1].y * sc);
             }

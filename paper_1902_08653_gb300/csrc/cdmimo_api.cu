@@ -17,7 +17,8 @@ using namespace cdmimo;
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kMaxThreads = 512;  // __launch_bounds__ of the CD kernels
+constexpr int kMaxThreads = 512;             // threads per CTA of the generic CD kernels
+constexpr int kMaxSpecializedThreads = 512;  // the compile-time-A variants (96 registers)
 
 int device_smem_optin()
 {
@@ -68,7 +69,7 @@ int validate(const cdmimo_params* p)
 }
 
 // Build the tiling for antennas-per-lane P.  Returns UNSUPPORTED if the CTA would need more than
-// 1024 threads or more shared memory than the device grants.
+// kMaxThreads threads or more shared memory than the device grants.
 int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan* pl)
 {
     std::memset(pl, 0, sizeof(*pl));
@@ -82,21 +83,24 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     pl->fuse = p->fuse;
     pl->inv_Ex = 1.f / p->Ex;
     pl->rho_c = (float)(p->rho / std::sqrt((double)p->C));
-    pl->coef_sweeps = 1;
     int off = 0, soff = 0;
-    bool unpadded = true;
+    bool all_even = true;
+    pl->A_uniform = -1;
     for (int c = 0; c < p->C; ++c) {
         ClusterTile& ct = pl->cl[c];
         ct.off = off;
         ct.size = p->cluster_size[c];
         ct.A = pow2ceil((ct.size + P - 1) / P);
         if (ct.A > 32) return CDMIMO_ERR_UNSUPPORTED;
+        ct.L = ct.A * P;
         ct.soff = soff;
-        if (ct.A * P != ct.size) unpadded = false;
+        if (ct.L != ct.size) pl->padded = 1;
+        if (ct.size & 1) all_even = false;
+        pl->A_uniform = (pl->A_uniform == -1 || pl->A_uniform == ct.A) ? ct.A : 0;
         off += ct.size;
-        soff += ct.A * P;
+        soff += p->U * ct.L + 2 * ct.A;  // skew: the next block starts 16*A bytes further in the bank cycle
     }
-    pl->Ltot = soff;
+    pl->h_entries = soff;
     // Lanes: clusters in order of decreasing A so every tile's lane group is A-aligned in its warp.
     int order[CDMIMO_MAX_CLUSTERS];
     for (int c = 0; c < p->C; ++c) order[c] = c;
@@ -112,12 +116,12 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     if (pl->n_lanes > kMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
 
     const unsigned U = p->U, C = p->C;
-    unsigned o = align16(U * pl->Ltot * 8u);
+    unsigned o = align16((unsigned)pl->h_entries * 8u);
     if (detect) {
         pl->off_X = o;
         o = align16(o + U * ((unsigned)pl->n_tiles | 1u) * 8u);
         pl->off_coef = o;
-        o = align16(o + pl->coef_sweeps * C * U * 8u);
+        o = align16(o + C * U * 8u);
         pl->off_lam = o;
         o = align16(o + C * 4u);
     } else {
@@ -135,13 +139,12 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     pl->smem_bytes = o;
     if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
 
-    const size_t hbytes = (size_t)U * p->B * 8u;
-    pl->bulk = (p->in_dtype == CDMIMO_C64 && unpadded && (hbytes % 16) == 0 && aligned(H, 16)) ? 1 : 0;
+    pl->bulk = (p->in_dtype == CDMIMO_C64 && all_even && aligned(H, 16)) ? 1 : 0;
     return CDMIMO_OK;
 }
 
 // Antennas per lane: 16 by default (two lanes per tile at B_c = 32), 8 for tiny clusters, 32 when
-// 16 would need more than 1024 threads per CTA.
+// 16 would need more threads than a CTA may have.
 int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
 {
     int maxBc = 0;
@@ -157,41 +160,55 @@ int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
 
 int threads_for(const CdPlan& pl) { return std::max(64, (pl.n_lanes + 31) / 32 * 32); }
 
+// Per-kernel attributes: dynamic shared memory above 48 KB, and the largest shared-memory carveout
+// so that several CTAs of one kernel share an SM.
 template <typename Kern>
-int prepare_kernel(Kern k, unsigned smem)
+int launch_cd(Kern k, const CdPlan& pl, cudaStream_t s)
 {
-    if (smem > 48u * 1024u) {
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    (void)s;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    if (pl.smem_bytes > 48u * 1024u) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_bytes) != cudaSuccess)
             return CDMIMO_ERR_CUDA;
     }
     return CDMIMO_OK;
 }
 
-template <int P, int IN>
+template <int P, int IN, int AT>
 int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
-    auto k = cd_detect_kernel<P, IN>;
-    if (int rc = prepare_kernel(k, pl.smem_bytes)) return rc;
+    auto k = cd_detect_kernel<P, IN, AT>;
+    if (int rc = launch_cd(k, pl, s)) return rc;
     k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
-template <int P, int IN>
+template <int P, int IN, int AT>
 int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 {
-    auto k = cd_precode_kernel<P, IN>;
-    if (int rc = prepare_kernel(k, pl.smem_bytes)) return rc;
+    auto k = cd_precode_kernel<P, IN, AT>;
+    if (int rc = launch_cd(k, pl, s)) return rc;
     k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
+// Kernel variant: compile-time lanes per tile for uniform partitions at P = 16 (B_c in (8, 64]),
+// run-time lanes per tile otherwise.
 template <int IN>
 int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
+    if (pl.P == 16 && pl.n_lanes <= kMaxSpecializedThreads) {
+        switch (pl.A_uniform) {
+        case 1: return launch_detect_t<16, IN, 1>(pl, io, s);
+        case 2: return launch_detect_t<16, IN, 2>(pl, io, s);
+        case 4: return launch_detect_t<16, IN, 4>(pl, io, s);
+        }
+    }
     switch (pl.P) {
-    case 8: return launch_detect_t<8, IN>(pl, io, s);
-    case 16: return launch_detect_t<16, IN>(pl, io, s);
-    case 32: return launch_detect_t<32, IN>(pl, io, s);
+    case 8: return launch_detect_t<8, IN, 0>(pl, io, s);
+    case 16: return launch_detect_t<16, IN, 0>(pl, io, s);
+    case 32: return launch_detect_t<32, IN, 0>(pl, io, s);
     }
     return CDMIMO_ERR_UNSUPPORTED;
 }
@@ -199,10 +216,17 @@ int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 template <int IN>
 int dispatch_precode(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 {
+    if (pl.P == 16 && pl.n_lanes <= kMaxSpecializedThreads) {
+        switch (pl.A_uniform) {
+        case 1: return launch_precode_t<16, IN, 1>(pl, io, s);
+        case 2: return launch_precode_t<16, IN, 2>(pl, io, s);
+        case 4: return launch_precode_t<16, IN, 4>(pl, io, s);
+        }
+    }
     switch (pl.P) {
-    case 8: return launch_precode_t<8, IN>(pl, io, s);
-    case 16: return launch_precode_t<16, IN>(pl, io, s);
-    case 32: return launch_precode_t<32, IN>(pl, io, s);
+    case 8: return launch_precode_t<8, IN, 0>(pl, io, s);
+    case 16: return launch_precode_t<16, IN, 0>(pl, io, s);
+    case 32: return launch_precode_t<32, IN, 0>(pl, io, s);
     }
     return CDMIMO_ERR_UNSUPPORTED;
 }
