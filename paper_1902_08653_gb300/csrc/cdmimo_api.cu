@@ -9,6 +9,7 @@
 #include <cstring>
 
 #include "cd_kernels.cuh"
+#include "cd_kernels_pp.cuh"
 #include "cdmimo.h"
 #include "plan.h"
 
@@ -178,7 +179,9 @@ int launch_cd(Kern k, const CdPlan& pl, cudaStream_t s)
 template <int P, int IN, int AT>
 int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
-    auto k = cd_detect_kernel<P, IN, AT>;
+    void (*k)(const CdPlan, const DetectIO);
+    if constexpr (AT > 0) k = cd_detect_pp_kernel<IN, AT>;
+    else k = cd_detect_kernel<P, IN, 0>;
     if (int rc = launch_cd(k, pl, s)) return rc;
     k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
@@ -187,14 +190,16 @@ int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 template <int P, int IN, int AT>
 int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 {
-    auto k = cd_precode_kernel<P, IN, AT>;
+    void (*k)(const CdPlan, const PrecodeIO);
+    if constexpr (AT > 0) k = cd_precode_pp_kernel<IN, AT>;
+    else k = cd_precode_kernel<P, IN, 0>;
     if (int rc = launch_cd(k, pl, s)) return rc;
     k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
-// Kernel variant: compile-time lanes per tile for uniform partitions at P = 16 (B_c in (8, 64]),
-// run-time lanes per tile otherwise.
+// Kernel variant: packed-FP32 kernels with compile-time lanes per tile for uniform partitions at
+// P = 16 (B_c in (8, 64]), scalar kernels with run-time lanes per tile otherwise.
 template <int IN>
 int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
