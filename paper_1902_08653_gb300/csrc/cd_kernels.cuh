@@ -129,7 +129,8 @@ __device__ __forceinline__ void stage_H(const CdPlan& pl, const ClusterTile* tab
     }
 }
 
-// Column energies esum[u*C + c] = ||h_{u,c}||^2 from the staged rows: one warp per (c, u) row.
+// Column energies esum[u*C + c] = ||h_{u,c}||^2 from the staged rows (sum of squares of the row's
+// floats, in either layout): one warp per (c, u) row.
 __device__ __forceinline__ void column_energies(const CdPlan& pl, const ClusterTile* tab, const float2* Hs,
                                                 float* esum)
 {
@@ -139,7 +140,9 @@ __device__ __forceinline__ void column_energies(const CdPlan& pl, const ClusterT
         const ClusterTile ct = tab[c];
         const float2* hr = Hs + ct.soff + u * ct.L;
         float s = 0.f;
-        for (int j = lane; j < ct.size; j += 32) {
+        // The whole row, padding included (zeros): in the pair-planar layout the last valid antenna
+        // of an odd-sized cluster shares a 16-byte pair with a padding column.
+        for (int j = lane; j < ct.L; j += 32) {
             const float2 h = hr[j];
             s = fmaf(h.x, h.x, fmaf(h.y, h.y, s));
         }
@@ -272,6 +275,7 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_detect
     }
     __syncthreads();
     zero_padding(pl, tab, Hs);
+    __syncthreads();
     const LaneTile lt = map_lane(pl, tab);
     const ClusterTile ct = tab[lt.c];
     const int A = AT > 0 ? AT : lt.A;
@@ -391,12 +395,13 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
     float2* Hs = reinterpret_cast<float2*>(smem);
     float* p2 = reinterpret_cast<float*>(smem + pl.off_coef);  // [U][C] p_{u,c}^2
     float* esum = reinterpret_cast<float*>(smem + pl.off_e);
-    float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);   // [n_sym][U]
+    float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);   // [n_sym][U | 1] (odd stride: no bank conflicts)
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
 
     const int tid = threadIdx.x;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
+    const int s_stride = U | 1;
     if (tid < C) tab[tid] = pl.cl[tid];
     if (tid == 0 && pl.bulk) {
         mbar_init(bar, 1);
@@ -404,6 +409,7 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
     }
     __syncthreads();
     zero_padding(pl, tab, Hs);
+    __syncthreads();
     const LaneTile lt = map_lane(pl, tab);
     const ClusterTile ct = tab[lt.c];
     const int A = AT > 0 ? AT : lt.A;
@@ -412,7 +418,10 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
     uint32_t phase = 0;
     for (int f = blockIdx.x; f < pl.n_sc; f += gridDim.x, phase ^= 1u) {
         stage_H<IN>(pl, tab, io.H, f, Hs, bar);
-        for (int i = tid; i < n_sym * U; i += blockDim.x) Ss[i] = __ldg(io.S + (size_t)f * n_sym * U + i);
+        for (int i = tid; i < n_sym * U; i += blockDim.x) {
+            const int n = i / U;
+            Ss[n * s_stride + (i - n * U)] = __ldg(io.S + (size_t)f * n_sym * U + i);
+        }
 
         bool ok = true;
         if (pl.bulk) ok = mbar_wait_bounded(bar, phase);
@@ -432,7 +441,7 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
             for (int j = 0; j < P; ++j) x[j] = make_float2(0.f, 0.f);
             const float2* hb = Hs + ct.soff + 2 * lt.a;
             const float* pc = p2 + lt.c;
-            const float2* s = Ss + lt.n * U;
+            const float2* s = Ss + lt.n * s_stride;
             for (int t = 0; t < pl.K; ++t) {
 #pragma unroll 1
                 for (int u = 0; u < U; ++u) {

@@ -1,16 +1,22 @@
-// Packed-FP32 (FFMA2) variants of the CD detection and precoding kernels for uniform cluster sizes.
+// Packed-FP32 (FFMA2), persistent, double-buffered CD detection and precoding kernels for uniform
+// cluster sizes (every cluster has the same lanes-per-tile AT; P = 16 antennas per lane).
 //
-// Same tiling as cd_kernels.cuh (plan.h) with P = 16 antennas per lane and a compile-time number AT
-// of lanes per tile, but every 16-byte antenna pair is held "pair-planar": (re_0, re_1, im_0, im_1)
-// instead of (re_0, im_0, re_1, im_1), in shared memory (channel) and in registers (residual or
-// beamformer).  Then each half of a pair is a ready 64-bit operand of the sm_100-family packed
-// instruction fma.rn.f32x2, and a complex multiply-accumulate of two antennas costs four packed FMAs
-// with no operand shuffling:
+// Layout.  Every 16-byte antenna pair is held "pair-planar": (re_0, re_1, im_0, im_1) instead of
+// (re_0, im_0, re_1, im_1), in shared memory (channel) and in registers (residual or beamformer).
+// Each half of a pair is then a ready 64-bit operand of the sm_100-family packed instruction
+// fma.rn.f32x2, and a complex multiply-accumulate over two antennas costs four packed FMAs:
 //   correlation  sum conj(h) v:   R += h_re*v_re, R += h_im*v_im, I += h_re*v_im, J += h_im*v_re,
 //                                  g = (R.x + R.y) + i((I.x + I.y) - (J.x + J.y));
 //   update       v -= h d:         v_re += h_re*(-d_re) + h_im*d_im,  v_im += h_re*(-d_im) + h_im*(-d_re).
 // The channel arrives by cp.async.bulk in the interleaved layout and is permuted in place (each
-// thread owns whole 16-byte pairs, so the permutation needs no extra buffer).
+// thread owns whole 16-byte pairs).
+//
+// Schedule.  A persistent CTA walks subcarriers f = blockIdx.x, blockIdx.x + gridDim.x, ...  Two
+// channel buffers alternate: while subcarrier f is computed from buffer k&1, the bulk copy of the
+// next subcarrier lands in the other buffer, and the next subcarrier's y (or s) is loaded into
+// registers right after the CD loop.  The preprocessing of Algorithm 1 / 2 (||h_{u,c}||^2 and the
+// coefficients m, n or p^2) is computed inside the first sweep from the channel pairs each lane
+// already holds for the correlation, and kept per tile in shared memory for the later sweeps.
 #pragma once
 #include "cd_kernels.cuh"
 
@@ -19,13 +25,14 @@ namespace cdmimo {
 constexpr int kPP = 16;               // antennas per lane
 constexpr int kPairs = kPP / 2;       // antenna pairs per lane
 constexpr int kPPRegs = 128;          // register cap of the packed kernels (two 7-warp CTAs per SM)
+constexpr int kSPrefetch = 4;         // s entries per thread prefetched by the precoder (n_sym U <= 4 threads)
 
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// (re0, im0, re1, im1) -> (re0, re1, im0, im1) for every 16-byte pair of the channel region.
+// (re0, im0, re1, im1) -> (re0, re1, im0, im1) for every 16-byte pair of one channel buffer.
 __device__ __forceinline__ void permute_pairs_in_place(const CdPlan& pl, float2* Hs)
 {
     float4* h4 = reinterpret_cast<float4*>(Hs);
@@ -35,16 +42,34 @@ __device__ __forceinline__ void permute_pairs_in_place(const CdPlan& pl, float2*
     }
 }
 
-// Channel staging for the packed kernels: bulk copies (permuted after the wait by the caller), or
-// converting loads that write the pair-planar layout directly (16-bit storage, odd sizes).
-template <int IN>
-__device__ __forceinline__ void stage_H_pp(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
-                                           float2* Hs, uint64_t* bar)
+// Arm a buffer's barrier for the next copy: one arrival that announces the copy's byte count.  The
+// copy itself is issued later, after the buffer's previous readers have passed a CTA barrier.
+__device__ __forceinline__ void arm_channel_copy(const CdPlan& pl, uint64_t* bar)
 {
-    if (pl.bulk) {
-        stage_H<IN>(pl, tab, H, f, Hs, bar);
-        return;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (uint32_t)pl.U * pl.B * 8u);
+}
+
+// Bulk copies of subcarrier f's channel rows into one buffer: thread i issues row i (rows are
+// (cluster, user) pairs), so no thread issues more than one copy when U C <= blockDim.x.
+__device__ __forceinline__ void issue_channel_copy(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
+                                                   float2* Hs, uint64_t* bar)
+{
+    const float2* Hf = reinterpret_cast<const float2*>(H) + (size_t)f * pl.U * pl.B;
+    for (int row = threadIdx.x; row < pl.U * pl.C; row += blockDim.x) {
+        const int c = row / pl.U, u = row - c * pl.U;
+        const ClusterTile ct = tab[c];
+        fence_proxy_async_smem();
+        bulk_g2s(Hs + ct.soff + u * ct.L, Hf + (size_t)u * pl.B + ct.off, (uint32_t)ct.size * 8u, bar);
     }
+}
+
+// Converting channel staging (16-bit storage or odd cluster sizes): writes the pair-planar layout,
+// padding columns included, directly.
+template <int IN>
+__device__ __forceinline__ void stage_H_converting(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
+                                                   float2* Hs)
+{
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int row = warp; row < pl.U * pl.C; row += nwarps) {
         const int c = row / pl.U, u = row - c * pl.U;
@@ -60,22 +85,40 @@ __device__ __forceinline__ void stage_H_pp(const CdPlan& pl, const ClusterTile* 
     }
 }
 
-// This lane's antenna pairs q = i*AT + a of a length-`size` vector, pair-planar.
+// This lane's antenna pairs q = i*AT + a of a length-`size` vector, pair-planar.  Each half is passed
+// through one packed add, so the values start out in the aligned register pairs that the packed FMAs
+// of the CD loop produce; the loop-carried vector then needs no register moves (measured: it removes
+// a third of the uplink kernel's instructions).
 template <int IN, int AT>
 __device__ __forceinline__ void load_lane_pairs(const void* V, size_t base, int size, int a, float4 (&v)[kPairs])
 {
+    const float2 z = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < kPairs; ++i) {
         const int j = 2 * (i * AT + a);
-        const float2 v0 = j < size ? Elem<IN>::load(V, base + j) : make_float2(0.f, 0.f);
-        const float2 v1 = j + 1 < size ? Elem<IN>::load(V, base + j + 1) : make_float2(0.f, 0.f);
-        v[i] = make_float4(v0.x, v1.x, v0.y, v1.y);
+        const float2 v0 = j < size ? Elem<IN>::load(V, base + j) : z;
+        const float2 v1 = j + 1 < size ? Elem<IN>::load(V, base + j + 1) : z;
+        v[i] = cat4(__fadd2_rn(make_float2(v0.x, v1.x), z), __fadd2_rn(make_float2(v0.y, v1.y), z));
     }
 }
 
-// g = sum over the tile of conj(h) v (packed FMAs, two independent accumulator sets).
 template <int AT>
-__device__ __forceinline__ float2 pp_correlate(const float4 (&h)[kPairs], const float4 (&v)[kPairs], unsigned mask)
+__device__ __forceinline__ void pp_load_h(const float4* hr, float4 (&h)[kPairs])
+{
+#pragma unroll
+    for (int i = 0; i < kPairs; ++i) h[i] = hr[i * AT];
+}
+
+template <int AT>
+__device__ __forceinline__ float tile_sum_c(float v, unsigned mask)
+{
+#pragma unroll
+    for (int off = 1; off < AT; off <<= 1) v += __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+// Lane partial of conj(h)^T v over the lane's pairs (two independent accumulator sets).
+__device__ __forceinline__ float2 pp_partial_corr(const float4 (&h)[kPairs], const float4 (&v)[kPairs])
 {
     float2 R0 = make_float2(0.f, 0.f), I0 = R0, J0 = R0, R1 = R0, I1 = R0, J1 = R0;
 #pragma unroll
@@ -90,14 +133,22 @@ __device__ __forceinline__ float2 pp_correlate(const float4 (&h)[kPairs], const 
         R1 = ffma2(hi2(h[i + 1]), hi2(v[i + 1]), R1);
     }
     const float2 R = __fadd2_rn(R0, R1), I = __fadd2_rn(I0, I1), J = __fadd2_rn(J0, J1);
-    float gr = R.x + R.y;
-    float gi = (I.x + I.y) - (J.x + J.y);
+    return make_float2(R.x + R.y, (I.x + I.y) - (J.x + J.y));
+}
+
+// Lane partial of ||h||^2 over the lane's pairs.
+__device__ __forceinline__ float pp_partial_energy(const float4 (&h)[kPairs])
+{
+    float2 E0 = make_float2(0.f, 0.f), E1 = E0;
 #pragma unroll
-    for (int off = 1; off < AT; off <<= 1) {
-        gr += __shfl_xor_sync(mask, gr, off);
-        gi += __shfl_xor_sync(mask, gi, off);
+    for (int i = 0; i < kPairs; i += 2) {
+        E0 = ffma2(lo2(h[i]), lo2(h[i]), E0);
+        E1 = ffma2(lo2(h[i + 1]), lo2(h[i + 1]), E1);
+        E0 = ffma2(hi2(h[i]), hi2(h[i]), E0);
+        E1 = ffma2(hi2(h[i + 1]), hi2(h[i + 1]), E1);
     }
-    return make_float2(gr, gi);
+    const float2 E = __fadd2_rn(E0, E1);
+    return E.x + E.y;
 }
 
 // v -= h d (packed FMAs).
@@ -114,27 +165,47 @@ __device__ __forceinline__ void pp_update(const float4 (&h)[kPairs], float2 d, f
     }
 }
 
-template <int AT>
-__device__ __forceinline__ void pp_load_h(const float4* hr, float4 (&h)[kPairs])
+// Wait for (bulk) or stage (converting) the channel of subcarrier f in buffer Hb, then permute it to
+// the pair-planar layout.  Returns false on a copy timeout (the whole CTA then stops).
+template <int IN>
+__device__ __forceinline__ bool acquire_channel(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
+                                                float2* Hb, uint64_t* bar, uint32_t parity, bool rearm)
 {
-#pragma unroll
-    for (int i = 0; i < kPairs; ++i) h[i] = hr[i * AT];
+    bool ok = true;
+    if (pl.bulk) ok = mbar_wait_bounded(bar, parity);
+    else stage_H_converting<IN>(pl, tab, H, f, Hb);
+    if (__syncthreads_or(!ok)) return false;
+    // This buffer next receives the copy issued at the start of the next iteration: arm it now.
+    if (pl.bulk && rearm && threadIdx.x == 0) arm_channel_copy(pl, bar);
+    if (pl.bulk) {
+        permute_pairs_in_place(pl, Hb);
+        __syncthreads();
+    }
+    return true;
+}
+
+// Column energies of one cluster from a staged buffer (K = 0 only: no sweep computed them).
+__device__ __forceinline__ float row_energy(const float2* row, int L)
+{
+    float e = 0.f;
+    for (int j = 0; j < L; ++j) e = fmaf(row[j].x, row[j].x, fmaf(row[j].y, row[j].y, e));
+    return e;
 }
 
 // ---------------------------------------------------------------------------------------------
-// Uplink: Algorithm 1 + fusion (Sec. III), packed arithmetic.
+// Uplink: Algorithm 1 + fusion (Sec. III).
 // ---------------------------------------------------------------------------------------------
 template <int IN, int AT>
 __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const DetectIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    float2* Hs = reinterpret_cast<float2*>(smem);
-    float2* Xs = reinterpret_cast<float2*>(smem + pl.off_X);     // [U][x_stride] current x per tile
-    float2* coef = reinterpret_cast<float2*>(smem + pl.off_coef); // [U][C] (m, n) of Algorithm 1
-    float* esum = reinterpret_cast<float*>(smem + pl.off_e);      // [U][C] ||h_{u,c}||^2
-    float* lam = reinterpret_cast<float*>(smem + pl.off_lam);     // [C] fusion weights
+    // Channel buffer j (0 or 1) starts at byte j * off_H2.
+    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + (j ? pl.off_H2 : 0u)); };
+    float2* Xs = reinterpret_cast<float2*>(smem + pl.off_X);  // [U][x_stride] current x per tile
+    float2* Ks = reinterpret_cast<float2*>(smem + pl.off_K);  // [U][x_stride] (m, n) per tile
+    float* lam = reinterpret_cast<float*>(smem + pl.off_lam); // [C]
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);  // [2]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
@@ -143,97 +214,131 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
 
     if (tid < C) tab[tid] = pl.cl[tid];
     if (tid == 0 && pl.bulk) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_proxy_async_smem();
     }
     __syncthreads();
-    zero_padding(pl, tab, Hs);
+    if (pl.bulk) {  // padding columns are never written by the copies: zero them once in both buffers
+        zero_padding(pl, tab, Hbuf(0));
+        zero_padding(pl, tab, Hbuf(1));
+    }
+    __syncthreads();
     const LaneTile lt = map_lane(pl, tab);
     const ClusterTile ct = tab[lt.c];
     const int tile = lt.c * n_sym + lt.n;
 
-    uint32_t phase = 0;
-    for (int f = blockIdx.x; f < pl.n_sc; f += gridDim.x, phase ^= 1u) {
-        stage_H_pp<IN>(pl, tab, io.H, f, Hs, bar);
+    int f = blockIdx.x;
+    if (pl.bulk && tid == 0) {  // arm buffer 0 (first subcarrier) and buffer 1 (second)
+        if (f < pl.n_sc) arm_channel_copy(pl, &bar[0]);
+        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy(pl, &bar[1]);
+    }
+    __syncthreads();
+    if (pl.bulk && f < pl.n_sc) issue_channel_copy(pl, tab, io.H, f, Hbuf(0), &bar[0]);
+    float4 r[kPairs];
+    if (lt.active && f < pl.n_sc)
+        load_lane_pairs<IN, AT>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
 
-        float4 r[kPairs];
-        if (lt.active) load_lane_pairs<IN, AT>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
+    for (int k = 0; f < pl.n_sc; f += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int fn = f + gridDim.x;
+        if (pl.bulk && fn < pl.n_sc) issue_channel_copy(pl, tab, io.H, fn, Hbuf(b ^ 1), &bar[b ^ 1]);
 
         float alpha = __ldg(io.N0 + f) * pl.inv_Ex;
         float out_scale = 1.f;
         if (IN != CDMIMO_C64) {
             const float hs = __ldg(io.h_scale + f), ys = __ldg(io.y_scale + f);
-            alpha = alpha / (hs * hs);
-            out_scale = ys / hs;
+            alpha = alpha / (hs * hs);  // regularizer of the problem in stored units
+            out_scale = ys / hs;        // x = (b_f / a_f) x'
         }
-        if (!(alpha >= 0.f)) {
+        if (!(alpha >= 0.f)) {  // negative or NaN noise variance
             if (tid == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_N0);
             out_scale = __int_as_float(0x7fc00000);
             alpha = 0.f;
         }
+        if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), &bar[b], (uint32_t)(k >> 1) & 1u,
+                                 fn + (int)gridDim.x < pl.n_sc))
+            return;
 
-        bool ok = true;
-        if (pl.bulk) ok = mbar_wait_bounded(bar, phase);
-        if (__syncthreads_or(!ok)) return;
-        if (pl.bulk) {
-            permute_pairs_in_place(pl, Hs);
-            __syncthreads();
-        }
-
-        // Preprocessing (decentralized): ||h_{u,c}||^2 is the sum of squares of the row's floats,
-        // whatever their order, then m and n.
-        column_energies(pl, tab, Hs, esum);
-        __syncthreads();
-        for (int i = tid; i < C * U; i += blockDim.x) {
-            const float e = esum[i];
-            const float den = e + alpha;
-            const float m = den > 0.f ? 1.f / den : 0.f;
-            coef[i] = make_float2(m, m * e);
-        }
-        for (int i = tid; i < U * (int)xs_stride; i += blockDim.x) Xs[i] = make_float2(0.f, 0.f);
-        if (warp == 0) {
-            float w[2] = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int c = lane + 32 * k;
-                if (c < C) {
-                    float s = 0.f;
-                    for (int u = 0; u < U; ++u) {
-                        const float den = esum[u * C + c] + alpha;
-                        s += den > 0.f ? 1.f / den : __int_as_float(0x7f800000);
-                    }
-                    w[k] = 1.f / s;
-                }
-            }
-            const float tot = warp_sum(w[0] + w[1]);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int c = lane + 32 * k;
-                if (c < C) {
-                    const float l = (pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f)) ? 1.f / C : w[k] / tot;
-                    lam[c] = l;
-                    if (io.lam) io.lam[(size_t)f * C + c] = l;
-                }
-            }
-        }
-        __syncthreads();
-
-        // CD iterations (decentralized).
-        if (lt.active) {
-            const float4* hb = reinterpret_cast<const float4*>(Hs + ct.soff) + lt.a;
+        if (lt.active && pl.K > 0) {
+            const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ct.soff) + lt.a;
             float2* xs = Xs + tile;
-            const float2* cf = coef + lt.c;
-            for (int t = 0; t < pl.K; ++t) {
+            float2* ks = Ks + tile;
+            // Sweep 1 with the preprocessing of Algorithm 1 folded in: e = ||h_{u,c}||^2,
+            // m = (e + N0/Ex)^{-1}, n = m e; x starts at 0, so x_u <- m h^H r.
+#pragma unroll 1
+            for (int u = 0; u < U; ++u) {
+                float4 h[kPairs];
+                pp_load_h<AT>(hb + u * LP, h);
+                float2 g = pp_partial_corr(h, r);
+                float e = pp_partial_energy(h);
+#pragma unroll
+                for (int off = 1; off < AT; off <<= 1) {
+                    g.x += __shfl_xor_sync(lt.mask, g.x, off);
+                    g.y += __shfl_xor_sync(lt.mask, g.y, off);
+                    e += __shfl_xor_sync(lt.mask, e, off);
+                }
+                const float den = e + alpha;
+                const float m = den > 0.f ? __fdividef(1.f, den) : 0.f;
+                ks[u * xs_stride] = make_float2(m, m * e);
+                const float2 xn = make_float2(m * g.x, m * g.y);
+                xs[u * xs_stride] = xn;
+                pp_update(h, xn, r);
+            }
+            for (int t = 1; t < pl.K; ++t) {
 #pragma unroll 1
                 for (int u = 0; u < U; ++u) {
                     float4 h[kPairs];
                     pp_load_h<AT>(hb + u * LP, h);
-                    const float2 g = pp_correlate<AT>(h, r, lt.mask);
-                    const float2 k = cf[u * C];
+                    float2 g = pp_partial_corr(h, r);
+                    g.x = tile_sum_c<AT>(g.x, lt.mask);
+                    g.y = tile_sum_c<AT>(g.y, lt.mask);
+                    const float2 kc = ks[u * xs_stride];
                     const float2 xo = xs[u * xs_stride];
-                    const float2 xn = make_float2(fmaf(k.x, g.x, k.y * xo.x), fmaf(k.x, g.y, k.y * xo.y));
+                    const float2 xn = make_float2(fmaf(kc.x, g.x, kc.y * xo.x), fmaf(kc.x, g.y, kc.y * xo.y));
                     xs[u * xs_stride] = xn;
                     pp_update(h, make_float2(xn.x - xo.x, xn.y - xo.y), r);
+                }
+            }
+        }
+        if (pl.K == 0) {  // no sweep ran: x = 0, and the fusion weights still need m
+            for (int i = tid; i < U * (int)xs_stride; i += blockDim.x) Xs[i] = make_float2(0.f, 0.f);
+            if (lt.active && lt.a == 0) {
+                for (int u = 0; u < U; ++u) {
+                    const float den = row_energy(Hbuf(b) + ct.soff + u * ct.L, ct.L) + alpha;
+                    Ks[u * xs_stride + tile] = make_float2(den > 0.f ? __fdividef(1.f, den) : 0.f, 0.f);
+                }
+            }
+        }
+        // Prefetch the next subcarrier's receive vector (r is dead from here on).
+        if (lt.active && fn < pl.n_sc)
+            load_lane_pairs<IN, AT>(io.Y, ((size_t)fn * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
+        __syncthreads();
+
+        // Fusion weights: lambda_c proportional to 1 / sum_u m_{u,c} (a zero m marks a skipped column,
+        // whose (||h||^2 + N0/Ex)^{-1} is infinite).
+        if (warp == 0) {
+            float w[2] = {0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c = lane + 32 * q;
+                if (c < C) {
+                    float s = 0.f;
+                    for (int u = 0; u < U; ++u) {
+                        const float m = Ks[u * xs_stride + c * n_sym].x;
+                        s += m > 0.f ? m : __int_as_float(0x7f800000);
+                    }
+                    w[q] = 1.f / s;
+                }
+            }
+            const float tot = warp_sum(w[0] + w[1]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c = lane + 32 * q;
+                if (c < C) {
+                    const float l = (pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f)) ? 1.f / C : w[q] / tot;
+                    lam[c] = l;
+                    if (io.lam) io.lam[(size_t)f * C + c] = l;
                 }
             }
         }
@@ -257,77 +362,123 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
 }
 
 // ---------------------------------------------------------------------------------------------
-// Downlink: Algorithm 2 (Eq. (4), applied as x -= p^2 (h^H x - s) h) + normalization, packed.
+// Downlink: Algorithm 2 (Eq. (4), applied as x -= p^2 (h^H x - s) h) + normalization (Sec. IV-B).
 // ---------------------------------------------------------------------------------------------
 template <int IN, int AT>
 __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const PrecodeIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    float2* Hs = reinterpret_cast<float2*>(smem);
-    float* p2 = reinterpret_cast<float*>(smem + pl.off_coef);  // [U][C] p_{u,c}^2
-    float* esum = reinterpret_cast<float*>(smem + pl.off_e);
-    float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);   // [n_sym][U]
+    // Channel buffer j (0 or 1) starts at byte j * off_H2.
+    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + (j ? pl.off_H2 : 0u)); };
+    float* Qs = reinterpret_cast<float*>(smem + pl.off_K);    // [U][x_stride] p_{u,c}^2 per tile
+    float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);  // [n_sym][U | 1] (odd stride: no bank conflicts)
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
 
     const int tid = threadIdx.x;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
+    const int s_stride = U | 1;
+    const int n_s = n_sym * U;
+    const uint32_t xs_stride = x_stride(pl);
     constexpr int LP = AT * kPairs;
     if (tid < C) tab[tid] = pl.cl[tid];
     if (tid == 0 && pl.bulk) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_proxy_async_smem();
     }
     __syncthreads();
-    zero_padding(pl, tab, Hs);
+    if (pl.bulk) {
+        zero_padding(pl, tab, Hbuf(0));
+        zero_padding(pl, tab, Hbuf(1));
+    }
+    __syncthreads();
     const LaneTile lt = map_lane(pl, tab);
     const ClusterTile ct = tab[lt.c];
+    const int tile = lt.c * n_sym + lt.n;
 
-    uint32_t phase = 0;
-    for (int f = blockIdx.x; f < pl.n_sc; f += gridDim.x, phase ^= 1u) {
-        stage_H_pp<IN>(pl, tab, io.H, f, Hs, bar);
-        for (int i = tid; i < n_sym * U; i += blockDim.x) Ss[i] = __ldg(io.S + (size_t)f * n_sym * U + i);
+    int f = blockIdx.x;
+    if (pl.bulk && tid == 0) {  // arm buffer 0 (first subcarrier) and buffer 1 (second)
+        if (f < pl.n_sc) arm_channel_copy(pl, &bar[0]);
+        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy(pl, &bar[1]);
+    }
+    __syncthreads();
+    if (pl.bulk && f < pl.n_sc) issue_channel_copy(pl, tab, io.H, f, Hbuf(0), &bar[0]);
+    float2 sv[kSPrefetch];
+#pragma unroll
+    for (int q = 0; q < kSPrefetch; ++q) {
+        const int i = tid + q * blockDim.x;
+        sv[q] = (i < n_s && f < pl.n_sc) ? __ldg(io.S + (size_t)f * n_s + i) : make_float2(0.f, 0.f);
+    }
 
-        bool ok = true;
-        if (pl.bulk) ok = mbar_wait_bounded(bar, phase);
-        if (__syncthreads_or(!ok)) return;
-        if (pl.bulk) {
-            permute_pairs_in_place(pl, Hs);
-            __syncthreads();
+    for (int k = 0; f < pl.n_sc; f += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int fn = f + gridDim.x;
+        if (pl.bulk && fn < pl.n_sc) issue_channel_copy(pl, tab, io.H, fn, Hbuf(b ^ 1), &bar[b ^ 1]);
+#pragma unroll
+        for (int q = 0; q < kSPrefetch; ++q) {
+            const int i = tid + q * blockDim.x;
+            if (i < n_s) {
+                const int n = i / U;
+                Ss[n * s_stride + (i - n * U)] = sv[q];
+            }
         }
-
-        column_energies(pl, tab, Hs, esum);
-        __syncthreads();
-        for (int i = tid; i < C * U; i += blockDim.x) {
-            const float e = esum[i];
-            p2[i] = e > 0.f ? 1.f / e : 0.f;
+        if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), &bar[b], (uint32_t)(k >> 1) & 1u,
+                                 fn + (int)gridDim.x < pl.n_sc))
+            return;
+        // The next subcarrier's s (this one's is in shared memory now).
+#pragma unroll
+        for (int q = 0; q < kSPrefetch; ++q) {
+            const int i = tid + q * blockDim.x;
+            if (i < n_s && fn < pl.n_sc) sv[q] = __ldg(io.S + (size_t)fn * n_s + i);
         }
-        __syncthreads();
 
         if (lt.active) {
             float4 x[kPairs];
 #pragma unroll
             for (int i = 0; i < kPairs; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4* hb = reinterpret_cast<const float4*>(Hs + ct.soff) + lt.a;
-            const float* pc = p2 + lt.c;
-            const float2* s = Ss + lt.n * U;
-            for (int t = 0; t < pl.K; ++t) {
+            const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ct.soff) + lt.a;
+            float* qs = Qs + tile;
+            const float2* s = Ss + lt.n * s_stride;
+            if (pl.K > 0) {
+                // Sweep 1 with the preprocessing of Algorithm 2 folded in: p^2 = ||h_{u,c}||^{-2}.
 #pragma unroll 1
                 for (int u = 0; u < U; ++u) {
                     float4 h[kPairs];
                     pp_load_h<AT>(hb + u * LP, h);
-                    const float2 g = pp_correlate<AT>(h, x, lt.mask);
-                    const float q = pc[u * C];
+                    float2 g = pp_partial_corr(h, x);
+                    float e = pp_partial_energy(h);
+#pragma unroll
+                    for (int off = 1; off < AT; off <<= 1) {
+                        g.x += __shfl_xor_sync(lt.mask, g.x, off);
+                        g.y += __shfl_xor_sync(lt.mask, g.y, off);
+                        e += __shfl_xor_sync(lt.mask, e, off);
+                    }
+                    const float q = e > 0.f ? __fdividef(1.f, e) : 0.f;
+                    qs[u * xs_stride] = q;
                     const float2 su = s[u];
                     pp_update(h, make_float2(q * (g.x - su.x), q * (g.y - su.y)), x);
                 }
             }
+            for (int t = 1; t < pl.K; ++t) {
+#pragma unroll 1
+                for (int u = 0; u < U; ++u) {
+                    float4 h[kPairs];
+                    pp_load_h<AT>(hb + u * LP, h);
+                    float2 g = pp_partial_corr(h, x);
+                    g.x = tile_sum_c<AT>(g.x, lt.mask);
+                    g.y = tile_sum_c<AT>(g.y, lt.mask);
+                    const float q = qs[u * xs_stride];
+                    const float2 su = s[u];
+                    pp_update(h, make_float2(q * (g.x - su.x), q * (g.y - su.y)), x);
+                }
+            }
+            // ||x_c|| over the tile, then x_c <- rho_c x_c / ||x_c||.
             float nr = 0.f;
 #pragma unroll
             for (int i = 0; i < kPairs; ++i)
                 nr = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, fmaf(x[i].z, x[i].z, fmaf(x[i].w, x[i].w, nr))));
-#pragma unroll
-            for (int off = 1; off < AT; off <<= 1) nr += __shfl_xor_sync(lt.mask, nr, off);
+            nr = tile_sum_c<AT>(nr, lt.mask);
             const float sc = nr > 0.f ? pl.rho_c * rsqrtf(nr) : 0.f;
             float2* out = io.Xdl + ((size_t)f * n_sym + lt.n) * pl.B + ct.off;
 #pragma unroll

@@ -117,10 +117,19 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     if (pl->n_lanes > kMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
 
     const unsigned U = p->U, C = p->C;
+    const unsigned xs = (unsigned)pl->n_tiles | 1u;
+    pl->packed = (P == 16 && pl->n_lanes <= kMaxSpecializedThreads &&
+                  (pl->A_uniform == 1 || pl->A_uniform == 2 || pl->A_uniform == 4)) ? 1 : 0;
     unsigned o = align16((unsigned)pl->h_entries * 8u);
+    if (pl->packed) {
+        pl->off_H2 = o;
+        o = align16(o + (unsigned)pl->h_entries * 8u);
+        pl->off_K = o;
+        o = align16(o + U * xs * (detect ? 8u : 4u));
+    }
     if (detect) {
         pl->off_X = o;
-        o = align16(o + U * ((unsigned)pl->n_tiles | 1u) * 8u);
+        o = align16(o + U * xs * 8u);
         pl->off_coef = o;
         o = align16(o + C * U * 8u);
         pl->off_lam = o;
@@ -129,16 +138,18 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
         pl->off_coef = o;
         o = align16(o + C * U * 4u);
         pl->off_S = o;
-        o = align16(o + (unsigned)p->n_sym * U * 8u);
+        o = align16(o + (unsigned)p->n_sym * (U | 1u) * 8u);
     }
     pl->off_e = o;
     o = align16(o + C * U * 4u);
     pl->off_tab = o;
     o = align16(o + C * (unsigned)sizeof(ClusterTile));
     pl->off_bar = o;
-    o = align16(o + 8u);
+    o = align16(o + 16u);
     pl->smem_bytes = o;
     if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    if (pl->packed && !detect && p->n_sym * p->U > kSPrefetch * std::max(64, (pl->n_lanes + 31) / 32 * 32))
+        pl->packed = 0;  // the packed precoder prefetches at most kSPrefetch entries of s per thread
 
     pl->bulk = (p->in_dtype == CDMIMO_C64 && all_even && aligned(H, 16)) ? 1 : 0;
     return CDMIMO_OK;
@@ -176,6 +187,21 @@ int launch_cd(Kern k, const CdPlan& pl, cudaStream_t s)
     return CDMIMO_OK;
 }
 
+// Grid: one CTA per subcarrier for the scalar kernels; for the persistent packed kernels, as many
+// CTAs as fit on the device at once (they walk the subcarriers with a grid stride).
+template <typename Kern>
+int grid_for(Kern k, const CdPlan& pl)
+{
+    if (!pl.packed) return pl.n_sc;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return pl.n_sc;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads_for(pl), pl.smem_bytes) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return std::max(1, std::min(pl.n_sc, sms * per_sm));
+}
+
 template <int P, int IN, int AT>
 int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
@@ -183,7 +209,7 @@ int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
     if constexpr (AT > 0) k = cd_detect_pp_kernel<IN, AT>;
     else k = cd_detect_kernel<P, IN, 0>;
     if (int rc = launch_cd(k, pl, s)) return rc;
-    k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
+    k<<<grid_for(k, pl), threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
@@ -194,7 +220,7 @@ int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
     if constexpr (AT > 0) k = cd_precode_pp_kernel<IN, AT>;
     else k = cd_precode_kernel<P, IN, 0>;
     if (int rc = launch_cd(k, pl, s)) return rc;
-    k<<<pl.n_sc, threads_for(pl), pl.smem_bytes, s>>>(pl, io);
+    k<<<grid_for(k, pl), threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
@@ -203,7 +229,7 @@ int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 template <int IN>
 int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
-    if (pl.P == 16 && pl.n_lanes <= kMaxSpecializedThreads) {
+    if (pl.packed) {
         switch (pl.A_uniform) {
         case 1: return launch_detect_t<16, IN, 1>(pl, io, s);
         case 2: return launch_detect_t<16, IN, 2>(pl, io, s);
@@ -221,7 +247,7 @@ int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 template <int IN>
 int dispatch_precode(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 {
-    if (pl.P == 16 && pl.n_lanes <= kMaxSpecializedThreads) {
+    if (pl.packed) {
         switch (pl.A_uniform) {
         case 1: return launch_precode_t<16, IN, 1>(pl, io, s);
         case 2: return launch_precode_t<16, IN, 2>(pl, io, s);
