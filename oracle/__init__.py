@@ -54,7 +54,10 @@ def lib():
         L.oracle_lmmse.argtypes = [i, i, i, i, i, i, d, P, P, P, P]
         L.oracle_zf.argtypes = [i, i, i, i, i, i, P, P, P]
         L.oracle_ml.argtypes = [i, i, i, P, P, i, P, P]
-        for fn in (L.oracle_detect, L.oracle_precode, L.oracle_lmmse, L.oracle_zf, L.oracle_ml):
+        L.oracle_learned_forward.argtypes = [i, i, i, i, i, P, i, d, i, P, P, P, P, P, P, P, i, i]
+        L.oracle_learned_grad.argtypes = [i, i, i, i, i, P, i, d, i, P, P, P, P, P, P, P, i, i]
+        for fn in (L.oracle_detect, L.oracle_precode, L.oracle_lmmse, L.oracle_zf, L.oracle_ml,
+                   L.oracle_learned_forward, L.oracle_learned_grad):
             fn.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -160,3 +163,49 @@ def ml(H, Y, points):
     if rc != 0:
         raise RuntimeError(f"oracle_ml failed with status {rc}")
     return lab
+
+
+def learned_param_count(K, U, hidden):
+    """Length of the master parameter vector [tau(K), graw(K), W1(hidden*(U+1)), b1, w2, b2]."""
+    return 2 * K + hidden * (U + 1) + 2 * hidden + 1
+
+
+def learned_forward(H, Y, N0, cluster_size, K, master, hidden, Ex=1.0, threads=1):
+    """Deep-unfolded CD with learned fusion.  Returns (Xhat, Xc, lam)."""
+    H = _c128(H)
+    Y = _c128(Y)
+    N0 = np.ascontiguousarray(N0, dtype=np.float64)
+    master = np.ascontiguousarray(master, dtype=np.float64)
+    n_sc, U, B = H.shape
+    n_sym = Y.shape[1]
+    assert master.size == learned_param_count(K, U, hidden)
+    cs = np.ascontiguousarray(cluster_size, dtype=np.int32)
+    C = cs.size
+    Xhat = np.zeros((n_sc, n_sym, U), np.complex128)
+    Xc = np.zeros((n_sc, C, n_sym, U), np.complex128)
+    lam = np.zeros((n_sc, C), np.float64)
+    L = lib()
+    _run("oracle_learned_forward", n_sc, threads, lambda f0, f1: L.oracle_learned_forward(
+        n_sc, n_sym, B, U, C, _ptr(cs), int(K), float(Ex), int(hidden), _ptr(master), _ptr(H), _ptr(Y), _ptr(N0),
+        _ptr(Xhat), _ptr(Xc), _ptr(lam), f0, f1))
+    return Xhat, Xc, lam
+
+
+def learned_grad(H, Y, N0, cluster_size, K, master, hidden, Xtarget, Ex=1.0):
+    """Loss mean ||xhat - xtarget||^2 over vectors and its gradient w.r.t. the master parameters."""
+    H = _c128(H)
+    Y = _c128(Y)
+    Xt = _c128(Xtarget)
+    N0 = np.ascontiguousarray(N0, dtype=np.float64)
+    master = np.ascontiguousarray(master, dtype=np.float64)
+    n_sc, U, B = H.shape
+    n_sym = Y.shape[1]
+    cs = np.ascontiguousarray(cluster_size, dtype=np.int32)
+    grad = np.zeros(master.size, np.float64)
+    loss = np.zeros(1, np.float64)
+    rc = lib().oracle_learned_grad(n_sc, n_sym, B, U, cs.size, _ptr(cs), int(K), float(Ex), int(hidden),
+                                   _ptr(master), _ptr(H), _ptr(Y), _ptr(N0), _ptr(Xt), _ptr(loss), _ptr(grad), 0,
+                                   n_sc)
+    if rc != 0:
+        raise RuntimeError(f"oracle_learned_grad failed with status {rc}")
+    return float(loss[0]), grad

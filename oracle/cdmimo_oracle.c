@@ -367,3 +367,281 @@ out:
     free(idx); free(best); free(e);
     return rc;
 }
+
+/* ============================================================================================== */
+/* Deep-unfolded CD with learned fusion (not in the paper: a learned extension of Algorithm 1).     */
+/* ============================================================================================== */
+/*
+ * Parameters ("masters"): per sweep t, a step tau_t and a raw regularizer parameter gr_t with
+ * gamma_t = softplus(gr_t) = log(1 + exp(gr_t)) > 0; a two-layer perceptron with hidden width Hd on
+ * F = U + 1 per-cluster features phi_c = [||h_{1,c}||^2 / B_c, ..., ||h_{U,c}||^2 / B_c,
+ * log10(max(N0/Ex, 1e-6))]: z = W1 phi + b1 (W1 row-major [Hd][F]), a = max(z, 0),
+ * logit_c = w2 . a + b2, lambda = softmax_c(logit).
+ *
+ * Sweep t, user u (Gauss-Seidel order as in Algorithm 1), with e = ||h_{u,c}||^2, alpha = N0/Ex:
+ *     x_u <- x_u + tau_t (h_u^H r - gamma_t alpha x_u) / (e + gamma_t alpha),   r <- r - h_u dx,
+ * i.e. x_new = a1 g + a2 x_old with a1 = tau_t / (e + gamma_t alpha), a2 = 1 - tau_t gamma_t alpha /
+ * (e + gamma_t alpha); tau_t = gamma_t = 1 is exactly Algorithm 1's update (a1 = m, a2 = n).  A
+ * column with e + gamma_t alpha <= 0 is skipped (a1 = 0, a2 = 1).
+ *
+ * Loss: L = (1 / (n_sc n_sym)) sum_{f,n} ||xhat_{f,n} - xtarget_{f,n}||^2.
+ */
+
+static double softplus(double v) { return v > 30.0 ? v : log1p(exp(v)); }
+static double sigmoid(double v) { return 1.0 / (1.0 + exp(-v)); }
+
+typedef struct {
+    int K, U, Hd, F;
+    const double *tau, *graw, *W1, *b1, *w2;
+    double b2;
+} orc_learned;
+
+/* Coefficients (a1, a2) of sweep t for a column of energy e. */
+static void learned_coef(const orc_learned *P, int t, double e, double alpha, double *a1, double *a2, double *den_out)
+{
+    const double gam = softplus(P->graw[t]);
+    const double den = e + gam * alpha;
+    *den_out = den;
+    if (den > 0.0) {
+        *a1 = P->tau[t] / den;
+        *a2 = 1.0 - P->tau[t] * gam * alpha / den;
+    } else {
+        *a1 = 0.0;
+        *a2 = 1.0;
+    }
+}
+
+/* MLP forward for one cluster's features: hidden pre-activations z[Hd] and the logit. */
+static double mlp_forward(const orc_learned *P, const double *phi, double *z)
+{
+    double logit = P->b2;
+    for (int k = 0; k < P->Hd; ++k) {
+        double s = P->b1[k];
+        for (int j = 0; j < P->F; ++j) s += P->W1[(size_t)k * P->F + j] * phi[j];
+        z[k] = s;
+        logit += P->w2[k] * (s > 0.0 ? s : 0.0);
+    }
+    return logit;
+}
+
+/*
+ * Forward and (if grad != NULL) reverse pass for subcarriers f0 <= f < f1.
+ * grad layout (masters): [tau(K), graw(K), W1(Hd*F), b1(Hd), w2(Hd), b2]; accumulated (+=).
+ * loss accumulated (+=) if non-NULL.  Xhat, Xc, lam outputs optional.
+ */
+static int learned_pass(int n_sc, int n_sym, int B, int U, int C, const int *csize, double Ex, const orc_learned *P,
+                        const cplx *H, const cplx *Y, const double *N0, const cplx *Xt, cplx *Xhat, cplx *Xc,
+                        double *lam_out, double *loss, double *grad, int f0, int f1)
+{
+    const int K = P->K, Hd = P->Hd, F = P->F;
+    const double inv_nvec = 1.0 / ((double)n_sc * n_sym);
+    int Bmax = 0;
+    for (int c = 0; c < C; ++c) Bmax = csize[c] > Bmax ? csize[c] : Bmax;
+    cplx *r = malloc(sizeof(cplx) * Bmax);
+    cplx *rb = malloc(sizeof(cplx) * Bmax);
+    cplx *x = malloc(sizeof(cplx) * U);
+    cplx *xb = malloc(sizeof(cplx) * U);
+    cplx *xc = malloc(sizeof(cplx) * (size_t)C * n_sym * U);
+    cplx *gsave = malloc(sizeof(cplx) * (size_t)K * U);   /* forward g per step (one tile) */
+    cplx *xsave = malloc(sizeof(cplx) * (size_t)K * U);   /* forward x_old per step */
+    double *e = malloc(sizeof(double) * (size_t)C * U);
+    double *phi = malloc(sizeof(double) * (size_t)C * F);
+    double *z = malloc(sizeof(double) * (size_t)C * Hd);
+    double *logit = malloc(sizeof(double) * C);
+    double *lam = malloc(sizeof(double) * C);
+    double *lamb = malloc(sizeof(double) * C);
+    double *a1b = malloc(sizeof(double) * (size_t)K * C * U); /* adjoints of a1, a2 per (t, c, u) */
+    double *a2b = malloc(sizeof(double) * (size_t)K * C * U);
+    cplx *gb = malloc(sizeof(cplx) * (size_t)n_sym * U);      /* dL/dxhat for this subcarrier */
+    int rc = ORC_OK;
+    if (!r || !rb || !x || !xb || !xc || !gsave || !xsave || !e || !phi || !z || !logit || !lam || !lamb || !a1b ||
+        !a2b || !gb) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    for (int f = f0; f < f1; ++f) {
+        const cplx *Hf = H + (size_t)f * U * B;
+        const double alpha = N0[f] / Ex;
+        /* features and fusion weights */
+        int o = 0;
+        for (int c = 0; c < C; ++c) {
+            for (int u = 0; u < U; ++u) {
+                double s = 0.0;
+                for (int b = 0; b < csize[c]; ++b) s += abs2(Hf[(size_t)u * B + o + b]);
+                e[c * U + u] = s;
+                phi[c * F + u] = s / csize[c];
+            }
+            phi[c * F + U] = log10(alpha > 1e-6 ? alpha : 1e-6);
+            logit[c] = mlp_forward(P, phi + c * F, z + (size_t)c * Hd);
+            o += csize[c];
+        }
+        double mx = logit[0];
+        for (int c = 1; c < C; ++c) mx = logit[c] > mx ? logit[c] : mx;
+        double zs = 0.0;
+        for (int c = 0; c < C; ++c) zs += exp(logit[c] - mx);
+        for (int c = 0; c < C; ++c) {
+            lam[c] = exp(logit[c] - mx) / zs;
+            if (lam_out) lam_out[(size_t)f * C + c] = lam[c];
+        }
+        /* unfolded CD per cluster and symbol (forward) */
+        o = 0;
+        for (int c = 0; c < C; ++c) {
+            const int Bc = csize[c];
+            for (int n = 0; n < n_sym; ++n) {
+                const cplx *y = Y + ((size_t)f * n_sym + n) * B + o;
+                for (int b = 0; b < Bc; ++b) r[b] = y[b];
+                for (int u = 0; u < U; ++u) x[u] = 0.0;
+                for (int t = 0; t < K; ++t)
+                    for (int u = 0; u < U; ++u) {
+                        const cplx *h = Hf + (size_t)u * B + o;
+                        double a1, a2, den;
+                        learned_coef(P, t, e[c * U + u], alpha, &a1, &a2, &den);
+                        cplx g = 0.0;
+                        for (int b = 0; b < Bc; ++b) g += conj(h[b]) * r[b];
+                        const cplx xn = a1 * g + a2 * x[u];
+                        const cplx dx = xn - x[u];
+                        x[u] = xn;
+                        for (int b = 0; b < Bc; ++b) r[b] -= h[b] * dx;
+                    }
+                for (int u = 0; u < U; ++u) xc[((size_t)c * n_sym + n) * U + u] = x[u];
+            }
+            o += Bc;
+        }
+        for (int n = 0; n < n_sym; ++n)
+            for (int u = 0; u < U; ++u) {
+                cplx acc = 0.0;
+                for (int c = 0; c < C; ++c) acc += lam[c] * xc[((size_t)c * n_sym + n) * U + u];
+                if (Xhat) Xhat[((size_t)f * n_sym + n) * U + u] = acc;
+                if (Xt) {
+                    const cplx d = acc - Xt[((size_t)f * n_sym + n) * U + u];
+                    if (loss) *loss += abs2(d) * inv_nvec;
+                    gb[(size_t)n * U + u] = 2.0 * inv_nvec * d;
+                }
+            }
+        if (Xc) memcpy(Xc + (size_t)f * C * n_sym * U, xc, sizeof(cplx) * (size_t)C * n_sym * U);
+        if (!grad || !Xt) continue;
+
+        /* ---- reverse pass ---- */
+        double *g_tau = grad, *g_gr = grad + K, *g_W1 = grad + 2 * K, *g_b1 = g_W1 + (size_t)Hd * F;
+        double *g_w2 = g_b1 + Hd, *g_b2 = g_w2 + Hd;
+        /* fusion: xhat = sum_c lam_c x_c */
+        double dot = 0.0;
+        for (int c = 0; c < C; ++c) {
+            double s = 0.0;
+            for (int i = 0; i < n_sym * U; ++i) s += creal(conj(gb[i]) * xc[(size_t)c * n_sym * U + i]);
+            lamb[c] = s;
+            dot += lam[c] * s;
+        }
+        for (int c = 0; c < C; ++c) {
+            const double lb = lam[c] * (lamb[c] - dot); /* softmax adjoint -> d logit_c */
+            const double *zc = z + (size_t)c * Hd;
+            *g_b2 += lb;
+            for (int k = 0; k < Hd; ++k) {
+                const double act = zc[k] > 0.0 ? zc[k] : 0.0;
+                g_w2[k] += lb * act;
+                const double zb = zc[k] > 0.0 ? lb * P->w2[k] : 0.0;
+                g_b1[k] += zb;
+                for (int j = 0; j < F; ++j) g_W1[(size_t)k * F + j] += zb * phi[c * F + j];
+            }
+        }
+        /* unfolded CD: recompute each tile's forward steps, then walk them backwards */
+        for (size_t i = 0; i < (size_t)K * C * U; ++i) a1b[i] = a2b[i] = 0.0;
+        o = 0;
+        for (int c = 0; c < C; ++c) {
+            const int Bc = csize[c];
+            for (int n = 0; n < n_sym; ++n) {
+                const cplx *y = Y + ((size_t)f * n_sym + n) * B + o;
+                for (int b = 0; b < Bc; ++b) r[b] = y[b];
+                for (int u = 0; u < U; ++u) x[u] = 0.0;
+                for (int t = 0; t < K; ++t)
+                    for (int u = 0; u < U; ++u) {
+                        const cplx *h = Hf + (size_t)u * B + o;
+                        double a1, a2, den;
+                        learned_coef(P, t, e[c * U + u], alpha, &a1, &a2, &den);
+                        cplx g = 0.0;
+                        for (int b = 0; b < Bc; ++b) g += conj(h[b]) * r[b];
+                        gsave[(size_t)t * U + u] = g;
+                        xsave[(size_t)t * U + u] = x[u];
+                        const cplx xn = a1 * g + a2 * x[u];
+                        const cplx dx = xn - x[u];
+                        x[u] = xn;
+                        for (int b = 0; b < Bc; ++b) r[b] -= h[b] * dx;
+                    }
+                for (int u = 0; u < U; ++u) xb[u] = lam[c] * gb[(size_t)n * U + u];
+                for (int b = 0; b < Bc; ++b) rb[b] = 0.0;
+                for (int t = K - 1; t >= 0; --t)
+                    for (int u = U - 1; u >= 0; --u) {
+                        const cplx *h = Hf + (size_t)u * B + o;
+                        double a1, a2, den;
+                        learned_coef(P, t, e[c * U + u], alpha, &a1, &a2, &den);
+                        cplx hr = 0.0;
+                        for (int b = 0; b < Bc; ++b) hr += conj(h[b]) * rb[b];
+                        const cplx db = xb[u] - hr; /* adjoint of dx */
+                        a1b[((size_t)t * C + c) * U + u] += creal(conj(db) * gsave[(size_t)t * U + u]);
+                        a2b[((size_t)t * C + c) * U + u] += creal(conj(db) * xsave[(size_t)t * U + u]);
+                        const cplx gbar = a1 * db;
+                        for (int b = 0; b < Bc; ++b) rb[b] += h[b] * gbar;
+                        xb[u] += (a2 - 1.0) * db;
+                    }
+            }
+            o += Bc;
+        }
+        /* chain (a1, a2) -> (tau_t, gamma_t) -> raw parameter */
+        for (int t = 0; t < K; ++t) {
+            const double gam = softplus(P->graw[t]);
+            double gt = 0.0, gg = 0.0;
+            for (int c = 0; c < C; ++c)
+                for (int u = 0; u < U; ++u) {
+                    const double ev = e[c * U + u], den = ev + gam * alpha;
+                    if (!(den > 0.0)) continue;
+                    const double A1 = a1b[((size_t)t * C + c) * U + u], A2 = a2b[((size_t)t * C + c) * U + u];
+                    gt += A1 / den - A2 * gam * alpha / den;
+                    gg += -A1 * P->tau[t] * alpha / (den * den) - A2 * P->tau[t] * alpha * ev / (den * den);
+                }
+            g_tau[t] += gt;
+            g_gr[t] += gg * sigmoid(P->graw[t]);
+        }
+    }
+out:
+    free(r); free(rb); free(x); free(xb); free(xc); free(gsave); free(xsave); free(e); free(phi); free(z);
+    free(logit); free(lam); free(lamb); free(a1b); free(a2b); free(gb);
+    return rc;
+}
+
+/* Public wrappers.  master: [tau(K), graw(K), W1(Hd*F), b1(Hd), w2(Hd), b2] with F = U + 1. */
+static int learned_setup(orc_learned *P, int K, int U, int Hd, const double *master)
+{
+    if (K < 0 || U < 1 || Hd < 1 || !master) return ORC_EINVAL;
+    P->K = K;
+    P->U = U;
+    P->Hd = Hd;
+    P->F = U + 1;
+    P->tau = master;
+    P->graw = master + K;
+    P->W1 = master + 2 * K;
+    P->b1 = P->W1 + (size_t)Hd * P->F;
+    P->w2 = P->b1 + Hd;
+    P->b2 = P->w2[Hd];
+    return ORC_OK;
+}
+
+int oracle_learned_forward(int n_sc, int n_sym, int B, int U, int C, const int *csize, int K, double Ex, int Hd,
+                           const double *master, const cplx *H, const cplx *Y, const double *N0, cplx *Xhat, cplx *Xc,
+                           double *lam, int f0, int f1)
+{
+    orc_learned P;
+    if (check_dims(n_sc, n_sym, B, U, C, csize, f0, f1) != ORC_OK || !(Ex > 0)) return ORC_EINVAL;
+    if (learned_setup(&P, K, U, Hd, master) != ORC_OK || !H || !Y || !N0) return ORC_EINVAL;
+    return learned_pass(n_sc, n_sym, B, U, C, csize, Ex, &P, H, Y, N0, NULL, Xhat, Xc, lam, NULL, NULL, f0, f1);
+}
+
+/* Loss and gradient (accumulated into grad[] and *loss, which the caller zeroes). */
+int oracle_learned_grad(int n_sc, int n_sym, int B, int U, int C, const int *csize, int K, double Ex, int Hd,
+                        const double *master, const cplx *H, const cplx *Y, const double *N0, const cplx *Xt,
+                        double *loss, double *grad, int f0, int f1)
+{
+    orc_learned P;
+    if (check_dims(n_sc, n_sym, B, U, C, csize, f0, f1) != ORC_OK || !(Ex > 0)) return ORC_EINVAL;
+    if (learned_setup(&P, K, U, Hd, master) != ORC_OK || !H || !Y || !N0 || !Xt || !loss || !grad) return ORC_EINVAL;
+    return learned_pass(n_sc, n_sym, B, U, C, csize, Ex, &P, H, Y, N0, Xt, NULL, NULL, NULL, loss, grad, f0, f1);
+}

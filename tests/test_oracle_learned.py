@@ -1,0 +1,116 @@
+"""Pins of the oracle's deep-unfolded CD with learned fusion (CPU only).
+
+  * The learned sweep is over-relaxed Gauss-Seidel (SOR, relaxation tau_t) on the normal equations
+    with regularizer gamma_t N0/Ex; checked against the SOR matrix splitting solved with a library
+    triangular solve.
+  * tau = gamma = 1 with a constant fusion logit reduces exactly to Algorithm 1 with equal fusion.
+  * The analytic reverse pass matches central finite differences of the forward loss.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_1902_08653_gb300 import workload as wl
+
+GRAW_ONE = np.log(np.e - 1.0)  # softplus(GRAW_ONE) = 1
+
+
+def crandn(g, *shape):
+    return (g.standard_normal(shape) + 1j * g.standard_normal(shape)) / np.sqrt(2)
+
+
+def make_master(g, K, U, Hd, tau=None, gamma_raw=None, scale=0.5, w2_zero=False):
+    F = U + 1
+    tau = g.uniform(0.6, 1.6, K) if tau is None else np.full(K, tau, float)
+    graw = g.uniform(-1.0, 1.5, K) if gamma_raw is None else np.full(K, gamma_raw, float)
+    W1 = g.standard_normal((Hd, F)) * scale
+    b1 = g.standard_normal(Hd) * scale
+    w2 = np.zeros(Hd) if w2_zero else g.standard_normal(Hd) * scale
+    b2 = np.array([g.standard_normal() * scale])
+    return np.concatenate([tau, graw, W1.ravel(), b1, w2, b2])
+
+
+def sor_reference(Hc, y, alpha, taus, gammas):
+    z = np.conj(Hc) @ y
+    x = np.zeros(Hc.shape[0], complex)
+    for tau, gam in zip(taus, gammas):
+        A = np.conj(Hc) @ Hc.T + gam * alpha * np.eye(Hc.shape[0])
+        D = np.diag(np.diag(A))
+        Lo = np.tril(A, -1)
+        Up = np.triu(A, 1)
+        x = sla.solve_triangular(D + tau * Lo, tau * z - (tau * Up + (tau - 1) * D) @ x, lower=True)
+    return x
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_learned_sweeps_are_sor(oracle, seed):
+    g = np.random.default_rng(300 + seed)
+    U, K, Hd = int(g.integers(1, 6)), int(g.integers(1, 4)), 4
+    cs = [int(v) for v in g.integers(max(1, U - 1), 10, size=3)]
+    H = crandn(g, 2, U, sum(cs))
+    Y = crandn(g, 2, 2, sum(cs))
+    N0 = g.uniform(0.1, 1.5, 2)
+    master = make_master(g, K, U, Hd)
+    _, Xc, lam = oracle.learned_forward(H, Y, N0, cs, K, master, Hd)
+    taus = master[:K]
+    gammas = np.log1p(np.exp(master[K:2 * K]))
+    o = np.concatenate([[0], np.cumsum(cs)])
+    for f in range(2):
+        for c in range(3):
+            for n in range(2):
+                ref = sor_reference(H[f, :, o[c]:o[c + 1]], Y[f, n, o[c]:o[c + 1]], N0[f], taus, gammas)
+                np.testing.assert_allclose(Xc[f, c, n], ref, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(lam.sum(axis=1), 1.0, atol=1e-14)
+    assert np.all(lam > 0)
+
+
+def test_reduces_to_plain_cd_with_equal_fusion(oracle):
+    g = np.random.default_rng(7)
+    d = wl.uplink(3, 5, 3, 64, 8, snr_db=wl.sweep_snr(5))
+    cs = [16] * 4
+    master = make_master(g, 3, 8, 16, tau=1.0, gamma_raw=GRAW_ONE, w2_zero=True)
+    Xl, Xcl, lam = oracle.learned_forward(d["H"], d["Y"], d["N0"], cs, 3, master, 16)
+    Xp, Xcp, _ = oracle.detect(d["H"], d["Y"], d["N0"], cs, 3, fuse="equal")
+    np.testing.assert_allclose(lam, 0.25, rtol=1e-14)
+    np.testing.assert_allclose(Xcl, Xcp, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(Xl, Xp, rtol=1e-12, atol=1e-14)
+
+
+def test_loss_matches_forward(oracle):
+    g = np.random.default_rng(11)
+    d = wl.uplink(4, 3, 2, 24, 4, snr_db=10.0)
+    cs = [8, 8, 8]
+    master = make_master(g, 2, 4, 6)
+    Xt = crandn(g, 3, 2, 4)
+    Xl, _, _ = oracle.learned_forward(d["H"], d["Y"], d["N0"], cs, 2, master, 6)
+    loss, _ = oracle.learned_grad(d["H"], d["Y"], d["N0"], cs, 2, master, 6, Xt)
+    np.testing.assert_allclose(loss, np.mean(np.sum(np.abs(Xl - Xt) ** 2, axis=-1)), rtol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gradient_matches_central_differences(oracle, seed):
+    g = np.random.default_rng(500 + seed)
+    U, K, Hd = 3, 2, 5
+    cs = [4, 6]
+    H = crandn(g, 2, U, 10)
+    Y = crandn(g, 2, 2, 10)
+    N0 = np.array([0.3, 0.8])
+    master = make_master(g, K, U, Hd)
+    Xt = crandn(g, 2, 2, U)
+    loss, grad = oracle.learned_grad(H, Y, N0, cs, K, master, Hd, Xt)
+    num = np.zeros_like(master)
+    eps = 1e-6
+    for i in range(master.size):
+        mp = master.copy()
+        mp[i] += eps
+        mm = master.copy()
+        mm[i] -= eps
+        num[i] = (oracle.learned_grad(H, Y, N0, cs, K, mp, Hd, Xt)[0] -
+                  oracle.learned_grad(H, Y, N0, cs, K, mm, Hd, Xt)[0]) / (2 * eps)
+    scale = np.max(np.abs(num))
+    assert scale > 0
+    np.testing.assert_allclose(grad, num, rtol=1e-5, atol=1e-7 * scale)
+    # every parameter group receives gradient
+    F = U + 1
+    groups = np.split(grad, np.cumsum([K, K, Hd * F, Hd, Hd]))
+    assert all(np.any(np.abs(gr) > 0) for gr in groups)
