@@ -48,6 +48,7 @@ typedef enum {
 /* Bits of the device-side status word (cdmimo_device_status). */
 #define CDMIMO_DEV_TIMEOUT 0x1   /* a bounded wait on an async copy or work queue expired */
 #define CDMIMO_DEV_BAD_N0 0x2    /* some N0[f] was negative or NaN: that subcarrier's output is NaN */
+#define CDMIMO_DEV_BAD_LEARNED 0x4 /* the learned block does not match p->K or p->U: output is NaN */
 
 #define CDMIMO_MAX_CLUSTERS 64
 #define CDMIMO_MAX_USERS 64
@@ -77,8 +78,11 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *                 CDMIMO_C16BF with per-subcarrier float32 scales: the true values are
  *                 H[f] = h_scale[f] * stored and Y[f] = y_scale[f] * stored.  All arithmetic is FP32.
  *   h_scale, y_scale  DEVICE arrays [n_sc] (16-bit dtypes only, else ignored; may be NULL).
- *   learned       DEVICE pointer to a cdmimo_learned block (fuse == LEARNED, or nonzero
- *                 learned sweeps), else NULL: plain CD.
+ *   learned       DEVICE pointer to a cdmimo_learned block, else NULL (plain CD).  With a block,
+ *                 the sweeps are the learned ones (p->K must equal the block's K; a mismatch sets
+ *                 CDMIMO_DEV_BAD_LEARNED and gives NaN output) and fuse may be any rule;
+ *                 fuse == CDMIMO_FUSE_LEARNED requires a block.  Learned detection needs equal
+ *                 cluster sizes of at most 64 antennas and 64-bit complex storage.
  */
 typedef struct {
     int n_sc, n_sym, B, U, C;
@@ -153,6 +157,72 @@ int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y
                        void* Xhat_host, void* dev_ws, size_t ws_bytes, void* stream);
 int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* S_host, void* Xdl_host,
                         void* dev_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Learned deep-unfolded CD (an extension beyond the paper; plain CD is the default).              */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * Sweep t (t = 0..K-1) of the learned detector replaces Algorithm 1's coordinate update by
+ *     x_u <- x_u + tau_t (h_{u,c}^H r - gamma_t alpha x_u) / (||h_{u,c}||^2 + gamma_t alpha),
+ * alpha = N0/Ex (over-relaxed Gauss-Seidel with a scaled regularizer; tau_t = gamma_t = 1 is exactly
+ * Algorithm 1).  With fuse == CDMIMO_FUSE_LEARNED the fusion weights are lambda = softmax_c(logit_c),
+ * logit_c = w2 . relu(W1 phi_c + b1) + b2, on the F = U + 1 cluster features
+ * phi_c = [||h_{1,c}||^2 / B_c, ..., ||h_{U,c}||^2 / B_c, log10(max(alpha, 1e-6))].
+ *
+ * Trainable ("master") parameters, one float32 vector of cdmimo_learned_param_count(K, U, hidden):
+ *     [tau (K), graw (K), W1 (hidden x F, row-major), b1 (hidden), w2 (hidden), b2 (1)]
+ * with gamma_t = softplus(graw_t).  The detection kernels read the packed inference block below,
+ * which cdmimo_learned_pack() writes from the masters (W1 and w2 rounded to bfloat16; all arithmetic
+ * FP32).
+ */
+#define CDMIMO_MAX_LEARNED_SWEEPS 16
+#define CDMIMO_MAX_HIDDEN 64
+
+typedef struct {
+    int K;                    /* sweeps the parameters were trained for (p->K must match) */
+    int U;                    /* users (F = U + 1 features) */
+    int hidden;               /* hidden width, 1..CDMIMO_MAX_HIDDEN */
+    int reserved0;
+    float tau[CDMIMO_MAX_LEARNED_SWEEPS];
+    float gamma[CDMIMO_MAX_LEARNED_SWEEPS];  /* softplus(graw), > 0 */
+    float b1[CDMIMO_MAX_HIDDEN];
+    float b2;
+    float reserved1[3];
+    unsigned short W1[CDMIMO_MAX_HIDDEN * (CDMIMO_MAX_USERS + 1)]; /* bfloat16 bits, row k: F entries */
+    unsigned short w2[CDMIMO_MAX_HIDDEN];                          /* bfloat16 bits */
+} cdmimo_learned;
+
+/* Number of master parameters for (K, U, hidden), or 0 if out of range. */
+size_t cdmimo_learned_param_count(int K, int U, int hidden);
+
+/*
+ * Write the inference block from the masters.  master DEVICE float [param_count];
+ * block DEVICE cdmimo_learned.  K in 1..CDMIMO_MAX_LEARNED_SWEEPS, U in 1..CDMIMO_MAX_USERS.
+ */
+int cdmimo_learned_pack(const float* master, int K, int U, int hidden, void* block, void* stream);
+
+/*
+ * Loss L = (1/(n_sc n_sym)) sum ||xhat - xtarget||^2 of the learned detector (p->learned = block
+ * packed from the masters, hidden = its hidden width, learned fusion, p->in_dtype = CDMIMO_C64, any
+ * cluster partition) and its gradient with respect to the master parameters, by a reverse pass
+ * through the K unfolded sweeps, the softmax and the perceptron (p->fuse is ignored).  Xtarget DEVICE c64 [n_sc][n_sym][U]; grad DEVICE float
+ * [param_count] (overwritten); loss DEVICE float [1] (overwritten).  workspace DEVICE scratch of
+ * cdmimo_learned_workspace_size(p) bytes (per-subcarrier partial sums, reduced in a fixed order, so
+ * the result is deterministic).
+ */
+int cdmimo_learned_grad(const cdmimo_params* p, int hidden, const void* H, const void* Y, const float* N0,
+                        const void* Xtarget, float* grad, float* loss, void* workspace, size_t ws_bytes,
+                        void* stream);
+size_t cdmimo_learned_workspace_size(const cdmimo_params* p, int hidden);
+
+/*
+ * One Adam step (Kingma and Ba, 2015) on n float32 parameters, in place:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   theta -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps),   step >= 1.
+ * All pointers DEVICE float [n].
+ */
+int cdmimo_adam_step(float* theta, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
+                     float eps, int step, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- */
 /* Queries.                                                                                        */

@@ -28,6 +28,8 @@ ERR_WORKSPACE = -6
 
 DEV_TIMEOUT = 0x1
 DEV_BAD_N0 = 0x2
+DEV_BAD_LEARNED = 0x4
+LEARNED_BLOCK_BYTES = 4 * 4 + 16 * 4 * 2 + 64 * 4 + 4 * 4 + 64 * 65 * 2 + 64 * 2
 
 C64, C16F, C16BF = 0, 1, 2
 FUSE = {"equal": 0, "colnorm": 1, "learned": 2}
@@ -73,6 +75,11 @@ def lib():
             "cdmimo_status_string": ([I], ctypes.c_char_p),
             "cdmimo_device_status": ([I], I),
             "cdmimo_version": ([], I),
+            "cdmimo_learned_param_count": ([I, I, I], S),
+            "cdmimo_learned_pack": ([P, I, I, I, P, P], I),
+            "cdmimo_learned_grad": ([PP, I, P, P, P, P, P, P, P, S, P], I),
+            "cdmimo_learned_workspace_size": ([PP, I], S),
+            "cdmimo_adam_step": ([P, P, P, P, I, F, F, F, F, I, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -236,3 +243,60 @@ def precode_host(H, S, cluster_size, K, Xdl, dev_ws, *, rho=1.0, stream=None):
                                    dev_ws.numel() * dev_ws.element_size(), _stream(stream))
     _check("cdmimo_precode_host", rc)
     return Xdl
+
+
+# ------------------------------------------------------------------------------------------------
+# learned deep-unfolded CD
+# ------------------------------------------------------------------------------------------------
+def learned_param_count(K, U, hidden):
+    return int(lib().cdmimo_learned_param_count(int(K), int(U), int(hidden)))
+
+
+def learned_pack(master, K, U, hidden, block, stream=None):
+    """cdmimo_learned_pack: masters (device float32) -> inference block (device, LEARNED_BLOCK_BYTES)."""
+    _need(master, "master")
+    _need(block, "block")
+    if master.dtype != torch.float32 or master.numel() != learned_param_count(K, U, hidden):
+        raise ValueError("master must be float32 of cdmimo_learned_param_count(K, U, hidden) entries")
+    if block.numel() * block.element_size() < LEARNED_BLOCK_BYTES:
+        raise ValueError("block too small")
+    _check("cdmimo_learned_pack", lib().cdmimo_learned_pack(_ptr(master), int(K), int(U), int(hidden), _ptr(block),
+                                                            _stream(stream)))
+    return block
+
+
+def learned_workspace_size(n_sc, n_sym, B, U, cluster_size, K, hidden):
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K)
+    return int(lib().cdmimo_learned_workspace_size(ctypes.byref(p), int(hidden)))
+
+
+def learned_grad(H, Y, N0, Xtarget, cluster_size, K, block, hidden, *, grad=None, loss=None, workspace=None,
+                 Ex=1.0, stream=None):
+    """cdmimo_learned_grad: loss and gradient w.r.t. the master parameters.  Returns (loss[1], grad)."""
+    for t, nm in ((H, "H"), (Y, "Y"), (N0, "N0"), (Xtarget, "Xtarget"), (block, "block")):
+        _need(t, nm)
+    n_sc, U, B = H.shape
+    n_sym = Y.shape[1]
+    n = learned_param_count(K, U, hidden)
+    if grad is None:
+        grad = torch.empty(n, dtype=torch.float32, device=H.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=H.device)
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse="learned", learned=block)
+    need = int(lib().cdmimo_learned_workspace_size(ctypes.byref(p), int(hidden)))
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=H.device)
+    rc = lib().cdmimo_learned_grad(ctypes.byref(p), int(hidden), _ptr(H), _ptr(Y), _ptr(N0), _ptr(Xtarget),
+                                   _ptr(grad), _ptr(loss), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("cdmimo_learned_grad", rc)
+    return loss, grad
+
+
+def adam_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """cdmimo_adam_step on float32 device tensors (in place)."""
+    for t, nm in ((theta, "theta"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, nm)
+    _check("cdmimo_adam_step", lib().cdmimo_adam_step(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(),
+                                                      float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                                      _stream(stream)))

@@ -31,6 +31,7 @@ __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x,
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float bf16_bits_to_float(unsigned short v) { return __uint_as_float((unsigned)v << 16); }
 
 // (re0, im0, re1, im1) -> (re0, re1, im0, im1) for every 16-byte pair of one channel buffer.
 __device__ __forceinline__ void permute_pairs_in_place(const CdPlan& pl, float2* Hs)
@@ -195,22 +196,32 @@ __device__ __forceinline__ float row_energy(const float2* row, int L)
 // ---------------------------------------------------------------------------------------------
 // Uplink: Algorithm 1 + fusion (Sec. III).
 // ---------------------------------------------------------------------------------------------
-template <int IN, int AT>
+template <int IN, int AT, bool LEARNED>
 __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const DetectIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     // Channel buffer j (0 or 1) starts at byte j * off_H2.
     auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + (j ? pl.off_H2 : 0u)); };
     float2* Xs = reinterpret_cast<float2*>(smem + pl.off_X);  // [U][x_stride] current x per tile
-    float2* Ks = reinterpret_cast<float2*>(smem + pl.off_K);  // [U][x_stride] (m, n) per tile
+    // [U][x_stride] per tile: (m, n) of Algorithm 1; learned sweeps keep (||h_{u,c}||^2, m) instead
+    float2* Ks = reinterpret_cast<float2*>(smem + pl.off_K);
     float* lam = reinterpret_cast<float*>(smem + pl.off_lam); // [C]
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);  // [2]
+
+    float* mlp = reinterpret_cast<float*>(smem + pl.off_mlp);   // [C][hidden <= 64] (learned fusion)
+    const cdmimo_learned* blk = reinterpret_cast<const cdmimo_learned*>(io.learned);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
     const uint32_t xs_stride = x_stride(pl);
     constexpr int LP = AT * kPairs;  // shared-memory row length in pairs
+    bool learned_ok = true;
+    if (LEARNED) {
+        const int hd = __ldg(&blk->hidden);
+        learned_ok = __ldg(&blk->K) == pl.K && __ldg(&blk->U) == U && hd >= 1 && hd <= CDMIMO_MAX_HIDDEN;
+        if (!learned_ok && tid == 0 && blockIdx.x == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_LEARNED);
+    }
 
     if (tid < C) tab[tid] = pl.cl[tid];
     if (tid == 0 && pl.bulk) {
@@ -256,11 +267,48 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             out_scale = __int_as_float(0x7fc00000);
             alpha = 0.f;
         }
+        if (LEARNED && !learned_ok) out_scale = __int_as_float(0x7fc00000);
         if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), &bar[b], (uint32_t)(k >> 1) & 1u,
                                  fn + (int)gridDim.x < pl.n_sc))
             return;
 
-        if (lt.active && pl.K > 0) {
+        if (LEARNED && lt.active && pl.K > 0) {
+            // Learned sweeps: x_u <- a1 h^H r + a2 x_u with a1 = tau_t / (e + gamma_t alpha),
+            // a2 = 1 - a1 gamma_t alpha (a skipped column when the denominator is not positive).
+            const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ct.soff) + lt.a;
+            float2* xs = Xs + tile;
+            float2* ks = Ks + tile;
+            for (int t = 0; t < pl.K; ++t) {
+                const float tau = __ldg(&blk->tau[t]), gam = __ldg(&blk->gamma[t]);
+                const float ga = gam * alpha;
+#pragma unroll 1
+                for (int u = 0; u < U; ++u) {
+                    float4 h[kPairs];
+                    pp_load_h<AT>(hb + u * LP, h);
+                    float2 g = pp_partial_corr(h, r);
+                    float e;
+                    if (t == 0) {
+                        e = pp_partial_energy(h);
+#pragma unroll
+                        for (int off = 1; off < AT; off <<= 1) e += __shfl_xor_sync(lt.mask, e, off);
+                        const float den0 = e + alpha;
+                        ks[u * xs_stride] = make_float2(e, den0 > 0.f ? __fdividef(1.f, den0) : 0.f);
+                    } else {
+                        e = ks[u * xs_stride].x;
+                    }
+                    g.x = tile_sum_c<AT>(g.x, lt.mask);
+                    g.y = tile_sum_c<AT>(g.y, lt.mask);
+                    const float den = e + ga;
+                    const float a1 = den > 0.f ? tau * __fdividef(1.f, den) : 0.f;
+                    const float a2 = 1.f - a1 * ga;
+                    const float2 xo = t == 0 ? make_float2(0.f, 0.f) : xs[u * xs_stride];
+                    const float2 xn = make_float2(fmaf(a1, g.x, a2 * xo.x), fmaf(a1, g.y, a2 * xo.y));
+                    xs[u * xs_stride] = xn;
+                    pp_update(h, make_float2(xn.x - xo.x, xn.y - xo.y), r);
+                }
+            }
+        }
+        if (!LEARNED && lt.active && pl.K > 0) {
             const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ct.soff) + lt.a;
             float2* xs = Xs + tile;
             float2* ks = Ks + tile;
@@ -305,8 +353,9 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             for (int i = tid; i < U * (int)xs_stride; i += blockDim.x) Xs[i] = make_float2(0.f, 0.f);
             if (lt.active && lt.a == 0) {
                 for (int u = 0; u < U; ++u) {
-                    const float den = row_energy(Hbuf(b) + ct.soff + u * ct.L, ct.L) + alpha;
-                    Ks[u * xs_stride + tile] = make_float2(den > 0.f ? __fdividef(1.f, den) : 0.f, 0.f);
+                    const float e = row_energy(Hbuf(b) + ct.soff + u * ct.L, ct.L);
+                    const float m = e + alpha > 0.f ? __fdividef(1.f, e + alpha) : 0.f;
+                    Ks[u * xs_stride + tile] = LEARNED ? make_float2(e, m) : make_float2(m, 0.f);
                 }
             }
         }
@@ -315,9 +364,52 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             load_lane_pairs<IN, AT>(io.Y, ((size_t)fn * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
         __syncthreads();
 
-        // Fusion weights: lambda_c proportional to 1 / sum_u m_{u,c} (a zero m marks a skipped column,
-        // whose (||h||^2 + N0/Ex)^{-1} is infinite).
-        if (warp == 0) {
+        if (LEARNED && pl.fuse == CDMIMO_FUSE_LEARNED) {
+            // Learned fusion: hidden unit kk of cluster c, z = W1[kk] . phi_c + b1[kk], contributes
+            // w2[kk] relu(z) to logit_c; phi_c = [||h_{u,c}||^2 / B_c (u < U), log10(max(alpha, 1e-6))].
+            const int Hd = learned_ok ? __ldg(&blk->hidden) : 1;
+            const int F = U + 1;
+            const float la = log10f(fmaxf(alpha, 1e-6f));
+            for (int i = tid; i < C * Hd; i += blockDim.x) {
+                const int c = i / Hd, kk = i - c * Hd;
+                const float inv_bc = 1.f / (float)tab[c].size;
+                const unsigned short* w1 = blk->W1 + (size_t)kk * F;
+                float z = __ldg(&blk->b1[kk]);
+                for (int j = 0; j < U; ++j) z = fmaf(bf16_bits_to_float(__ldg(w1 + j)), Ks[j * xs_stride + c * n_sym].x * inv_bc, z);
+                z = fmaf(bf16_bits_to_float(__ldg(w1 + U)), la, z);
+                mlp[i] = bf16_bits_to_float(__ldg(&blk->w2[kk])) * fmaxf(z, 0.f);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                float lg[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < C) {
+                        float s = __ldg(&blk->b2);
+                        for (int kk = 0; kk < Hd; ++kk) s += mlp[c * Hd + kk];
+                        lg[q] = s;
+                    }
+                }
+                float mx = fmaxf(lg[0], lg[1]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                float ex[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) ex[q] = lane + 32 * q < C ? __expf(lg[q] - mx) : 0.f;
+                const float tot = warp_sum(ex[0] + ex[1]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < C) {
+                        lam[c] = ex[q] / tot;
+                        if (io.lam) io.lam[(size_t)f * C + c] = ex[q] / tot;
+                    }
+                }
+            }
+        } else if (warp == 0) {
+            // Fusion weights: lambda_c proportional to 1 / sum_u m_{u,c} (a zero m marks a skipped
+            // column, whose (||h||^2 + N0/Ex)^{-1} is infinite).
             float w[2] = {0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -325,7 +417,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
                 if (c < C) {
                     float s = 0.f;
                     for (int u = 0; u < U; ++u) {
-                        const float m = Ks[u * xs_stride + c * n_sym].x;
+                        const float m = LEARNED ? Ks[u * xs_stride + c * n_sym].y : Ks[u * xs_stride + c * n_sym].x;
                         s += m > 0.f ? m : __int_as_float(0x7f800000);
                     }
                     w[q] = 1.f / s;

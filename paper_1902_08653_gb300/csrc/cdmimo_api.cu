@@ -10,6 +10,7 @@
 
 #include "cd_kernels.cuh"
 #include "cd_kernels_pp.cuh"
+#include "learned_kernels.cuh"
 #include "cdmimo.h"
 #include "plan.h"
 
@@ -73,6 +74,7 @@ int validate(const cdmimo_params* p)
 // kMaxThreads threads or more shared memory than the device grants.
 int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan* pl)
 {
+    const bool learned = detect && p->learned != nullptr;
     std::memset(pl, 0, sizeof(*pl));
     pl->n_sc = p->n_sc;
     pl->n_sym = p->n_sym;
@@ -142,6 +144,11 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     }
     pl->off_e = o;
     o = align16(o + C * U * 4u);
+    pl->learned = learned ? 1 : 0;
+    if (learned) {
+        pl->off_mlp = o;
+        o = align16(o + C * (unsigned)CDMIMO_MAX_HIDDEN * 4u);
+    }
     pl->off_tab = o;
     o = align16(o + C * (unsigned)sizeof(ClusterTile));
     pl->off_bar = o;
@@ -206,8 +213,12 @@ template <int P, int IN, int AT>
 int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
     void (*k)(const CdPlan, const DetectIO);
-    if constexpr (AT > 0) k = cd_detect_pp_kernel<IN, AT>;
-    else k = cd_detect_kernel<P, IN, 0>;
+    if constexpr (AT > 0) {
+        if constexpr (IN == CDMIMO_C64) k = pl.learned ? cd_detect_pp_kernel<IN, AT, true> : cd_detect_pp_kernel<IN, AT, false>;
+        else k = cd_detect_pp_kernel<IN, AT, false>;
+    } else {
+        k = cd_detect_kernel<P, IN, 0>;
+    }
     if (int rc = launch_cd(k, pl, s)) return rc;
     k<<<grid_for(k, pl), threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
@@ -278,10 +289,14 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
     if (int rc = validate(p)) return rc;
     if (int rc = check_detect_ptrs(p, H, Y, N0, Xhat)) return rc;
     if ((Xc && !aligned(Xc, 8)) || (lam && !aligned(lam, 4))) return CDMIMO_ERR_INVALID_ARG;
-    if (p->fuse == CDMIMO_FUSE_LEARNED) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->fuse == CDMIMO_FUSE_LEARNED && !p->learned) return CDMIMO_ERR_INVALID_ARG;
+    if (p->learned && (p->in_dtype != CDMIMO_C64 || p->K < 1 || p->K > CDMIMO_MAX_LEARNED_SWEEPS ||
+                       !aligned(p->learned, 16)))
+        return p->in_dtype != CDMIMO_C64 ? CDMIMO_ERR_UNSUPPORTED : CDMIMO_ERR_INVALID_ARG;
     if (p->n_sc == 0) return CDMIMO_OK;
     CdPlan pl;
     if (int rc = plan_auto(p, true, H, &pl)) return rc;
+    if (pl.learned && !pl.packed) return CDMIMO_ERR_UNSUPPORTED;  // learned sweeps: uniform B_c <= 64
     DetectIO io{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), reinterpret_cast<float2*>(Xc),
                 lam, p->learned};
     switch (p->in_dtype) {
@@ -311,6 +326,60 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
 }
 
 size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+namespace {
+
+// Plan and shared-memory layout of the learned gradient kernel (generic tiling, converting staging).
+int grad_plan(const cdmimo_params* p, int hidden, CdPlan* pl, GradLayout* gl)
+{
+    if (int rc = validate(p)) return rc;
+    if (p->in_dtype != CDMIMO_C64 || !cdmimo_learned_param_count(p->K, p->U, hidden)) return CDMIMO_ERR_INVALID_ARG;
+    cdmimo_params q = *p;
+    q.learned = nullptr;
+    if (int rc = plan_auto(&q, true, nullptr, pl)) return rc;
+    pl->bulk = 0;
+    pl->packed = 0;
+    const unsigned U = p->U, C = p->C, K = p->K, T = (unsigned)pl->n_tiles, xs = T | 1u;
+    gl->K = p->K;
+    gl->Hd = hidden;
+    gl->F = p->U + 1;
+    gl->n_params = (int)cdmimo_learned_param_count(p->K, p->U, hidden);
+    gl->ws_stride = (gl->n_params + 1 + 3) & ~3;
+    gl->inv_nvec = 1.f / ((float)p->n_sc * (float)p->n_sym);
+    unsigned o = align16((unsigned)pl->h_entries * 8u);
+    gl->off_e = o;      o = align16(o + U * C * 4u);
+    gl->off_cf = o;     o = align16(o + K * U * C * 8u);
+    gl->off_save = o;   o = align16(o + K * U * T * 16u);
+    gl->off_X = o;      o = align16(o + U * xs * 8u);
+    gl->off_Xb = o;     o = align16(o + U * xs * 8u);
+    gl->off_Ab = o;     o = align16(o + K * U * T * 8u);
+    gl->off_phi = o;    o = align16(o + C * (U + 1) * 4u);
+    gl->off_z = o;      o = align16(o + C * (unsigned)hidden * 4u);
+    gl->off_zb = o;     o = align16(o + C * (unsigned)hidden * 4u);
+    gl->off_lam = o;    o = align16(o + C * 4u);
+    gl->off_lamb = o;   o = align16(o + C * 4u);
+    gl->off_lgb = o;    o = align16(o + C * 4u);
+    gl->off_gx = o;     o = align16(o + (unsigned)p->n_sym * U * 8u);
+    gl->off_tg = o;     o = align16(o + K * C * 8u);
+    gl->off_red = o;    o = align16(o + 32u * 4u);
+    gl->off_tab = o;    o = align16(o + C * (unsigned)sizeof(ClusterTile));
+    gl->smem_bytes = o;
+    if ((int)o > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    return CDMIMO_OK;
+}
+
+template <int P>
+int launch_grad_t(const CdPlan& pl, const GradLayout& gl, const GradIO& io, cudaStream_t s)
+{
+    auto k = learned_grad_kernel<P>;
+    if (gl.smem_bytes > 48u * 1024u &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gl.smem_bytes) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    k<<<pl.n_sc, threads_for(pl), gl.smem_bytes, s>>>(pl, gl, io);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
 
 }  // namespace
 
@@ -423,6 +492,73 @@ int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* 
     if (int rc = precode_impl(p, dH, dS, dX, s)) return rc;
     if (cudaMemcpyAsync(Xdl_host, dX, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     return CDMIMO_OK;
+}
+
+size_t cdmimo_learned_param_count(int K, int U, int hidden)
+{
+    if (K < 1 || K > CDMIMO_MAX_LEARNED_SWEEPS || U < 1 || U > CDMIMO_MAX_USERS || hidden < 1 ||
+        hidden > CDMIMO_MAX_HIDDEN)
+        return 0;
+    return (size_t)2 * K + (size_t)hidden * (U + 1) + 2 * (size_t)hidden + 1;
+}
+
+int cdmimo_learned_pack(const float* master, int K, int U, int hidden, void* block, void* stream)
+{
+    if (!cdmimo_learned_param_count(K, U, hidden)) return CDMIMO_ERR_INVALID_ARG;
+    if (!master || !block || !aligned(master, 4) || !aligned(block, 16)) return CDMIMO_ERR_INVALID_ARG;
+    learned_pack_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(master, K, U, hidden,
+                                                                           static_cast<cdmimo_learned*>(block));
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+size_t cdmimo_learned_workspace_size(const cdmimo_params* p, int hidden)
+{
+    CdPlan pl;
+    GradLayout gl;
+    if (!p || grad_plan(p, hidden, &pl, &gl) != CDMIMO_OK) return 0;
+    return (size_t)p->n_sc * gl.ws_stride * sizeof(float);
+}
+
+int cdmimo_learned_grad(const cdmimo_params* p, int hidden, const void* H, const void* Y, const float* N0,
+                        const void* Xtarget, float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream)
+{
+    CdPlan pl;
+    GradLayout gl;
+    if (int rc = grad_plan(p, hidden, &pl, &gl)) return rc;
+    if (!p->learned || !aligned(p->learned, 16) || !grad || !loss) return CDMIMO_ERR_INVALID_ARG;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H || !Y || !N0 || !Xtarget || !aligned(H, 8) || !aligned(Y, 8) || !aligned(Xtarget, 8))
+        return CDMIMO_ERR_INVALID_ARG;
+    if (!workspace || !aligned(workspace, 16) || ws_bytes < (size_t)p->n_sc * gl.ws_stride * sizeof(float))
+        return CDMIMO_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GradIO io{static_cast<const float2*>(H), static_cast<const float2*>(Y), N0, static_cast<const float2*>(Xtarget),
+              static_cast<const cdmimo_learned*>(p->learned), static_cast<float*>(workspace)};
+    int rc = CDMIMO_ERR_UNSUPPORTED;
+    switch (pl.P) {
+    case 8: rc = launch_grad_t<8>(pl, gl, io, s); break;
+    case 16: rc = launch_grad_t<16>(pl, gl, io, s); break;
+    case 32: rc = launch_grad_t<32>(pl, gl, io, s); break;
+    }
+    if (rc) return rc;
+    const int threads = 256, blocks = (gl.n_params + 1 + threads - 1) / threads;
+    learned_reduce_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(workspace), p->n_sc, gl.ws_stride,
+                                                     gl.n_params, grad, loss);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+int cdmimo_adam_step(float* theta, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
+                     float eps, int step, void* stream)
+{
+    if (n < 0 || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return CDMIMO_ERR_INVALID_ARG;
+    if (n == 0) return CDMIMO_OK;
+    if (!theta || !grad || !m || !v) return CDMIMO_ERR_INVALID_ARG;
+    const float c1 = (float)(1.0 - std::pow((double)beta1, step)), c2 = (float)(1.0 - std::pow((double)beta2, step));
+    const int threads = 256, blocks = std::min((n + threads - 1) / threads, 1024);
+    adam_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(theta, grad, m, v, n, lr, beta1, beta2, eps,
+                                                                          c1, c2);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
 const char* cdmimo_status_string(int status)

@@ -36,11 +36,13 @@ struct CdPlan {
     int padded;       // 1: some B_c < A_c P (zero columns must be written once)
     int packed;       // 1: the packed persistent kernels (uniform A in {1, 2, 4}, P = 16) run this plan
     int fuse;         // cdmimo_fuse_rule
+    int learned;      // 1: learned sweeps (and possibly learned fusion) from a cdmimo_learned block
     float inv_Ex;
     float rho_c;      // downlink per-cluster norm rho / sqrt(C)
     // byte offsets of the shared-memory regions (channel blocks start at 0; the packed kernels keep
     // a second channel buffer at off_H2 and per-tile coefficients at off_K)
-    unsigned off_H2, off_X, off_K, off_coef, off_e, off_lam, off_S, off_tab, off_bar, smem_bytes;
+    // off_mlp: [C][CDMIMO_MAX_HIDDEN] floats of learned-fusion partial sums (learned plans only)
+    unsigned off_H2, off_X, off_K, off_coef, off_e, off_lam, off_S, off_mlp, off_tab, off_bar, smem_bytes;
     ClusterTile cl[CDMIMO_MAX_CLUSTERS];
 };
 

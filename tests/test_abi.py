@@ -101,3 +101,20 @@ def test_host_workspace_sizes():
     assert L.cdmimo_workspace_size(ctypes.byref(p), cdmimo.OP_DETECT) == 0
     assert L.cdmimo_detect_host(ctypes.byref(p), ctypes.c_void_p(1), ctypes.c_void_p(1), ctypes.c_void_p(1),
                                 ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None) == cdmimo.ERR_WORKSPACE
+
+
+def test_learned_block_layout_and_param_count():
+    class Block(ctypes.Structure):
+        _fields_ = [("K", ctypes.c_int), ("U", ctypes.c_int), ("hidden", ctypes.c_int), ("r0", ctypes.c_int),
+                    ("tau", ctypes.c_float * 16), ("gamma", ctypes.c_float * 16), ("b1", ctypes.c_float * 64),
+                    ("b2", ctypes.c_float), ("r1", ctypes.c_float * 3), ("W1", ctypes.c_uint16 * (64 * 65)),
+                    ("w2", ctypes.c_uint16 * 64)]
+
+    assert ctypes.sizeof(Block) == cdmimo.LEARNED_BLOCK_BYTES
+    assert cdmimo.learned_param_count(2, 16, 64) == 2 * 2 + 64 * 17 + 2 * 64 + 1
+    assert cdmimo.learned_param_count(0, 16, 64) == 0
+    assert cdmimo.learned_param_count(17, 16, 64) == 0
+    assert cdmimo.learned_param_count(2, 16, 65) == 0
+    L = cdmimo.lib()
+    assert L.cdmimo_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == cdmimo.ERR_INVALID_ARG
+    assert L.cdmimo_learned_pack(None, 2, 16, 64, None, None) == cdmimo.ERR_INVALID_ARG
