@@ -216,6 +216,28 @@ int cdmimo_learned_grad(const cdmimo_params* p, int hidden, const void* H, const
 size_t cdmimo_learned_workspace_size(const cdmimo_params* p, int hidden);
 
 /*
+ * Allocation-free variant of cdmimo_learned_grad (the paper has no counterpart: this is a library
+ * convenience).  Same inputs, outputs and result, but no workspace argument: the per-subcarrier
+ * partial sums live in a fixed array of CDMIMO_NOALLOC_SCRATCH_BYTES bytes that the library keeps
+ * in device memory on every GPU that loads it, until the process exits.  It is for callers that
+ * cannot call cudaMalloc or any allocator at the point where they train, for example a real-time
+ * baseband pipeline that forbids allocation once it is running, or C code that only receives
+ * device pointers from another runtime and has no allocator of its own.
+ *   - Limit: n_sc * (cdmimo_learned_param_count(p->K, p->U, hidden) + 1, rounded up to a multiple
+ *     of 4) * 4 bytes must not exceed CDMIMO_NOALLOC_SCRATCH_BYTES; larger batches return
+ *     CDMIMO_ERR_WORKSPACE (use cdmimo_learned_grad with a workspace, or split the batch).
+ *   - The first call on a device looks up the array's device address with that device current;
+ *     make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents (nothing in it has to
+ *     start at zero).  Calls that overlap on the GPU (other streams, other host threads) race on
+ *     it: serialize them.
+ *   - It allocates nothing and frees nothing.
+ */
+#define CDMIMO_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int cdmimo_learned_grad_noalloc(const cdmimo_params* p, int hidden, const void* H, const void* Y, const float* N0,
+                                const void* Xtarget, float* grad, float* loss, void* stream);
+
+/*
  * One Adam step (Kingma and Ba, 2015) on n float32 parameters, in place:
  *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
  *   theta -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps),   step >= 1.

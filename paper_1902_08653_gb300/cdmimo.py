@@ -80,6 +80,7 @@ def lib():
             "cdmimo_learned_grad": ([PP, I, P, P, P, P, P, P, P, S, P], I),
             "cdmimo_learned_workspace_size": ([PP, I], S),
             "cdmimo_adam_step": ([P, P, P, P, I, F, F, F, F, I, P], I),
+            "cdmimo_learned_grad_noalloc": ([PP, I, P, P, P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -290,6 +291,21 @@ def learned_grad(H, Y, N0, Xtarget, cluster_size, K, block, hidden, *, grad=None
                                    _ptr(grad), _ptr(loss), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), _stream(stream))
     _check("cdmimo_learned_grad", rc)
+    return loss, grad
+
+
+def learned_grad_noalloc(H, Y, N0, Xtarget, cluster_size, K, block, hidden, *, grad, loss, Ex=1.0, stream=None):
+    """cdmimo_learned_grad_noalloc: like learned_grad, with the library's fixed scratch instead of a
+    caller workspace (for callers that cannot allocate device memory); grad and loss must be given."""
+    for t, nm in ((H, "H"), (Y, "Y"), (N0, "N0"), (Xtarget, "Xtarget"), (block, "block"), (grad, "grad"),
+                  (loss, "loss")):
+        _need(t, nm)
+    n_sc, U, B = H.shape
+    n_sym = Y.shape[1]
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse="learned", learned=block)
+    rc = lib().cdmimo_learned_grad_noalloc(ctypes.byref(p), int(hidden), _ptr(H), _ptr(Y), _ptr(N0), _ptr(Xtarget),
+                                           _ptr(grad), _ptr(loss), _stream(stream))
+    _check("cdmimo_learned_grad_noalloc", rc)
     return loss, grad
 
 

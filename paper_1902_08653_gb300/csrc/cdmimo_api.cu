@@ -383,6 +383,29 @@ int launch_grad_t(const CdPlan& pl, const GradLayout& gl, const GradIO& io, cuda
 
 }  // namespace
 
+// Scratch of cdmimo_learned_grad_noalloc: a fixed device array owned by the library, for callers
+// that cannot allocate device memory.  Host code only ever sees its address through
+// cudaGetSymbolAddress (the symbol itself is a host-side stand-in); the address is looked up once
+// per device, with that device current, on the first call made on it.
+static __device__ __align__(256) float g_noalloc_scratch[CDMIMO_NOALLOC_SCRATCH_BYTES / sizeof(float)];
+
+namespace {
+
+float* noalloc_scratch_address()
+{
+    static float* addr[kMaxDevices] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (!addr[dev]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return nullptr;
+        addr[dev] = static_cast<float*>(ptr);
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
 extern "C" {
 
 int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc_opt,
@@ -545,6 +568,22 @@ int cdmimo_learned_grad(const cdmimo_params* p, int hidden, const void* H, const
     learned_reduce_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(workspace), p->n_sc, gl.ws_stride,
                                                      gl.n_params, grad, loss);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+int cdmimo_learned_grad_noalloc(const cdmimo_params* p, int hidden, const void* H, const void* Y, const float* N0,
+                                const void* Xtarget, float* grad, float* loss, void* stream)
+{
+    CdPlan pl;
+    GradLayout gl;
+    if (int rc = grad_plan(p, hidden, &pl, &gl)) return rc;
+    const size_t need = (size_t)p->n_sc * gl.ws_stride * sizeof(float);
+    if (need > CDMIMO_NOALLOC_SCRATCH_BYTES) return CDMIMO_ERR_WORKSPACE;
+    if (p->n_sc == 0) return cdmimo_learned_grad(p, hidden, H, Y, N0, Xtarget, grad, loss, nullptr, 0, stream);
+    float* ws = noalloc_scratch_address();
+    if (!ws) return CDMIMO_ERR_CUDA;
+    // Every partial-sum entry the reduction reads is written by the gradient kernel first, so the
+    // scratch needs no clearing between calls.
+    return cdmimo_learned_grad(p, hidden, H, Y, N0, Xtarget, grad, loss, ws, CDMIMO_NOALLOC_SCRATCH_BYTES, stream);
 }
 
 int cdmimo_adam_step(float* theta, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
