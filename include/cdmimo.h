@@ -115,6 +115,9 @@ typedef struct {
  * workspace, ws_bytes  DEVICE scratch of at least cdmimo_workspace_size(p, CDMIMO_OP_DETECT) bytes
  *          (currently 0 for every supported shape; NULL is accepted when 0 is needed).
  * stream   cudaStream_t (NULL = legacy default stream).
+ * Shapes whose per-subcarrier channel does not fit in shared memory (or needs more than 512 lanes
+ * per CTA) run by streaming cluster groups through shared memory (one CTA per subcarrier); that
+ * path takes c64 storage, EQUAL or COLNORM fusion and no Xc_opt / lambda_opt, else UNSUPPORTED.
  */
 int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
                   void* Xc_opt, float* lambda_opt, void* workspace, size_t ws_bytes, void* stream);
@@ -127,6 +130,7 @@ int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const fl
  *   x_c <- rho_c x_c / ||x_c|| (x_c = 0 stays 0).  Output Xdl = [x_1; ...; x_C].
  * H        DEVICE, dtype p->in_dtype (16-bit storage needs no scale: the normalization removes it).
  * S        DEVICE c64 [n_sc][n_sym][U], 8-byte aligned.   Xdl DEVICE c64 [n_sc][n_sym][B].
+ * Shapes beyond shared memory stream cluster groups as cdmimo_detect does (c64 storage only).
  */
 int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* Xdl, void* workspace,
                    size_t ws_bytes, void* stream);
@@ -157,6 +161,65 @@ int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y
                        void* Xhat_host, void* dev_ws, size_t ws_bytes, void* stream);
 int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* S_host, void* Xdl_host,
                         void* dev_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Batched uneven launch (an extension beyond the paper).                                          */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * A batch is a list of descriptors, each a resource block (or any set of subcarriers) with its own
+ * B, U, cluster partition, K and operation; all of it runs in ONE persistent launch whose CTAs pop
+ * (descriptor, subcarrier) work items from a device counter.  Per item the clusters are processed in
+ * groups that fit the plan's shared-memory budget; detection fuses across groups exactly as
+ * cdmimo_detect does (EQUAL or COLNORM), precoding normalizes each cluster (Sec. IV-B).
+ * Usage: fill the descriptors, call cdmimo_batch_build (host only) to get the table bytes, copy the
+ * table to device memory, then call cdmimo_detect_batched as often as wanted; it only enqueues a
+ * 4-byte counter reset and the kernel, so the call can be recorded in a CUDA graph.
+ */
+typedef struct {
+    int op;                   /* CDMIMO_OP_DETECT or CDMIMO_OP_PRECODE */
+    int n_sc, n_sym, B, U, C, K;
+    int fuse;                 /* detection: CDMIMO_FUSE_EQUAL or CDMIMO_FUSE_COLNORM */
+    float Ex;                 /* detection: per-user energy (> 0) */
+    float rho;                /* precoding: total power constraint, rho_c = rho / sqrt(C) */
+    const int* cluster_size;  /* HOST [C], read by cdmimo_batch_build only */
+    const void* H;            /* DEVICE c64 [n_sc][U][B] */
+    const void* V;            /* DEVICE c64: detection Y [n_sc][n_sym][B]; precoding S [n_sc][n_sym][U] */
+    const float* N0;          /* DEVICE float [n_sc] (detection) */
+    void* out;                /* DEVICE c64: detection Xhat [n_sc][n_sym][U]; precoding Xdl [n_sc][n_sym][B] */
+} cdmimo_batch_desc;
+
+typedef struct {
+    /* tile parameters (inputs; cdmimo_batch_default_plan gives defaults, an autotuner may change them) */
+    int P;            /* antennas per lane: 8, 16 or 32 */
+    int threads;      /* threads per CTA: multiple of 32 in [64, 512]; every cluster group's tiles fit */
+    int group_bytes;  /* shared-memory budget of one cluster group (channel rows + per-tile state) */
+    int ctas_per_sm;  /* persistent CTAs per SM, 0 = as many as fit */
+    /* filled by cdmimo_batch_build */
+    int n_items, n_groups, C_max;
+    unsigned smem_bytes;
+    unsigned offsets[9];
+    size_t table_bytes;
+} cdmimo_batch_plan;
+
+/* Default tile parameters: P = 16, 256 threads, 64 KiB groups, all CTAs that fit. */
+void cdmimo_batch_default_plan(cdmimo_batch_plan* plan);
+
+/*
+ * Host only: validate the descriptors, split every descriptor's clusters into groups, and write the
+ * device table (which embeds the descriptors' device pointers) into table_host if it is non-NULL and
+ * at least plan->table_bytes long (call once with NULL to learn the size).  Errors: INVALID_ARG,
+ * BAD_PARTITION, UNSUPPORTED (a single cluster does not fit the budget or the threads, or more than
+ * 32 lanes per tile), WORKSPACE (table_host too small).
+ */
+int cdmimo_batch_build(const cdmimo_batch_desc* desc, int n_desc, cdmimo_batch_plan* plan, void* table_host,
+                       size_t table_bytes);
+
+/*
+ * Run the batch: table_dev DEVICE copy of the built table (16-byte aligned), counter DEVICE int
+ * scratch (reset by this call), stream as elsewhere.  Returns UNSUPPORTED if the plan's shared
+ * memory exceeds the device limit.
+ */
+int cdmimo_detect_batched(const cdmimo_batch_plan* plan, const void* table_dev, int* counter, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- */
 /* Learned deep-unfolded CD (an extension beyond the paper; plain CD is the default).              */

@@ -49,6 +49,20 @@ class Params(ctypes.Structure):
                 ("h_scale", ctypes.c_void_p), ("y_scale", ctypes.c_void_p), ("learned", ctypes.c_void_p)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("n_sc", ctypes.c_int), ("n_sym", ctypes.c_int), ("B", ctypes.c_int),
+                ("U", ctypes.c_int), ("C", ctypes.c_int), ("K", ctypes.c_int), ("fuse", ctypes.c_int),
+                ("Ex", ctypes.c_float), ("rho", ctypes.c_float), ("cluster_size", ctypes.POINTER(ctypes.c_int)),
+                ("H", ctypes.c_void_p), ("V", ctypes.c_void_p), ("N0", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("threads", ctypes.c_int), ("group_bytes", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("n_items", ctypes.c_int), ("n_groups", ctypes.c_int),
+                ("C_max", ctypes.c_int), ("smem_bytes", ctypes.c_uint), ("offsets", ctypes.c_uint * 9),
+                ("table_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 
 
@@ -81,6 +95,9 @@ def lib():
             "cdmimo_learned_workspace_size": ([PP, I], S),
             "cdmimo_adam_step": ([P, P, P, P, I, F, F, F, F, I, P], I),
             "cdmimo_learned_grad_noalloc": ([PP, I, P, P, P, P, P, P, P], I),
+            "cdmimo_batch_default_plan": ([ctypes.POINTER(BatchPlan)], None),
+            "cdmimo_batch_build": ([ctypes.POINTER(BatchDesc), I, ctypes.POINTER(BatchPlan), P, S], I),
+            "cdmimo_detect_batched": ([ctypes.POINTER(BatchPlan), P, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

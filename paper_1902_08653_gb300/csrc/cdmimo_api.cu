@@ -6,11 +6,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
+#include <vector>
 
 #include "cd_kernels.cuh"
 #include "cd_kernels_pp.cuh"
 #include "learned_kernels.cuh"
+#include "batched_kernel.cuh"
 #include "cdmimo.h"
 #include "plan.h"
 
@@ -283,6 +286,10 @@ int check_detect_ptrs(const cdmimo_params* p, const void* H, const void* Y, cons
     return CDMIMO_OK;
 }
 
+// Cluster-group streaming for shapes the whole-channel kernels cannot hold (defined further down).
+int streaming_launch(const cdmimo_params* p, int op, const void* H, const void* V, const float* N0, void* out,
+                     cudaStream_t s);
+
 int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc,
                 float* lam, cudaStream_t s)
 {
@@ -295,7 +302,10 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
         return p->in_dtype != CDMIMO_C64 ? CDMIMO_ERR_UNSUPPORTED : CDMIMO_ERR_INVALID_ARG;
     if (p->n_sc == 0) return CDMIMO_OK;
     CdPlan pl;
-    if (int rc = plan_auto(p, true, H, &pl)) return rc;
+    if (int rc = plan_auto(p, true, H, &pl)) {
+        if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam) return rc;
+        return streaming_launch(p, CDMIMO_OP_DETECT, H, Y, N0, Xhat, s);
+    }
     if (pl.learned && !pl.packed) return CDMIMO_ERR_UNSUPPORTED;  // learned sweeps: uniform B_c <= 64
     DetectIO io{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), reinterpret_cast<float2*>(Xc),
                 lam, p->learned};
@@ -315,7 +325,10 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
     const size_t ea = p->in_dtype == CDMIMO_C64 ? 8 : 4;
     if (!aligned(H, ea) || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
-    if (int rc = plan_auto(p, false, H, &pl)) return rc;
+    if (int rc = plan_auto(p, false, H, &pl)) {
+        if (rc != CDMIMO_ERR_UNSUPPORTED) return rc;
+        return streaming_launch(p, CDMIMO_OP_PRECODE, H, S, nullptr, Xdl, s);
+    }
     PrecodeIO io{H, reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
     switch (p->in_dtype) {
     case CDMIMO_C64: return dispatch_precode<CDMIMO_C64>(pl, io, s);
@@ -402,6 +415,270 @@ float* noalloc_scratch_address()
         addr[dev] = static_cast<float*>(ptr);
     }
     return addr[dev];
+}
+
+}  // namespace
+
+namespace {
+
+// Host-side split of a batch into cluster groups, and the kernel's shared-memory layout.
+struct BatchBuild {
+    std::vector<BatchDesc> descs;
+    std::vector<BatchGroup> groups;
+    std::vector<BatchCluster> clusters;
+    BatchLaunch bl{};
+};
+
+int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan, BatchBuild* bb)
+{
+    if (!d || n_desc < 1 || !plan) return CDMIMO_ERR_INVALID_ARG;
+    const int P = plan->P, T = plan->threads;
+    if ((P != 8 && P != 16 && P != 32) || T < 64 || T > 512 || (T & 31) || plan->group_bytes < 4096 ||
+        plan->ctas_per_sm < 0)
+        return CDMIMO_ERR_INVALID_ARG;
+    unsigned h_max = 0, x_max = 0, uc_max = 0, acc_max = 0, s_max = 0;
+    int C_max = 1, items = 0;
+    for (int i = 0; i < n_desc; ++i) {
+        const cdmimo_batch_desc& q = d[i];
+        if (q.op != CDMIMO_OP_DETECT && q.op != CDMIMO_OP_PRECODE) return CDMIMO_ERR_INVALID_ARG;
+        if (q.n_sc < 0 || q.n_sym < 1 || q.B < 1 || q.U < 1 || q.C < 1 || q.K < 0) return CDMIMO_ERR_INVALID_ARG;
+        if (q.U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
+        if (!q.cluster_size || q.C > CDMIMO_MAX_CLUSTERS) return CDMIMO_ERR_BAD_PARTITION;
+        if (q.op == CDMIMO_OP_DETECT && (!(q.Ex > 0.f) || (q.fuse != CDMIMO_FUSE_EQUAL && q.fuse != CDMIMO_FUSE_COLNORM)))
+            return CDMIMO_ERR_INVALID_ARG;
+        if (q.n_sc > 0 && (!q.H || !q.V || !q.out || (q.op == CDMIMO_OP_DETECT && !q.N0)))
+            return CDMIMO_ERR_INVALID_ARG;
+        if (!aligned(q.H, 8) || !aligned(q.V, 8) || !aligned(q.out, 8)) return CDMIMO_ERR_INVALID_ARG;
+        long sum = 0;
+        bool all_even = (q.B % 2) == 0;
+        for (int c = 0; c < q.C; ++c) {
+            if (q.cluster_size[c] < 1) return CDMIMO_ERR_BAD_PARTITION;
+            sum += q.cluster_size[c];
+            if (q.cluster_size[c] & 1) all_even = false;
+        }
+        if (sum != q.B) return CDMIMO_ERR_BAD_PARTITION;
+        BatchDesc bd{};
+        bd.H = q.H;
+        bd.V = q.V;
+        bd.N0 = q.N0;
+        bd.out = q.out;
+        bd.op = q.op;
+        bd.n_sc = q.n_sc;
+        bd.n_sym = q.n_sym;
+        bd.B = q.B;
+        bd.U = q.U;
+        bd.C = q.C;
+        bd.K = q.K;
+        bd.fuse = q.fuse;
+        bd.inv_Ex = q.op == CDMIMO_OP_DETECT ? 1.f / q.Ex : 0.f;
+        bd.rho_c = (float)(q.rho / std::sqrt((double)q.C));
+        bd.item0 = items;
+        bd.group0 = (int)bb->groups.size();
+        bd.bulk = (all_even && aligned(q.H, 16)) ? 1 : 0;
+        items += q.n_sc;
+        const unsigned U = q.U, ns = q.n_sym;
+        // Greedy groups of consecutive clusters.
+        int off = 0, c = 0;
+        while (c < q.C) {
+            BatchGroup g{};
+            g.c0 = c;
+            g.cl0 = (int)bb->clusters.size();
+            unsigned h = 0, lanes = 0, tiles = 0, rowb = 0;
+            std::vector<BatchCluster> cur;
+            while (c < q.C) {
+                BatchCluster bc{};
+                bc.off = off;
+                bc.size = q.cluster_size[c];
+                bc.A = pow2ceil((bc.size + P - 1) / P);
+                if (bc.A > 32) return CDMIMO_ERR_UNSUPPORTED;
+                bc.L = bc.A * P;
+                const unsigned h2 = h + U * (unsigned)bc.L + 2u * (unsigned)bc.A;
+                const unsigned t2 = tiles + ns, l2 = lanes + ns * (unsigned)bc.A, cg2 = (unsigned)cur.size() + 1;
+                const unsigned bytes = h2 * 8u + U * (t2 | 1u) * 8u + U * cg2 * 12u;
+                if (bytes > (unsigned)plan->group_bytes || l2 > (unsigned)T || cg2 > 64u) {
+                    if (cur.empty()) return CDMIMO_ERR_UNSUPPORTED;
+                    break;
+                }
+                bc.soff = (int)h;
+                h = h2;
+                tiles = t2;
+                lanes = l2;
+                rowb += U * (unsigned)bc.size * 8u;
+                if (bc.L != bc.size) g.padded = 1;
+                cur.push_back(bc);
+                off += bc.size;
+                ++c;
+            }
+            // Lanes: clusters of the group in order of decreasing A (A-aligned lane groups).
+            std::vector<int> order(cur.size());
+            for (size_t k2 = 0; k2 < cur.size(); ++k2) order[k2] = (int)k2;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cur[a].A > cur[b].A; });
+            int lane = 0;
+            for (int k2 : order) {
+                cur[k2].lane0 = lane;
+                lane += (int)ns * cur[k2].A;
+            }
+            g.c1 = c;
+            g.n_lanes = lane;
+            g.h_entries = (int)h;
+            g.row_bytes = (int)rowb;
+            for (const BatchCluster& bc : cur) bb->clusters.push_back(bc);
+            bb->groups.push_back(g);
+            const unsigned Cg = (unsigned)cur.size();
+            h_max = std::max(h_max, h);
+            x_max = std::max(x_max, U * (tiles | 1u));
+            uc_max = std::max(uc_max, U * Cg);
+            C_max = std::max(C_max, (int)Cg);
+        }
+        bd.n_groups = (int)bb->groups.size() - bd.group0;
+        if (q.op == CDMIMO_OP_DETECT) acc_max = std::max(acc_max, 2u * ns * U);
+        else s_max = std::max(s_max, ns * (U | 1u));
+        bb->descs.push_back(bd);
+    }
+    BatchLaunch& bl = bb->bl;
+    bl.P = P;
+    bl.C_max = C_max;
+    unsigned o = align16(h_max * 8u);
+    bl.off_X = o;    o = align16(o + x_max * 8u);
+    bl.off_coef = o; o = align16(o + uc_max * 8u);
+    bl.off_e = o;    o = align16(o + uc_max * 4u);
+    bl.off_acc = o;  o = align16(o + acc_max * 8u);
+    bl.off_w = o;    o = align16(o + (unsigned)(C_max + 1) * 4u);
+    bl.off_S = o;    o = align16(o + s_max * 8u);
+    bl.off_tab = o;  o = align16(o + (unsigned)C_max * (unsigned)sizeof(ClusterTile));
+    bl.off_bar = o;  o = align16(o + 8u);
+    bl.off_item = o; o = align16(o + 4u);
+    bl.smem_bytes = o;
+    plan->n_items = items;
+    plan->n_groups = (int)bb->groups.size();
+    plan->C_max = C_max;
+    plan->smem_bytes = o;
+    const unsigned offs[9] = {bl.off_X, bl.off_coef, bl.off_e, bl.off_acc, bl.off_w, bl.off_S, bl.off_tab, bl.off_bar, bl.off_item};
+    for (int i = 0; i < 9; ++i) plan->offsets[i] = offs[i];
+    const size_t hb = (sizeof(BatchTableHeader) + 15) & ~(size_t)15;
+    const size_t db = (bb->descs.size() * sizeof(BatchDesc) + 15) & ~(size_t)15;
+    const size_t gb = (bb->groups.size() * sizeof(BatchGroup) + 15) & ~(size_t)15;
+    const size_t cb = (bb->clusters.size() * sizeof(BatchCluster) + 15) & ~(size_t)15;
+    plan->table_bytes = hb + db + gb + cb;
+    return CDMIMO_OK;
+}
+
+BatchLaunch launch_from_plan(const cdmimo_batch_plan* plan)
+{
+    BatchLaunch bl{};
+    bl.P = plan->P;
+    bl.C_max = plan->C_max;
+    bl.off_X = plan->offsets[0];
+    bl.off_coef = plan->offsets[1];
+    bl.off_e = plan->offsets[2];
+    bl.off_acc = plan->offsets[3];
+    bl.off_w = plan->offsets[4];
+    bl.off_S = plan->offsets[5];
+    bl.off_tab = plan->offsets[6];
+    bl.off_bar = plan->offsets[7];
+    bl.off_item = plan->offsets[8];
+    bl.smem_bytes = plan->smem_bytes;
+    return bl;
+}
+
+template <int P>
+int launch_batched_t(const cdmimo_batch_plan* plan, const void* table, int* counter, cudaStream_t s)
+{
+    auto k = cd_batched_kernel<P>;
+    const BatchLaunch bl = launch_from_plan(plan);
+    if ((int)bl.smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    if (bl.smem_bytes > 48u * 1024u &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem_bytes) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, plan->threads, bl.smem_bytes) != cudaSuccess ||
+        per_sm < 1)
+        return CDMIMO_ERR_UNSUPPORTED;
+    if (plan->ctas_per_sm > 0) per_sm = std::min(per_sm, plan->ctas_per_sm);
+    const int grid = std::max(1, std::min(plan->n_items, sms * per_sm));
+    if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    k<<<grid, plan->threads, bl.smem_bytes, s>>>(static_cast<const unsigned char*>(table), bl, counter);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+}  // namespace
+
+namespace {
+
+// cdmimo_detect / cdmimo_precode for shapes whose whole channel does not fit in shared memory (or
+// needs more than 512 lanes): the batched kernel's cluster-group streaming, one CTA per subcarrier,
+// with the one-descriptor table passed by value.  c64 storage, EQUAL or COLNORM fusion, and no
+// per-cluster outputs.
+template <int P>
+int launch_streaming_t(const SingleTable& t, const cdmimo_batch_plan& plan, cudaStream_t s)
+{
+    auto k = cd_streaming_kernel<P>;
+    const BatchLaunch bl = launch_from_plan(&plan);
+    if ((int)bl.smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    if (bl.smem_bytes > 48u * 1024u &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem_bytes) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    k<<<plan.n_items, plan.threads, bl.smem_bytes, s>>>(t, bl);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+int streaming_launch(const cdmimo_params* p, int op, const void* H, const void* V, const float* N0, void* out,
+                     cudaStream_t s)
+{
+    if (p->in_dtype != CDMIMO_C64 || p->learned || (op == CDMIMO_OP_DETECT && p->fuse == CDMIMO_FUSE_LEARNED))
+        return CDMIMO_ERR_UNSUPPORTED;
+    cdmimo_batch_desc d{};
+    d.op = op;
+    d.n_sc = p->n_sc;
+    d.n_sym = p->n_sym;
+    d.B = p->B;
+    d.U = p->U;
+    d.C = p->C;
+    d.K = p->K;
+    d.fuse = p->fuse;
+    d.Ex = p->Ex;
+    d.rho = p->rho;
+    d.cluster_size = p->cluster_size;
+    d.H = H;
+    d.V = V;
+    d.N0 = N0;
+    d.out = out;
+    const int budget = std::min(device_smem_optin() - 16 * 1024, 160 * 1024);
+    int rc = CDMIMO_ERR_UNSUPPORTED;
+    for (int P = 16; P <= 32; P *= 2) {
+        cdmimo_batch_plan plan;
+        cdmimo_batch_default_plan(&plan);
+        plan.P = P;
+        plan.threads = 512;
+        plan.group_bytes = budget;
+        BatchBuild bb;
+        rc = batch_split(&d, 1, &plan, &bb);
+        if (rc == CDMIMO_ERR_UNSUPPORTED) continue;
+        if (rc) return rc;
+        SingleTable t{};
+        t.hdr.n_desc = 1;
+        t.hdr.n_items = plan.n_items;
+        t.hdr.n_groups = (int)bb.groups.size();
+        t.hdr.n_clusters = (int)bb.clusters.size();
+        t.hdr.off_desc = (unsigned)offsetof(SingleTable, desc);
+        t.hdr.off_group = (unsigned)offsetof(SingleTable, groups);
+        t.hdr.off_cluster = (unsigned)offsetof(SingleTable, clusters);
+        t.hdr.total_bytes = (unsigned)sizeof(SingleTable);
+        t.desc = bb.descs[0];
+        std::memcpy(t.groups, bb.groups.data(), bb.groups.size() * sizeof(BatchGroup));
+        std::memcpy(t.clusters, bb.clusters.data(), bb.clusters.size() * sizeof(BatchCluster));
+        switch (P) {
+        case 16: return launch_streaming_t<16>(t, plan, s);
+        case 32: return launch_streaming_t<32>(t, plan, s);
+        }
+    }
+    return rc;
 }
 
 }  // namespace
@@ -598,6 +875,56 @@ int cdmimo_adam_step(float* theta, const float* grad, float* m, float* v, int n,
     adam_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(theta, grad, m, v, n, lr, beta1, beta2, eps,
                                                                           c1, c2);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
+void cdmimo_batch_default_plan(cdmimo_batch_plan* plan)
+{
+    if (!plan) return;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->P = 16;
+    plan->threads = 256;
+    plan->group_bytes = 64 * 1024;
+    plan->ctas_per_sm = 0;
+}
+
+int cdmimo_batch_build(const cdmimo_batch_desc* desc, int n_desc, cdmimo_batch_plan* plan, void* table_host,
+                       size_t table_bytes)
+{
+    BatchBuild bb;
+    if (int rc = batch_split(desc, n_desc, plan, &bb)) return rc;
+    if (!table_host) return CDMIMO_OK;
+    if (table_bytes < plan->table_bytes || !aligned(table_host, 16)) return CDMIMO_ERR_WORKSPACE;
+    unsigned char* t = static_cast<unsigned char*>(table_host);
+    std::memset(t, 0, plan->table_bytes);
+    BatchTableHeader hdr{};
+    hdr.n_desc = (int)bb.descs.size();
+    hdr.n_items = plan->n_items;
+    hdr.n_groups = (int)bb.groups.size();
+    hdr.n_clusters = (int)bb.clusters.size();
+    hdr.off_desc = (unsigned)((sizeof(BatchTableHeader) + 15) & ~(size_t)15);
+    hdr.off_group = hdr.off_desc + (unsigned)((bb.descs.size() * sizeof(BatchDesc) + 15) & ~(size_t)15);
+    hdr.off_cluster = hdr.off_group + (unsigned)((bb.groups.size() * sizeof(BatchGroup) + 15) & ~(size_t)15);
+    hdr.total_bytes = (unsigned)plan->table_bytes;
+    std::memcpy(t, &hdr, sizeof(hdr));
+    std::memcpy(t + hdr.off_desc, bb.descs.data(), bb.descs.size() * sizeof(BatchDesc));
+    std::memcpy(t + hdr.off_group, bb.groups.data(), bb.groups.size() * sizeof(BatchGroup));
+    std::memcpy(t + hdr.off_cluster, bb.clusters.data(), bb.clusters.size() * sizeof(BatchCluster));
+    return CDMIMO_OK;
+}
+
+int cdmimo_detect_batched(const cdmimo_batch_plan* plan, const void* table_dev, int* counter, void* stream)
+{
+    if (!plan || !table_dev || !counter || !aligned(table_dev, 16) || !aligned(counter, 4)) return CDMIMO_ERR_INVALID_ARG;
+    if (plan->n_items == 0) return CDMIMO_OK;
+    if (plan->threads < 64 || plan->threads > 512 || (plan->threads & 31) || plan->smem_bytes == 0)
+        return CDMIMO_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (plan->P) {
+    case 8: return launch_batched_t<8>(plan, table_dev, counter, s);
+    case 16: return launch_batched_t<16>(plan, table_dev, counter, s);
+    case 32: return launch_batched_t<32>(plan, table_dev, counter, s);
+    }
+    return CDMIMO_ERR_INVALID_ARG;
 }
 
 const char* cdmimo_status_string(int status)

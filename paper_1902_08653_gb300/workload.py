@@ -188,3 +188,39 @@ def as_c64(A: np.ndarray) -> np.ndarray:
     """complex64 copy of A, and (as second value) the complex128 value the complex64 data holds."""
     a32 = np.ascontiguousarray(A, dtype=np.complex64)
     return a32, a32.astype(np.complex128)
+
+
+# --------------------------------------------------------------------------------------------
+# uneven resource blocks (batched launches)
+# --------------------------------------------------------------------------------------------
+def random_partition(g: np.random.Generator, B: int, sizes=(16, 32, 64)):
+    """A seeded random sequence of cluster sizes from `sizes` that sums to B."""
+    cs, rem = [], B
+    while rem > 0:
+        opts = [s for s in sizes if s <= rem]
+        if not opts:
+            raise ValueError("B cannot be partitioned into the given sizes")
+        s = int(g.choice(opts))
+        cs.append(s)
+        rem -= s
+    return cs
+
+
+def resource_blocks(seed: int, n_rb: int = 100, n_sc: int = 12, n_sym: int = 14, Bs=(128, 256, 512),
+                    sizes=(16, 32, 64), U_range=(8, 64), snr_db=20.0, M: int = 16, downlink_too: bool = False):
+    """Uneven resource blocks: per block B uniform from Bs, a random partition into `sizes`, U uniform
+    in U_range (inclusive), n_sc subcarriers x n_sym symbols of uplink data (and downlink symbols if
+    asked).  Returns a list of dicts: B, U, cluster_size and the uplink (and downlink) arrays."""
+    g = rng(seed, 4)
+    out = []
+    for r in range(n_rb):
+        B = int(g.choice(Bs))
+        cs = random_partition(g, B, sizes)
+        U = int(g.integers(U_range[0], U_range[1] + 1))
+        blk = {"B": B, "U": U, "cluster_size": cs}
+        blk.update(uplink(seed * 100003 + r, n_sc, n_sym, B, U, snr_db=snr_db, M=M, tag=5))
+        if downlink_too:
+            dl = downlink(seed * 100003 + r, n_sc, n_sym, B, U, M=M, tag=6)
+            blk["S"] = dl["S"]
+        out.append(blk)
+    return out

@@ -1,0 +1,157 @@
+"""GPU parity of the batched uneven launch (one persistent kernel over many resource blocks).
+
+Every block's output is compared with the FP64 oracle (1e-4 relative L2 per estimate vector) and
+with the single-block entry points (cdmimo_detect / cdmimo_precode), and CUDA-graph replay must
+reproduce the eager launch bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1902_08653_gb300 import batched, cdmimo
+from paper_1902_08653_gb300 import workload as wl
+
+from _util import assert_vectors_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    orc.build()
+    cdmimo.lib()
+    cdmimo.device_status(clear=True)
+    return torch.device("cuda:0")
+
+
+def make_items(blocks, dev, K=3, with_precode=False, fuse="colnorm"):
+    t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
+    items = []
+    for b in blocks:
+        n_sc, U, B = b["H"].shape
+        n_sym = b["Y"].shape[1]
+        H = t(b["H"])
+        items.append(dict(op=batched.DETECT, H=H, V=t(b["Y"]), N0=torch.from_numpy(b["N0"].astype(np.float32)).to(dev),
+                          out=torch.zeros((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
+                          cluster_size=b["cluster_size"], K=K, fuse=fuse, Ex=1.0))
+        if with_precode:
+            items.append(dict(op=batched.PRECODE, H=H, V=t(b["S"]),
+                              out=torch.zeros((n_sc, n_sym, B), dtype=torch.complex64, device=dev),
+                              cluster_size=b["cluster_size"], K=K, rho=1.0))
+    return items
+
+
+def check_against_oracle(blocks, items, K=3, fuse="colnorm", sample=None):
+    k = 0
+    for i, b in enumerate(blocks):
+        n = b["H"].shape[0] if sample is None else min(sample, b["H"].shape[0])
+        H64 = wl.as_c64(b["H"])[1][:n]
+        Y64 = wl.as_c64(b["Y"])[1][:n]
+        N0 = b["N0"].astype(np.float32).astype(np.float64)[:n]
+        Xo, _, _ = orc.detect(H64, Y64, N0, b["cluster_size"], K, fuse=fuse)
+        assert_vectors_close(items[k]["out"].cpu().numpy()[:n], Xo, 1e-4, f"detect block {i}")
+        k += 1
+        if k < len(items) and items[k]["op"] == batched.PRECODE:
+            S64 = wl.as_c64(b["S"])[1][:n]
+            Xd = orc.precode(H64, S64, b["cluster_size"], K)
+            assert_vectors_close(items[k]["out"].cpu().numpy()[:n], Xd, 1e-4, f"precode block {i}")
+            k += 1
+
+
+def test_batched_detect_and_precode_parity(dev):
+    blocks = wl.resource_blocks(7, n_rb=12, n_sc=3, n_sym=14, downlink_too=True)
+    items = make_items(blocks, dev, with_precode=True)
+    b = batched.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    check_against_oracle(blocks, items)
+    assert cdmimo.device_status(clear=True) == 0
+    # against the single-block entry points
+    for it in items:
+        if it["op"] == batched.DETECT:
+            ref = cdmimo.detect(it["H"], it["V"], it["N0"], it["cluster_size"], it["K"], fuse=it["fuse"])
+        else:
+            ref = cdmimo.precode(it["H"], it["V"], it["cluster_size"], it["K"])
+        assert_vectors_close(it["out"].cpu().numpy(), ref.cpu().numpy(), 2e-5, "vs single-block call")
+
+
+@pytest.mark.parametrize("cand", batched.CANDIDATES)
+def test_every_tile_candidate_is_correct(dev, cand):
+    blocks = wl.resource_blocks(11, n_rb=6, n_sc=2, n_sym=14)
+    items = make_items(blocks, dev)
+    b = batched.Batch(items, plan=batched.default_plan(**cand))
+    b.run()
+    torch.cuda.synchronize()
+    check_against_oracle(blocks, items)
+
+
+def test_odd_sizes_equal_fusion_and_converting_staging(dev):
+    # odd cluster sizes (no bulk copies), padded tiles, equal fusion, small K
+    blocks = []
+    for r, (cs, U) in enumerate([([7, 9, 5], 3), ([13, 20], 6), ([33, 17, 16], 9)]):
+        d = wl.uplink(40 + r, 4, 5, sum(cs), U, snr_db=12.0)
+        d["cluster_size"] = cs
+        blocks.append(d)
+    items = make_items(blocks, dev, K=2, fuse="equal")
+    b = batched.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    check_against_oracle(blocks, items, K=2, fuse="equal")
+
+
+def test_graph_replay_matches_eager(dev):
+    blocks = wl.resource_blocks(3, n_rb=10, n_sc=4, n_sym=14, downlink_too=True)
+    items = make_items(blocks, dev, with_precode=True)
+    b = batched.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    eager = [it["out"].clone() for it in items]
+    for it in items:
+        it["out"].zero_()
+    b.capture()
+    for it in items:
+        it["out"].zero_()
+    b.replay()
+    b.replay()
+    torch.cuda.synchronize()
+    for e, it in zip(eager, items):
+        assert torch.equal(e, it["out"])
+
+
+def test_autotune_and_full_size_sample(dev):
+    """The full uneven workload: 100 blocks x 12 subcarriers x 14 symbols, B in {128, 256, 512},
+    clusters of {16, 32, 64}, U in [8, 64], K = 3, 20 dB; autotuned; two subcarriers per block
+    checked against the oracle."""
+    blocks = wl.resource_blocks(20190222, n_rb=100, n_sc=12, n_sym=14)
+    items = make_items(blocks, dev)
+    b = batched.Batch(items)
+    plan, times = batched.autotune(b, reps=3)
+    assert len(times) >= 2
+    b.run()
+    torch.cuda.synchronize()
+    check_against_oracle(blocks, items, sample=2)
+    assert cdmimo.device_status(clear=True) == 0
+
+
+def test_single_block_streaming_path(dev):
+    """cdmimo_detect / cdmimo_precode on a block whose channel exceeds shared memory (B = 512 in 64-
+    antenna clusters, U = 64) stream cluster groups; parity with the oracle."""
+    cs = [64] * 8
+    d = wl.uplink(61, 3, 14, 512, 64, snr_db=20.0)
+    dl = wl.downlink(62, 3, 14, 512, 64)
+    t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
+    N0 = torch.from_numpy(d["N0"].astype(np.float32)).to(dev)
+    X = cdmimo.detect(t(d["H"]), t(d["Y"]), N0, cs, 3).cpu().numpy()
+    Xo, _, _ = orc.detect(wl.as_c64(d["H"])[1], wl.as_c64(d["Y"])[1], d["N0"].astype(np.float32).astype(np.float64),
+                          cs, 3, threads=8)
+    assert_vectors_close(X, Xo, 1e-4, "streaming detect")
+    Xd = cdmimo.precode(t(dl["H"]), t(dl["S"]), cs, 3).cpu().numpy()
+    Xdo = orc.precode(wl.as_c64(dl["H"])[1], wl.as_c64(dl["S"])[1], cs, 3, threads=8)
+    assert_vectors_close(Xd, Xdo, 1e-4, "streaming precode")
+    with pytest.raises(cdmimo.CdmimoError) as e:
+        cdmimo.detect(t(d["H"]), t(d["Y"]), N0, cs, 3,
+                      Xc=torch.zeros((3, 8, 14, 64), dtype=torch.complex64, device=dev))
+    assert e.value.status == cdmimo.ERR_UNSUPPORTED
