@@ -310,6 +310,21 @@ int cdmimo_adam_step(float* theta, const float* grad, float* m, float* v, int n,
                      float eps, int step, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- */
+/* Seeded synthetic inputs on the device (the system model of Sec. II; not part of the method).     */
+/* ---------------------------------------------------------------------------------------------- */
+/*
+ * H i.i.d. CN(0, 1) [n_sc][U][B]; X uniform Gray-labelled square M-QAM with unit average energy
+ * [n_sc][n_sym][U] (labels_opt [n_sc][n_sym][U] int32, or NULL); N0[f] = U 10^(-snr_db[f]/10)
+ * (per-receive-antenna SNR U Ex / N0 with Ex = 1); Y = H x + n with n i.i.d. CN(0, N0[f])
+ * [n_sc][n_sym][B].  All DEVICE; c64 outputs.  Random numbers: Philox4x32-10 keyed by `seed`, the
+ * counter of element i of stream s (0 channel, 1 labels, 2 noise) being (lo32(i), hi32(i), s, 0); a
+ * normal pair comes from the first two words by Box-Muller with u = (w + 0.5) / 2^32.  M in
+ * {4, 16, 64, 256}.  Three launches on `stream`.
+ */
+int cdmimo_synth_uplink(unsigned long long seed, int n_sc, int n_sym, int B, int U, int M, const float* snr_db, void* H,
+                        void* X, int* labels_opt, void* Y, float* N0, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
 /* Queries.                                                                                        */
 /* ---------------------------------------------------------------------------------------------- */
 #define CDMIMO_OP_DETECT 0

@@ -98,6 +98,7 @@ def lib():
             "cdmimo_batch_default_plan": ([ctypes.POINTER(BatchPlan)], None),
             "cdmimo_batch_build": ([ctypes.POINTER(BatchDesc), I, ctypes.POINTER(BatchPlan), P, S], I),
             "cdmimo_detect_batched": ([ctypes.POINTER(BatchPlan), P, P, P], I),
+            "cdmimo_synth_uplink": ([ctypes.c_ulonglong, I, I, I, I, I, P, P, P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -333,3 +334,22 @@ def adam_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8
     _check("cdmimo_adam_step", lib().cdmimo_adam_step(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(),
                                                       float(lr), float(beta1), float(beta2), float(eps), int(step),
                                                       _stream(stream)))
+
+
+def synth_uplink(seed, n_sc, n_sym, B, U, snr_db, M=16, device="cuda", labels=False, stream=None):
+    """cdmimo_synth_uplink: seeded synthetic uplink batch on the device.  snr_db: device float32 [n_sc].
+    Returns dict(H, X, Y, N0[, labels])."""
+    dev = torch.device(device)
+    out = {"H": torch.empty((n_sc, U, B), dtype=torch.complex64, device=dev),
+           "X": torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=dev),
+           "Y": torch.empty((n_sc, n_sym, B), dtype=torch.complex64, device=dev),
+           "N0": torch.empty(n_sc, dtype=torch.float32, device=dev)}
+    lab = torch.empty((n_sc, n_sym, U), dtype=torch.int32, device=dev) if labels else None
+    _need(snr_db, "snr_db")
+    rc = lib().cdmimo_synth_uplink(int(seed) & 0xFFFFFFFFFFFFFFFF, int(n_sc), int(n_sym), int(B), int(U), int(M),
+                                   _ptr(snr_db), _ptr(out["H"]), _ptr(out["X"]), _ptr(lab), _ptr(out["Y"]),
+                                   _ptr(out["N0"]), _stream(stream))
+    _check("cdmimo_synth_uplink", rc)
+    if labels:
+        out["labels"] = lab
+    return out

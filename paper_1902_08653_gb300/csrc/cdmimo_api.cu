@@ -14,6 +14,7 @@
 #include "cd_kernels_pp.cuh"
 #include "learned_kernels.cuh"
 #include "batched_kernel.cuh"
+#include "synth_kernels.cuh"
 #include "cdmimo.h"
 #include "plan.h"
 
@@ -925,6 +926,44 @@ int cdmimo_detect_batched(const cdmimo_batch_plan* plan, const void* table_dev, 
     case 32: return launch_batched_t<32>(plan, table_dev, counter, s);
     }
     return CDMIMO_ERR_INVALID_ARG;
+}
+
+int cdmimo_synth_uplink(unsigned long long seed, int n_sc, int n_sym, int B, int U, int M, const float* snr_db, void* H,
+                        void* X, int* labels, void* Y, float* N0, void* stream)
+{
+    if (n_sc < 0 || n_sym < 1 || B < 1 || U < 1) return CDMIMO_ERR_INVALID_ARG;
+    int L = 0;
+    switch (M) {
+    case 4: L = 2; break;
+    case 16: L = 4; break;
+    case 64: L = 8; break;
+    case 256: L = 16; break;
+    default: return CDMIMO_ERR_INVALID_ARG;
+    }
+    if (n_sc == 0) return CDMIMO_OK;
+    if (!snr_db || !H || !X || !Y || !N0 || !aligned(H, 8) || !aligned(X, 8) || !aligned(Y, 8)) return CDMIMO_ERR_INVALID_ARG;
+    SynthArgs a{};
+    a.seed = seed;
+    a.n_sc = n_sc;
+    a.n_sym = n_sym;
+    a.B = B;
+    a.U = U;
+    a.M = M;
+    a.L = L;
+    a.k = L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : 4;
+    a.scale = (float)(1.0 / std::sqrt(2.0 * (L * L - 1) / 3.0));
+    a.snr_db = snr_db;
+    a.H = static_cast<float2*>(H);
+    a.X = static_cast<float2*>(X);
+    a.labels = labels;
+    a.Y = static_cast<float2*>(Y);
+    a.N0 = N0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 152 * 8;
+    synth_channel_kernel<<<blocks, threads, 0, s>>>(a);
+    synth_symbol_kernel<<<blocks, threads, 0, s>>>(a);
+    synth_receive_kernel<<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
 const char* cdmimo_status_string(int status)

@@ -224,3 +224,56 @@ def resource_blocks(seed: int, n_rb: int = 100, n_sc: int = 12, n_sym: int = 14,
             blk["S"] = dl["S"]
         out.append(blk)
     return out
+
+
+# --------------------------------------------------------------------------------------------
+# Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): the host twin of the device generator
+# --------------------------------------------------------------------------------------------
+_PHILOX_M = (np.uint64(0xD2511F53), np.uint64(0xCD9E8D57))
+_PHILOX_W = (np.uint32(0x9E3779B9), np.uint32(0xBB67AE85))
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Vectorized Philox4x32-10 on uint32 arrays (counter words c0..c3, key words k0, k1)."""
+    c = [np.asarray(v, dtype=np.uint32).copy() for v in (c0, c1, c2, c3)]
+    k = [np.asarray(k0, dtype=np.uint32).copy(), np.asarray(k1, dtype=np.uint32).copy()]
+    m32 = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k[0] = (k[0].astype(np.uint64) + np.uint64(_PHILOX_W[0])).astype(np.uint32)
+            k[1] = (k[1].astype(np.uint64) + np.uint64(_PHILOX_W[1])).astype(np.uint32)
+        p0 = _PHILOX_M[0] * c[0].astype(np.uint64)
+        p1 = _PHILOX_M[1] * c[2].astype(np.uint64)
+        hi0, lo0 = (p0 >> np.uint64(32)).astype(np.uint32), (p0 & m32).astype(np.uint32)
+        hi1, lo1 = (p1 >> np.uint64(32)).astype(np.uint32), (p1 & m32).astype(np.uint32)
+        c = [hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0]
+    return c
+
+
+def philox_stream(seed: int, stream: int, n: int):
+    """The four output words for elements 0..n-1 of a stream (counter (lo(i), hi(i), stream, 0))."""
+    i = np.arange(n, dtype=np.uint64)
+    return philox4x32_10((i & np.uint64(0xFFFFFFFF)).astype(np.uint32), (i >> np.uint64(32)).astype(np.uint32),
+                         np.full(n, stream, np.uint32), np.zeros(n, np.uint32),
+                         np.full(n, seed & 0xFFFFFFFF, np.uint32), np.full(n, (seed >> 32) & 0xFFFFFFFF, np.uint32))
+
+
+def philox_cnormal(seed: int, stream: int, n: int, var=1.0):
+    """CN(0, var) samples by Box-Muller from the first two words, u = (w + 0.5) / 2^32 (FP64)."""
+    w = philox_stream(seed, stream, n)
+    u1 = (w[0].astype(np.float64) + 0.5) / 2.0 ** 32
+    u2 = (w[1].astype(np.float64) + 0.5) / 2.0 ** 32
+    rad = np.sqrt(-2.0 * np.log(u1) * 0.5 * np.asarray(var, dtype=np.float64))
+    return rad * np.cos(2 * np.pi * u2) + 1j * rad * np.sin(2 * np.pi * u2)
+
+
+def philox_uplink(seed: int, n_sc: int, n_sym: int, B: int, U: int, snr_db, M: int = 16):
+    """The batch cdmimo_synth_uplink draws, computed on the host in FP64 (for tests)."""
+    H = philox_cnormal(seed, 0, n_sc * U * B).reshape(n_sc, U, B)
+    lab = (philox_stream(seed, 1, n_sc * n_sym * U)[0] & np.uint32(M - 1)).astype(np.int64).reshape(n_sc, n_sym, U)
+    pts, _, _ = qam(M)
+    X = pts[lab]
+    N0 = snr_to_n0(np.broadcast_to(np.asarray(snr_db, dtype=np.float64), (n_sc,)), U)
+    noise = philox_cnormal(seed, 2, n_sc * n_sym * B, var=np.repeat(N0, n_sym * B)).reshape(n_sc, n_sym, B)
+    Y = np.einsum("fub,fnu->fnb", H, X) + noise
+    return {"H": H, "X": X, "labels": lab, "Y": Y, "N0": N0, "noise": noise}

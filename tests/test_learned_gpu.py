@@ -179,3 +179,16 @@ def test_training_beats_untrained_model(dev, tmp_path):
     back = learned.LearnedCD.load(p, device=dev)
     assert back.step == model.step and torch.equal(back.master, model.master)
     assert torch.equal(back.detect(H, Y, N0, cs), model.detect(H, Y, N0, cs))
+
+
+def test_centralized_cd_target_is_lmmse(dev):
+    """The training target (one cluster of all 256 antennas, 32 sweeps) equals the centralized
+    L-MMSE of Eq. (1) from the oracle's Cholesky solve."""
+    d = wl.uplink(77, 16, 2, 256, 16, snr_db=wl.sweep_snr(16))
+    H32, H64 = wl.as_c64(d["H"])
+    Y32, Y64 = wl.as_c64(d["Y"])
+    N0 = d["N0"].astype(np.float32)
+    X = cdmimo.detect(torch.from_numpy(H32).to(dev), torch.from_numpy(Y32).to(dev), torch.from_numpy(N0).to(dev),
+                      [256], 32, fuse="equal").cpu().numpy()
+    Xm = orc.lmmse(H64, Y64, N0.astype(np.float64))
+    assert_vectors_close(X, Xm, 1e-4, "centralized CD vs L-MMSE")

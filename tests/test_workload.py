@@ -73,3 +73,25 @@ def test_quantize_c16(kind, eps):
     rel = np.abs(deq - d["H"]) / np.maximum(np.abs(d["H"]), 1e-3)
     assert np.max(rel) < 2 * eps
     np.testing.assert_allclose(np.sqrt(np.mean(np.abs(d["H"].reshape(6, -1)) ** 2, axis=1)), scale, rtol=1e-6)
+
+
+def test_philox_known_answers():
+    """Known-answer vectors of Philox4x32-10 published with the algorithm's reference
+    implementation (Salmon et al., SC 2011)."""
+    f = 0xFFFFFFFF
+    cases = [((0, 0, 0, 0, 0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+             ((f, f, f, f, f, f), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+             ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344, 0xA4093822, 0x299F31D0),
+              (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for args, want in cases:
+        got = wl.philox4x32_10(*[[a] for a in args])
+        assert tuple(int(w[0]) for w in got) == want
+
+
+def test_philox_uplink_statistics():
+    d = wl.philox_uplink(123, 64, 4, 64, 8, snr_db=10.0, M=16)
+    assert abs(np.mean(np.abs(d["H"]) ** 2) - 1) < 0.03 and abs(np.mean(d["H"])) < 0.03
+    assert np.all((d["labels"] >= 0) & (d["labels"] < 16))
+    assert abs(np.mean(np.abs(d["noise"]) ** 2) / d["N0"][0] - 1) < 0.05
+    hist = np.bincount(d["labels"].ravel(), minlength=16) / d["labels"].size
+    assert np.all(np.abs(hist - 1 / 16) < 0.02)
