@@ -341,12 +341,197 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------------------------------------
+# other configurations (python bench.py --config N): measurement lines for the rest of the path
+# ------------------------------------------------------------------------------------------------
+def time_device(fn, steps, warmup, dev, flush_mb=256):
+    """Median/mean device time of fn() in ms with CUDA events, L2 flushed (untimed) between calls."""
+    import torch
+
+    flush = torch.empty(flush_mb * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i & 7))
+        ev[i][0].record()
+        fn()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    t = np.array([a.elapsed_time(b) for a, b in ev])
+    return float(np.median(t)), float(np.mean(t))
+
+
+def base_line(name, value, unit, args, config, **kw):
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "config": dict(workload=name, l2="flushed between timed calls (256 MB write, untimed)", **config)}
+    line.update(kw)
+    return line
+
+
+def run_config1(args, dev):
+    """B = 32 in 2 clusters of 16, U = 4, K = 3, 64 subcarriers x 1 symbol, QPSK at 10 dB, equal fusion."""
+    import torch
+
+    from paper_1902_08653_gb300 import cdmimo
+    from paper_1902_08653_gb300 import workload as wl
+
+    d = wl.uplink(20190222, 64, 1, 32, 4, snr_db=10.0, M=4)
+    H = torch.from_numpy(wl.as_c64(d["H"])[0]).to(dev)
+    Y = torch.from_numpy(wl.as_c64(d["Y"])[0]).to(dev)
+    N0 = torch.from_numpy(d["N0"].astype(np.float32)).to(dev)
+    X = torch.empty((64, 1, 4), dtype=torch.complex64, device=dev)
+    med, mean = time_device(lambda: cdmimo.detect(H, Y, N0, [16, 16], 3, fuse="equal", out=X), args.steps, args.warmup, dev)
+    return base_line("UL CD detection, B=32 (2 x 16), U=4, K=3, 64 subcarriers x 1 symbol, QPSK 10 dB, equal fusion",
+                     64 / (med * 1e-3), "vectors/s", args, {"n_sc": 64, "n_sym": 1, "B": 32, "C": 2, "U": 4, "K": 3},
+                     dtype="f32", ms_per_step=med, latency_us=med * 1e3, gpu_launches=1 * args.steps)
+
+
+def run_config3(args, dev):
+    """Config 2's shape at U = 32 with 64-QAM; H and y stored as c64, fp16 or bf16 (+ scale), K = 3 and 5."""
+    import torch
+
+    from paper_1902_08653_gb300 import cdmimo
+    from paper_1902_08653_gb300 import workload as wl
+
+    Uc, M3 = 32, 64
+    up = wl.uplink(20190222, N_SC, N_SYM, B, Uc, snr_db=wl.sweep_snr(N_SC), M=M3)
+    N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
+    store = {"c64": (torch.from_numpy(wl.as_c64(up["H"])[0]).to(dev), torch.from_numpy(wl.as_c64(up["Y"])[0]).to(dev),
+                     None, None)}
+    for kind, tdt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
+        qH, sH, _ = wl.quantize_c16(up["H"], kind)
+        qY, sY, _ = wl.quantize_c16(up["Y"], kind)
+        store[kind] = (torch.from_numpy(qH.view(np.int16)).to(dev).view(tdt),
+                       torch.from_numpy(qY.view(np.int16)).to(dev).view(tdt),
+                       torch.from_numpy(sH).to(dev), torch.from_numpy(sY).to(dev))
+    X = torch.empty((N_SC, N_SYM, Uc), dtype=torch.complex64, device=dev)
+    res, ref = {}, {}
+    for K3 in (3, 5):
+        for kind, (Ht, Yt, sH, sY) in store.items():
+            fn = lambda: cdmimo.detect(Ht, Yt, N0, CS, K3, h_scale=sH, y_scale=sY, out=X)
+            med, _ = time_device(fn, args.steps, args.warmup, dev)
+            fn()
+            xh = X.cpu().numpy().astype(np.complex128)
+            if kind == "c64":
+                ref[K3] = xh
+            rel = np.linalg.norm(xh - ref[K3], axis=-1) / np.linalg.norm(ref[K3], axis=-1)
+            mse, ber = mse_vs_mmse_U(up, xh, Uc, M3)
+            in_bytes = (Ht.numel() * Ht.element_size() + Yt.numel() * Yt.element_size()) / (N_SC * N_SYM)
+            res[f"{kind}_K{K3}"] = {"ms": med, "vectors_per_s": N_SC * N_SYM / (med * 1e-3),
+                                    "gbps": N_SC * N_SYM * Uc * 6 / (med * 1e-3) / 1e9,
+                                    "input_bytes_per_vector": in_bytes,
+                                    "rel_l2_vs_c64_median": float(np.median(rel)), "rel_l2_vs_c64_max": float(rel.max()),
+                                    "mse_vs_mmse_mean": float(np.mean(list(mse.values()))), "ber": ber}
+    best = res["f16_K3"]
+    return base_line("UL CD detection, B=256 (8 x 32), U=32, 64-QAM, 1200 x 14, SNR sweep; H, y in c64 / fp16 / bf16",
+                     best["vectors_per_s"], "vectors/s", args,
+                     {"n_sc": N_SC, "n_sym": N_SYM, "B": B, "C": C, "U": Uc, "K": 3, "qam": M3, "storage": "f16"},
+                     dtype="f32 (f16 storage)", ms_per_step=best["ms"], variants=res, gpu_launches=6 * args.steps)
+
+
+def mse_vs_mmse_U(up, Xhat, Uc, Mq):
+    H = up["H"]
+    A = np.einsum("fub,fvb->fuv", np.conj(H), H) + up["N0"][:, None, None] * np.eye(Uc)[None]
+    Z = np.einsum("fub,fnb->fun", np.conj(H), up["Y"])
+    Xm = np.linalg.solve(A, Z).transpose(0, 2, 1)
+    err = np.sum(np.abs(Xhat - Xm) ** 2, axis=-1) / Uc
+    from paper_1902_08653_gb300 import workload as wl
+
+    mse, ber = {}, {}
+    for sv in np.unique(up["snr_db"]):
+        sel = up["snr_db"] == sv
+        mse[f"{int(sv)}dB"] = float(np.mean(err[sel]))
+        lab, _ = wl.hard_decision(Xhat[sel], Mq)
+        ber[f"{int(sv)}dB"] = wl.bit_errors(lab, up["labels"][sel]) / (lab.size * int(np.log2(Mq)))
+    return mse, ber
+
+
+def run_config4(args, dev):
+    """100 resource blocks x 12 subcarriers x 14 symbols, B in {128,256,512}, clusters {16,32,64}, U in [8,64],
+    K = 3, 16-QAM at 20 dB: one persistent launch per step, replayed from a CUDA graph, autotuned tiles."""
+    import torch
+
+    from paper_1902_08653_gb300 import batched, cdmimo
+    from paper_1902_08653_gb300 import workload as wl
+
+    blocks = wl.resource_blocks(20190222, n_rb=100, n_sc=12, n_sym=14)
+    t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
+    items = []
+    flops = 0
+    for b in blocks:
+        n_sc, Ub, Bb = b["H"].shape
+        items.append(dict(op=batched.DETECT, H=t(b["H"]), V=t(b["Y"]),
+                          N0=torch.from_numpy(b["N0"].astype(np.float32)).to(dev),
+                          out=torch.empty((n_sc, 14, Ub), dtype=torch.complex64, device=dev),
+                          cluster_size=b["cluster_size"], K=3, fuse="colnorm", Ex=1.0))
+        flops += n_sc * 14 * 2 * 3 * Ub * Bb * 8
+    bt = batched.Batch(items)
+    plan, times = batched.autotune(bt, reps=5)
+    bt.capture()
+    med, _ = time_device(bt.replay, args.steps, args.warmup, dev)
+    n_vec = sum(b["H"].shape[0] * 14 for b in blocks)
+    # the same work as 100 separate single-block calls (one launch per block)
+    def separate():
+        for it in items:
+            cdmimo.detect(it["H"], it["V"], it["N0"], it["cluster_size"], 3, out=it["out"])
+    med_sep, _ = time_device(separate, max(3, args.steps // 10), args.warmup, dev)
+    tflops = flops / (med * 1e-3) / 1e12
+    return base_line("batched uneven UL CD detection, 100 RBs x 12 subcarriers x 14 symbols, B in {128,256,512}, "
+                     "clusters {16,32,64}, U in [8,64], K=3, 16-QAM 20 dB, CUDA graph", n_vec / (med * 1e-3),
+                     "vectors/s", args, {"n_rb": 100, "n_sc_per_rb": 12, "n_sym": 14, "K": 3},
+                     dtype="f32", ms_per_step=med, gpu_launches=1 * args.steps,
+                     roofline={"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": tflops / FP32_PEAK_TFLOPS, "traffic": None},
+                     autotune={"chosen": {k: getattr(plan, k) for k in ("P", "threads", "group_bytes", "ctas_per_sm")},
+                               "candidates_ms": times},
+                     separate_launches={"ms": med_sep, "vectors_per_s": n_vec / (med_sep * 1e-3),
+                                        "speedup_of_one_launch": med_sep / med})
+
+
+def run_config5(args, dev):
+    """Learned deep-unfolded CD, K = 2 (trained here on 1M device-generated channels) against plain CD
+    K = 2, 3, 5 on config 2's workload (B = 256, 8 x 32, U = 16, 1200 x 14, SNR sweep)."""
+    import torch
+
+    from paper_1902_08653_gb300 import cdmimo, train_learned
+    from paper_1902_08653_gb300 import workload as wl
+
+    model, info = train_learned.train(K=2, channels=args.train_channels, device=dev)
+    up, _ = make_inputs(20190223)
+    H = torch.from_numpy(wl.as_c64(up["H"])[0]).to(dev)
+    Y = torch.from_numpy(wl.as_c64(up["Y"])[0]).to(dev)
+    N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
+    X = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64, device=dev)
+    res = {}
+    runs = {"learned_K2": lambda: model.detect(H, Y, N0, CS, out=X)}
+    for Kp in (2, 3, 5):
+        runs[f"plain_K{Kp}"] = (lambda Kp=Kp: cdmimo.detect(H, Y, N0, CS, Kp, out=X))
+    for name, fn in runs.items():
+        med, _ = time_device(fn, args.steps, args.warmup, dev)
+        fn()
+        mse, ber = mse_vs_mmse(up, X.cpu().numpy().astype(np.complex128))
+        res[name] = {"ms": med, "vectors_per_s": N_SC * N_SYM / (med * 1e-3),
+                     "mse_vs_mmse": mse, "mse_vs_mmse_mean": float(np.mean(list(mse.values()))), "ber": ber}
+    lr = res["learned_K2"]
+    return base_line("learned deep-unfolded CD K=2 (tau_t, gamma_t, 17-64-1 MLP fusion) vs plain CD; B=256 (8 x 32), "
+                     "U=16, 1200 x 14, 16-QAM, SNR sweep", lr["vectors_per_s"], "vectors/s", args,
+                     {"n_sc": N_SC, "n_sym": N_SYM, "B": B, "C": C, "U": U, "K": 2},
+                     dtype="f32 (bf16 MLP weights)", ms_per_step=lr["ms"], variants=res,
+                     training={k: v for k, v in info.items() if k != "loss"}, gpu_launches=1 * args.steps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
+                    help="2 (default): UL detect + DL precode bench line; 1, 3, 4, 5: the other configurations")
+    ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -355,6 +540,15 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.config != 2:
+        import torch
+
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        fn = {1: run_config1, 3: run_config3, 4: run_config4, 5: run_config5}[args.config]
+        if rank == 0:
+            print(json.dumps(fn(args, dev)), flush=True)
         return
     if world > 1:
         import torch

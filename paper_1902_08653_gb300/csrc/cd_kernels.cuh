@@ -24,6 +24,10 @@ struct Elem<CDMIMO_C64> {
     {
         return __ldg(reinterpret_cast<const float2*>(base) + i);
     }
+    static __device__ __forceinline__ float2 load_shared(const void* base, size_t i)
+    {
+        return reinterpret_cast<const float2*>(base)[i];
+    }
 };
 template <>
 struct Elem<CDMIMO_C16F> {
@@ -31,12 +35,20 @@ struct Elem<CDMIMO_C16F> {
     {
         return __half22float2(__ldg(reinterpret_cast<const __half2*>(base) + i));
     }
+    static __device__ __forceinline__ float2 load_shared(const void* base, size_t i)
+    {
+        return __half22float2(reinterpret_cast<const __half2*>(base)[i]);
+    }
 };
 template <>
 struct Elem<CDMIMO_C16BF> {
     static __device__ __forceinline__ float2 load(const void* base, size_t i)
     {
         return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(base) + i));
+    }
+    static __device__ __forceinline__ float2 load_shared(const void* base, size_t i)
+    {
+        return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[i]);
     }
 };
 

@@ -45,23 +45,48 @@ __device__ __forceinline__ void permute_pairs_in_place(const CdPlan& pl, float2*
 
 // Arm a buffer's barrier for the next copy: one arrival that announces the copy's byte count.  The
 // copy itself is issued later, after the buffer's previous readers have passed a CTA barrier.
+template <int IN>
 __device__ __forceinline__ void arm_channel_copy(const CdPlan& pl, uint64_t* bar)
 {
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (uint32_t)pl.U * pl.B * 8u);
+    mbar_arrive_expect_tx(bar, (uint32_t)pl.U * pl.B * (IN == CDMIMO_C64 ? 8u : 4u));
 }
 
-// Bulk copies of subcarrier f's channel rows into one buffer: thread i issues row i (rows are
-// (cluster, user) pairs), so no thread issues more than one copy when U C <= blockDim.x.
+// Bulk copies of subcarrier f's channel rows: thread i issues row i (rows are (cluster, user)
+// pairs).  64-bit complex rows land in the skewed per-cluster layout of a channel buffer; 16-bit
+// rows land densely ([c][u][B_c], cluster c at U o_c) in a staging buffer, converted later.
+template <int IN>
 __device__ __forceinline__ void issue_channel_copy(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
-                                                   float2* Hs, uint64_t* bar)
+                                                   void* dst, uint64_t* bar)
 {
-    const float2* Hf = reinterpret_cast<const float2*>(H) + (size_t)f * pl.U * pl.B;
+    constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
+    const char* Hf = reinterpret_cast<const char*>(H) + (size_t)f * pl.U * pl.B * eb;
     for (int row = threadIdx.x; row < pl.U * pl.C; row += blockDim.x) {
         const int c = row / pl.U, u = row - c * pl.U;
         const ClusterTile ct = tab[c];
+        const size_t dofs = IN == CDMIMO_C64 ? (size_t)(ct.soff + u * ct.L) : (size_t)pl.U * ct.off + (size_t)u * ct.size;
         fence_proxy_async_smem();
-        bulk_g2s(Hs + ct.soff + u * ct.L, Hf + (size_t)u * pl.B + ct.off, (uint32_t)ct.size * 8u, bar);
+        bulk_g2s(reinterpret_cast<char*>(dst) + dofs * eb, Hf + ((size_t)u * pl.B + ct.off) * eb, (uint32_t)ct.size * eb,
+                 bar);
+    }
+}
+
+// 16-bit staging buffer (dense rows) -> pair-planar FP32 channel rows, padding columns included.
+template <int IN>
+__device__ __forceinline__ void convert_staged(const CdPlan& pl, const ClusterTile* tab, const void* stg, float2* Hs)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int row = warp; row < pl.U * pl.C; row += nwarps) {
+        const int c = row / pl.U, u = row - c * pl.U;
+        const ClusterTile ct = tab[c];
+        const size_t s0 = (size_t)pl.U * ct.off + (size_t)u * ct.size;
+        float4* dst = reinterpret_cast<float4*>(Hs + ct.soff + u * ct.L);
+        for (int q = lane; q < ct.L / 2; q += 32) {
+            const int j = 2 * q;
+            const float2 v0 = j < ct.size ? Elem<IN>::load_shared(stg, s0 + j) : make_float2(0.f, 0.f);
+            const float2 v1 = j + 1 < ct.size ? Elem<IN>::load_shared(stg, s0 + j + 1) : make_float2(0.f, 0.f);
+            dst[q] = make_float4(v0.x, v1.x, v0.y, v1.y);
+        }
     }
 }
 
@@ -170,16 +195,18 @@ __device__ __forceinline__ void pp_update(const float4 (&h)[kPairs], float2 d, f
 // the pair-planar layout.  Returns false on a copy timeout (the whole CTA then stops).
 template <int IN>
 __device__ __forceinline__ bool acquire_channel(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
-                                                float2* Hb, uint64_t* bar, uint32_t parity, bool rearm)
+                                                float2* Hb, const void* stg, uint64_t* bar, uint32_t parity,
+                                                bool rearm)
 {
     bool ok = true;
     if (pl.bulk) ok = mbar_wait_bounded(bar, parity);
     else stage_H_converting<IN>(pl, tab, H, f, Hb);
     if (__syncthreads_or(!ok)) return false;
     // This buffer next receives the copy issued at the start of the next iteration: arm it now.
-    if (pl.bulk && rearm && threadIdx.x == 0) arm_channel_copy(pl, bar);
+    if (pl.bulk && rearm && threadIdx.x == 0) arm_channel_copy<IN>(pl, bar);
     if (pl.bulk) {
-        permute_pairs_in_place(pl, Hb);
+        if (IN == CDMIMO_C64) permute_pairs_in_place(pl, Hb);
+        else convert_staged<IN>(pl, tab, stg, Hb);
         __syncthreads();
     }
     return true;
@@ -200,8 +227,11 @@ template <int IN, int AT, bool LEARNED>
 __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const DetectIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    // Channel buffer j (0 or 1) starts at byte j * off_H2.
-    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + (j ? pl.off_H2 : 0u)); };
+    // Channel buffer j: 64-bit storage double-buffers the channel itself (buffer 1 at off_H2); 16-bit
+    // storage double-buffers the raw copies (staging j at off_H2 / off_H3) and converts into one buffer.
+    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + ((IN == CDMIMO_C64 && j) ? pl.off_H2 : 0u)); };
+    auto Stg = [&](int j) { return reinterpret_cast<void*>(smem + (j ? pl.off_H3 : pl.off_H2)); };
+    auto Dst = [&](int j) { return IN == CDMIMO_C64 ? reinterpret_cast<void*>(Hbuf(j)) : Stg(j); };
     float2* Xs = reinterpret_cast<float2*>(smem + pl.off_X);  // [U][x_stride] current x per tile
     // [U][x_stride] per tile: (m, n) of Algorithm 1; learned sweeps keep (||h_{u,c}||^2, m) instead
     float2* Ks = reinterpret_cast<float2*>(smem + pl.off_K);
@@ -241,11 +271,11 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
 
     int f = blockIdx.x;
     if (pl.bulk && tid == 0) {  // arm buffer 0 (first subcarrier) and buffer 1 (second)
-        if (f < pl.n_sc) arm_channel_copy(pl, &bar[0]);
-        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy(pl, &bar[1]);
+        if (f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
+        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy<IN>(pl, &bar[1]);
     }
     __syncthreads();
-    if (pl.bulk && f < pl.n_sc) issue_channel_copy(pl, tab, io.H, f, Hbuf(0), &bar[0]);
+    if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, f, Dst(0), &bar[0]);
     float4 r[kPairs];
     if (lt.active && f < pl.n_sc)
         load_lane_pairs<IN, AT>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
@@ -253,7 +283,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
     for (int k = 0; f < pl.n_sc; f += gridDim.x, ++k) {
         const int b = k & 1;
         const int fn = f + gridDim.x;
-        if (pl.bulk && fn < pl.n_sc) issue_channel_copy(pl, tab, io.H, fn, Hbuf(b ^ 1), &bar[b ^ 1]);
+        if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
 
         float alpha = __ldg(io.N0 + f) * pl.inv_Ex;
         float out_scale = 1.f;
@@ -268,7 +298,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             alpha = 0.f;
         }
         if (LEARNED && !learned_ok) out_scale = __int_as_float(0x7fc00000);
-        if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), &bar[b], (uint32_t)(k >> 1) & 1u,
+        if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
                                  fn + (int)gridDim.x < pl.n_sc))
             return;
 
@@ -460,8 +490,11 @@ template <int IN, int AT>
 __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const PrecodeIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    // Channel buffer j (0 or 1) starts at byte j * off_H2.
-    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + (j ? pl.off_H2 : 0u)); };
+    // Channel buffer j: 64-bit storage double-buffers the channel itself (buffer 1 at off_H2); 16-bit
+    // storage double-buffers the raw copies (staging j at off_H2 / off_H3) and converts into one buffer.
+    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + ((IN == CDMIMO_C64 && j) ? pl.off_H2 : 0u)); };
+    auto Stg = [&](int j) { return reinterpret_cast<void*>(smem + (j ? pl.off_H3 : pl.off_H2)); };
+    auto Dst = [&](int j) { return IN == CDMIMO_C64 ? reinterpret_cast<void*>(Hbuf(j)) : Stg(j); };
     float* Qs = reinterpret_cast<float*>(smem + pl.off_K);    // [U][x_stride] p_{u,c}^2 per tile
     float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);  // [n_sym][U | 1] (odd stride: no bank conflicts)
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
@@ -491,11 +524,11 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
 
     int f = blockIdx.x;
     if (pl.bulk && tid == 0) {  // arm buffer 0 (first subcarrier) and buffer 1 (second)
-        if (f < pl.n_sc) arm_channel_copy(pl, &bar[0]);
-        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy(pl, &bar[1]);
+        if (f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
+        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy<IN>(pl, &bar[1]);
     }
     __syncthreads();
-    if (pl.bulk && f < pl.n_sc) issue_channel_copy(pl, tab, io.H, f, Hbuf(0), &bar[0]);
+    if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, f, Dst(0), &bar[0]);
     float2 sv[kSPrefetch];
 #pragma unroll
     for (int q = 0; q < kSPrefetch; ++q) {
@@ -506,7 +539,7 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
     for (int k = 0; f < pl.n_sc; f += gridDim.x, ++k) {
         const int b = k & 1;
         const int fn = f + gridDim.x;
-        if (pl.bulk && fn < pl.n_sc) issue_channel_copy(pl, tab, io.H, fn, Hbuf(b ^ 1), &bar[b ^ 1]);
+        if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
 #pragma unroll
         for (int q = 0; q < kSPrefetch; ++q) {
             const int i = tid + q * blockDim.x;
@@ -515,7 +548,7 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
                 Ss[n * s_stride + (i - n * U)] = sv[q];
             }
         }
-        if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), &bar[b], (uint32_t)(k >> 1) & 1u,
+        if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
                                  fn + (int)gridDim.x < pl.n_sc))
             return;
         // The next subcarrier's s (this one's is in shared memory now).

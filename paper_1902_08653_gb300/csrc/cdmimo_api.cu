@@ -126,10 +126,28 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     const unsigned xs = (unsigned)pl->n_tiles | 1u;
     pl->packed = (P == 16 && pl->n_lanes <= kMaxSpecializedThreads &&
                   (pl->A_uniform == 1 || pl->A_uniform == 2 || pl->A_uniform == 4)) ? 1 : 0;
-    unsigned o = align16((unsigned)pl->h_entries * 8u);
+    bool all_mult4 = true;
+    for (int c = 0; c < p->C; ++c) all_mult4 = all_mult4 && (p->cluster_size[c] % 4 == 0);
+    if (p->in_dtype == CDMIMO_C64) pl->bulk = (all_even && aligned(H, 16)) ? 1 : 0;
+    else pl->bulk = (pl->packed && all_mult4 && aligned(H, 16)) ? 1 : 0;
+    const unsigned hreg = align16((unsigned)pl->h_entries * 8u);
+    unsigned o = hreg;
+    // The packed kernels prefetch by bulk copy into a second buffer: the channel itself (c64), or two
+    // 16-bit staging buffers of the raw rows (converted into the one channel buffer).  The
+    // converting path stages into one buffer (both buffer indices alias it).
     if (pl->packed) {
-        pl->off_H2 = o;
-        o = align16(o + (unsigned)pl->h_entries * 8u);
+        pl->off_H2 = 0u;
+        pl->off_H3 = 0u;
+        if (pl->bulk && p->in_dtype == CDMIMO_C64) {
+            pl->off_H2 = o;
+            o = align16(o + hreg);
+        } else if (pl->bulk) {
+            const unsigned sreg = align16(U * (unsigned)p->B * 4u);
+            pl->off_H2 = o;
+            o = align16(o + sreg);
+            pl->off_H3 = o;
+            o = align16(o + sreg);
+        }
         pl->off_K = o;
         o = align16(o + U * xs * (detect ? 8u : 4u));
     }
@@ -162,7 +180,6 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     if (pl->packed && !detect && p->n_sym * p->U > kSPrefetch * std::max(64, (pl->n_lanes + 31) / 32 * 32))
         pl->packed = 0;  // the packed precoder prefetches at most kSPrefetch entries of s per thread
 
-    pl->bulk = (p->in_dtype == CDMIMO_C64 && all_even && aligned(H, 16)) ? 1 : 0;
     return CDMIMO_OK;
 }
 

@@ -32,7 +32,8 @@ struct CdPlan {
     int h_entries;    // complex entries of the shared-memory channel region
     int n_lanes;      // lanes that run CD tiles: n_sym * sum A_c
     int n_tiles;      // C * n_sym
-    int bulk;         // 1: channel rows arrive by cp.async.bulk (c64, every B_c even, 16-B aligned H)
+    int bulk;         // 1: channel rows arrive by cp.async.bulk (c64: every B_c even; 16-bit storage,
+                      //    packed kernels only: every B_c a multiple of 4; H 16-byte aligned)
     int padded;       // 1: some B_c < A_c P (zero columns must be written once)
     int packed;       // 1: the packed persistent kernels (uniform A in {1, 2, 4}, P = 16) run this plan
     int fuse;         // cdmimo_fuse_rule
@@ -42,7 +43,7 @@ struct CdPlan {
     // byte offsets of the shared-memory regions (channel blocks start at 0; the packed kernels keep
     // a second channel buffer at off_H2 and per-tile coefficients at off_K)
     // off_mlp: [C][CDMIMO_MAX_HIDDEN] floats of learned-fusion partial sums (learned plans only)
-    unsigned off_H2, off_X, off_K, off_coef, off_e, off_lam, off_S, off_mlp, off_tab, off_bar, smem_bytes;
+    unsigned off_H2, off_H3, off_X, off_K, off_coef, off_e, off_lam, off_S, off_mlp, off_tab, off_bar, smem_bytes;
     ClusterTile cl[CDMIMO_MAX_CLUSTERS];
 };
 

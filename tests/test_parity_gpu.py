@@ -254,3 +254,26 @@ def test_host_variants_match_device_calls(dev):
     cdmimo.precode_host(Hd, S, cs, 3, Xd, ws)
     torch.cuda.synchronize()
     assert torch.equal(Xd, cdmimo.precode(Hd.to(dev), S.to(dev), cs, 3).cpu())
+
+
+@pytest.mark.parametrize("cs,U", [([20] * 4, 8), ([18] * 2, 5), ([16] * 4, 12), ([64] * 2, 16)])
+def test_low_precision_staging_paths(dev, cs, U):
+    """16-bit storage: cluster sizes that are multiples of 4 take the bulk-copied staging buffers
+    (with padding columns when B_c < A P), others the converting loads; both match the oracle."""
+    n_sc, n_sym = 13, 6
+    d = wl.uplink(91, n_sc, n_sym, sum(cs), U, snr_db=wl.sweep_snr(n_sc), M=16)
+    dl = wl.downlink(92, n_sc, n_sym, sum(cs), U)
+    N0 = d["N0"].astype(np.float32)
+    for kind, tdt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
+        qH, sH, dH = wl.quantize_c16(d["H"], kind)
+        qY, sY, dY = wl.quantize_c16(d["Y"], kind)
+        Xg = cdmimo.detect(torch.from_numpy(qH.view(np.int16)).to(dev).view(tdt),
+                           torch.from_numpy(qY.view(np.int16)).to(dev).view(tdt), to_dev(N0, dev), cs, 3,
+                           h_scale=to_dev(sH, dev), y_scale=to_dev(sY, dev)).cpu().numpy()
+        Xo, _, _ = orc.detect(dH, dY, N0.astype(np.float64), cs, 3)
+        assert_vectors_close(Xg, Xo, TOL, f"{kind} detect {cs}")
+        qHd, _, dHd = wl.quantize_c16(dl["H"], kind)
+        S32, S64 = wl.as_c64(dl["S"])
+        Xd = cdmimo.precode(torch.from_numpy(qHd.view(np.int16)).to(dev).view(tdt), to_dev(S32, dev), cs,
+                            3).cpu().numpy()
+        assert_vectors_close(Xd, orc.precode(dHd, S64, cs, 3), TOL, f"{kind} precode {cs}")
