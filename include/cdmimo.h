@@ -49,6 +49,7 @@ typedef enum {
 #define CDMIMO_DEV_TIMEOUT 0x1   /* a bounded wait on an async copy or work queue expired */
 #define CDMIMO_DEV_BAD_N0 0x2    /* some N0[f] was negative or NaN: that subcarrier's output is NaN */
 #define CDMIMO_DEV_BAD_LEARNED 0x4 /* the learned block does not match p->K or p->U: output is NaN */
+#define CDMIMO_DEV_BAD_SCHED 0x8  /* a workspace's schedule counters were not zero: output incomplete */
 
 #define CDMIMO_MAX_CLUSTERS 64
 #define CDMIMO_MAX_USERS 64
@@ -112,8 +113,14 @@ typedef struct {
  * Xhat     DEVICE c64 [n_sc][n_sym][U] output, 8-byte aligned.
  * Xc_opt   DEVICE c64 [n_sc][C][n_sym][U] per-cluster estimates, or NULL.
  * lambda_opt DEVICE float [n_sc][C] fusion weights, or NULL.
- * workspace, ws_bytes  DEVICE scratch of at least cdmimo_workspace_size(p, CDMIMO_OP_DETECT) bytes
- *          (currently 0 for every supported shape; NULL is accepted when 0 is needed).
+ * workspace, ws_bytes  optional DEVICE scratch of cdmimo_workspace_size(p, op) (256) bytes, 16-byte
+ *          aligned (else CDMIMO_ERR_WORKSPACE), zero-filled before its first use; every call leaves
+ *          it zero-filled when its kernel completes.  With it the persistent kernels hand out
+ *          subcarriers dynamically (an atomic ticket counter), so CTAs that share an SM and run at
+ *          different speeds finish together; with NULL they take a static round-robin schedule.
+ *          The output is the same bit for bit.  One workspace serves one call at a time: calls that
+ *          may run concurrently (other streams) need their own.  Counters found non-zero at the
+ *          start leave subcarriers undone and set CDMIMO_DEV_BAD_SCHED.
  * stream   cudaStream_t (NULL = legacy default stream).
  * Shapes whose per-subcarrier channel does not fit in shared memory (or needs more than 512 lanes
  * per CTA) run by streaming cluster groups through shared memory (one CTA per subcarrier); that
@@ -130,6 +137,7 @@ int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const fl
  *   x_c <- rho_c x_c / ||x_c|| (x_c = 0 stays 0).  Output Xdl = [x_1; ...; x_C].
  * H        DEVICE, dtype p->in_dtype (16-bit storage needs no scale: the normalization removes it).
  * S        DEVICE c64 [n_sc][n_sym][U], 8-byte aligned.   Xdl DEVICE c64 [n_sc][n_sym][B].
+ * workspace as for cdmimo_detect.
  * Shapes beyond shared memory stream cluster groups as cdmimo_detect does (c64 storage only).
  */
 int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* Xdl, void* workspace,
@@ -330,11 +338,12 @@ int cdmimo_synth_uplink(unsigned long long seed, int n_sc, int n_sym, int B, int
 #define CDMIMO_OP_DETECT 0
 #define CDMIMO_OP_PRECODE 1
 
-/* Device scratch bytes that cdmimo_detect / cdmimo_precode need for p (0 when none), or 0 with an
- * invalid p (the call itself then reports the error). */
+/* Bytes of the optional device workspace of cdmimo_detect / cdmimo_precode (the schedule counters:
+ * 256 for every p). */
 size_t cdmimo_workspace_size(const cdmimo_params* p, int op);
 
-/* Device staging bytes that cdmimo_detect_host / cdmimo_precode_host need for p. */
+/* Device staging bytes that cdmimo_detect_host / cdmimo_precode_host need for p (the last 256 hold
+ * the schedule counters, which every host call zeroes before its launch). */
 size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
 
 /* Static name of a status code. */

@@ -167,9 +167,35 @@ def make_params(n_sc, n_sym, B, U, cluster_size, K, *, Ex=1.0, fuse="colnorm", r
     return p, cs
 
 
+_SCHED = {}
+
+
+def schedule_workspace(device, stream=None):
+    """The zero-filled 256-byte schedule workspace this binding passes to cdmimo_detect /
+    cdmimo_precode on (device, stream): one per stream, so calls on different streams never share
+    counters.  Pass workspace=False to a call for the static schedule."""
+    device = torch.device(device)
+    key = (device.index if device.index is not None else torch.cuda.current_device(), _stream(stream).value)
+    ws = _SCHED.get(key)
+    if ws is None:
+        ws = _SCHED[key] = torch.zeros(int(lib().cdmimo_workspace_size(None, OP_DETECT)), dtype=torch.uint8,
+                                       device=device)
+    return ws
+
+
+def _workspace_args(workspace, device, stream):
+    if workspace is False:
+        return None, 0
+    if workspace is None:
+        workspace = schedule_workspace(device, stream)
+    return workspace.data_ptr(), workspace.numel() * workspace.element_size()
+
+
 def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y_scale=None, learned=None,
            out=None, Xc=None, lam=None, workspace=None, stream=None):
-    """cdmimo_detect: Algorithm 1 + fusion.  Returns Xhat [n_sc, n_sym, U] complex64."""
+    """cdmimo_detect: Algorithm 1 + fusion.  Returns Xhat [n_sc, n_sym, U] complex64.
+    workspace: None = this binding's per-stream schedule workspace, False = static schedule, or a
+    zero-filled device tensor of cdmimo_workspace_size bytes."""
     _need(H, "H")
     _need(Y, "Y")
     _need(N0, "N0")
@@ -185,8 +211,7 @@ def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y
     _need(out, "out")
     p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse=fuse, in_dtype=dt, h_scale=h_scale,
                           y_scale=y_scale, learned=learned)
-    ws = workspace.data_ptr() if workspace is not None else None
-    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ws, wsb = _workspace_args(workspace, H.device, stream)
     rc = lib().cdmimo_detect(ctypes.byref(p), _ptr(H), _ptr(Y), _ptr(N0), _ptr(out), _ptr(Xc), _ptr(lam),
                              ws, wsb, _stream(stream))
     _check("cdmimo_detect", rc)
@@ -194,7 +219,8 @@ def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y
 
 
 def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=None):
-    """cdmimo_precode: Algorithm 2 + per-cluster normalization.  Returns Xdl [n_sc, n_sym, B] complex64."""
+    """cdmimo_precode: Algorithm 2 + per-cluster normalization.  Returns Xdl [n_sc, n_sym, B] complex64.
+    workspace as for detect."""
     _need(H, "H")
     _need(S, "S")
     dt = _dtype_of(H)
@@ -206,8 +232,7 @@ def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=
         out = torch.empty((n_sc, n_sym, B), dtype=torch.complex64, device=H.device)
     _need(out, "out")
     p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, rho=rho, in_dtype=dt)
-    ws = workspace.data_ptr() if workspace is not None else None
-    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ws, wsb = _workspace_args(workspace, H.device, stream)
     rc = lib().cdmimo_precode(ctypes.byref(p), _ptr(H), _ptr(S), _ptr(out), ws, wsb, _stream(stream))
     _check("cdmimo_precode", rc)
     return out

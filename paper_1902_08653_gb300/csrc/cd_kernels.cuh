@@ -72,22 +72,25 @@ struct LaneTile {
 __device__ __forceinline__ LaneTile map_lane(const CdPlan& pl, const ClusterTile* tab)
 {
     LaneTile t{};
-    const int tid = threadIdx.x;
-    t.active = tid < pl.n_lanes;
+    // Tile lane v sits in warp v / lpw at lane v % lpw (lpw = 32 unless the plan spreads the tiles
+    // over more warps); the tiles of one warp are whole and A-aligned.
+    const int wl = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = w * pl.lpw + wl;
+    t.active = wl < pl.lpw && v < pl.n_lanes;
     t.c = 0;
     t.A = 1;
     if (t.active) {
         for (int k = 0; k < pl.C; ++k) {
             const int l0 = tab[k].lane0;
-            if (tid >= l0 && tid < l0 + pl.n_sym * tab[k].A) {
+            if (v >= l0 && v < l0 + pl.n_sym * tab[k].A) {
                 t.c = k;
                 t.A = tab[k].A;
-                t.n = (tid - l0) / t.A;
-                t.a = (tid - l0) & (t.A - 1);
+                t.n = (v - l0) / t.A;
+                t.a = (v - l0) & (t.A - 1);
             }
         }
     }
-    const int n_act = min(32, pl.n_lanes - (tid & ~31));
+    const int n_act = min(pl.lpw, pl.n_lanes - w * pl.lpw);
     t.mask = n_act >= 32 ? 0xffffffffu : (n_act > 0 ? ((1u << n_act) - 1u) : 0u);
     t.Awarp = t.active ? (int)__reduce_max_sync(t.mask, (unsigned)t.A) : 1;
     return t;

@@ -115,8 +115,9 @@ __device__ __forceinline__ void stage_H_converting(const CdPlan& pl, const Clust
 // through one packed add, so the values start out in the aligned register pairs that the packed FMAs
 // of the CD loop produce; the loop-carried vector then needs no register moves (measured: it removes
 // a third of the uplink kernel's instructions).
+// The lane's entries of one vector as loaded: (re_j, im_j, re_{j+1}, im_{j+1}) per pair.
 template <int IN, int AT>
-__device__ __forceinline__ void load_lane_pairs(const void* V, size_t base, int size, int a, float4 (&v)[kPairs])
+__device__ __forceinline__ void load_lane_raw(const void* V, size_t base, int size, int a, float4 (&v)[kPairs])
 {
     const float2 z = make_float2(0.f, 0.f);
 #pragma unroll
@@ -124,8 +125,19 @@ __device__ __forceinline__ void load_lane_pairs(const void* V, size_t base, int 
         const int j = 2 * (i * AT + a);
         const float2 v0 = j < size ? Elem<IN>::load(V, base + j) : z;
         const float2 v1 = j + 1 < size ? Elem<IN>::load(V, base + j + 1) : z;
-        v[i] = cat4(__fadd2_rn(make_float2(v0.x, v1.x), z), __fadd2_rn(make_float2(v0.y, v1.y), z));
+        v[i] = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
+}
+
+// To the pair-planar register layout (re_j, re_{j+1}, im_j, im_{j+1}).  The packed adds (of zero)
+// write each pair into an aligned register pair, so the sweeps' packed FMAs need no moves.  Done
+// just before the sweeps, so a prefetch issued one subcarrier earlier is not waited for sooner.
+__device__ __forceinline__ void raw_to_pairs(float4 (&v)[kPairs])
+{
+    const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kPairs; ++i)
+        v[i] = cat4(__fadd2_rn(make_float2(v[i].x, v[i].z), z), __fadd2_rn(make_float2(v[i].y, v[i].w), z));
 }
 
 template <int AT>
@@ -212,6 +224,42 @@ __device__ __forceinline__ bool acquire_channel(const CdPlan& pl, const ClusterT
     return true;
 }
 
+// Subcarrier schedule of the persistent kernels.  With G CTAs, CTA i starts with subcarriers i and
+// i + G.  Static (no counters): it goes on with i + 2G, i + 3G, ...  Dynamic (three counters in the
+// caller's workspace): each later subcarrier is 2G + a ticket drawn from counter 0 one iteration
+// ahead, so CTAs that run faster take more subcarriers.  A subcarrier's result does not depend on
+// the CTA that computes it, so both schedules give the same output bit for bit.
+__device__ __forceinline__ unsigned sched_draw(unsigned* sched, bool need)
+{
+    return (sched && need && threadIdx.x == 0) ? atomicAdd(sched, 1u) : 0u;
+}
+
+// The subcarrier after fn (n_sc: none).
+__device__ __forceinline__ int sched_next(const unsigned* sched, bool drew, unsigned ticket, int fn, int n_sc)
+{
+    if (!sched) return fn + (int)gridDim.x;
+    const unsigned v = 2u * gridDim.x + ticket;
+    return (drew && v < (unsigned)n_sc) ? (int)v : n_sc;
+}
+
+// End of a dynamically scheduled launch: counter 1 counts finished CTAs, counter 2 subcarriers
+// done.  The last CTA checks that every subcarrier was taken exactly once and zeroes the counters
+// for the next call on the same workspace.
+__device__ __forceinline__ void sched_finish(unsigned* sched, int done, int n_sc)
+{
+    if (!sched || threadIdx.x != 0) return;
+    atomicAdd(sched + 2, (unsigned)done);
+    __threadfence();
+    if (atomicAdd(sched + 1, 1u) == gridDim.x - 1u) {
+        __threadfence();
+        if (atomicAdd(sched + 2, 0u) != (unsigned)n_sc) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_SCHED);
+        sched[0] = 0u;
+        sched[1] = 0u;
+        sched[2] = 0u;
+        __threadfence();
+    }
+}
+
 // Column energies of one cluster from a staged buffer (K = 0 only: no sweep computed them).
 __device__ __forceinline__ float row_energy(const float2* row, int L)
 {
@@ -238,6 +286,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
     float* lam = reinterpret_cast<float*>(smem + pl.off_lam); // [C]
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);  // [2]
+    int* nxt = reinterpret_cast<int*>(smem + pl.off_bar + 16);       // [2] schedule hand-off
 
     float* mlp = reinterpret_cast<float*>(smem + pl.off_mlp);   // [C][hidden <= 64] (learned fusion)
     const cdmimo_learned* blk = reinterpret_cast<const cdmimo_learned*>(io.learned);
@@ -278,11 +327,14 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
     if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, f, Dst(0), &bar[0]);
     float4 r[kPairs];
     if (lt.active && f < pl.n_sc)
-        load_lane_pairs<IN, AT>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
+        load_lane_raw<IN, AT>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
 
-    for (int k = 0; f < pl.n_sc; f += gridDim.x, ++k) {
+    int fn = f + (int)gridDim.x;  // this CTA's next subcarrier
+    int done = 0;
+    for (int k = 0; f < pl.n_sc; ++k) {
         const int b = k & 1;
-        const int fn = f + gridDim.x;
+        const bool draw = fn < pl.n_sc;
+        const unsigned ticket = sched_draw(io.sched, draw);
         if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
 
         float alpha = __ldg(io.N0 + f) * pl.inv_Ex;
@@ -299,8 +351,12 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
         }
         if (LEARNED && !learned_ok) out_scale = __int_as_float(0x7fc00000);
         if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
-                                 fn + (int)gridDim.x < pl.n_sc))
-            return;
+                                 io.sched != nullptr || fn + (int)gridDim.x < pl.n_sc)) {
+            // copy timeout: let the copy in flight into the other buffer land (bounded), then stop
+            if (pl.bulk && fn < pl.n_sc && tid == 0) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+            break;
+        }
+        if (lt.active) raw_to_pairs(r);
 
         if (LEARNED && lt.active && pl.K > 0) {
             // Learned sweeps: x_u <- a1 h^H r + a2 x_u with a1 = tau_t / (e + gamma_t alpha),
@@ -343,7 +399,10 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             float2* xs = Xs + tile;
             float2* ks = Ks + tile;
             // Sweep 1 with the preprocessing of Algorithm 1 folded in: e = ||h_{u,c}||^2,
-            // m = (e + N0/Ex)^{-1}, n = m e; x starts at 0, so x_u <- m h^H r.
+            // m = (e + N0/Ex)^{-1}, n = m e; x starts at 0, so x_u <- m h^H r.  Every lane also sums
+            // m over u for the fusion weight of its cluster (a skipped column, m = 0, counts as an
+            // infinite (||h||^2 + N0/Ex)^{-1} and gives the cluster weight 0).
+            float msum = 0.f;
 #pragma unroll 1
             for (int u = 0; u < U; ++u) {
                 float4 h[kPairs];
@@ -358,6 +417,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
                 }
                 const float den = e + alpha;
                 const float m = den > 0.f ? __fdividef(1.f, den) : 0.f;
+                msum += m > 0.f ? m : __int_as_float(0x7f800000);
                 ks[u * xs_stride] = make_float2(m, m * e);
                 const float2 xn = make_float2(m * g.x, m * g.y);
                 xs[u * xs_stride] = xn;
@@ -378,100 +438,116 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
                     pp_update(h, make_float2(xn.x - xo.x, xn.y - xo.y), r);
                 }
             }
+            if (lt.n == 0 && lt.a == 0) lam[lt.c] = 1.f / msum;  // w_c, normalized in the fusion
         }
         if (pl.K == 0) {  // no sweep ran: x = 0, and the fusion weights still need m
             for (int i = tid; i < U * (int)xs_stride; i += blockDim.x) Xs[i] = make_float2(0.f, 0.f);
             if (lt.active && lt.a == 0) {
+                float msum = 0.f;
                 for (int u = 0; u < U; ++u) {
                     const float e = row_energy(Hbuf(b) + ct.soff + u * ct.L, ct.L);
                     const float m = e + alpha > 0.f ? __fdividef(1.f, e + alpha) : 0.f;
+                    msum += m > 0.f ? m : __int_as_float(0x7f800000);
                     Ks[u * xs_stride + tile] = LEARNED ? make_float2(e, m) : make_float2(m, 0.f);
                 }
+                if (!LEARNED && lt.n == 0) lam[lt.c] = 1.f / msum;
             }
         }
+        if (tid == 0) nxt[b] = sched_next(io.sched, draw, ticket, fn, pl.n_sc);
         // Prefetch the next subcarrier's receive vector (r is dead from here on).
         if (lt.active && fn < pl.n_sc)
-            load_lane_pairs<IN, AT>(io.Y, ((size_t)fn * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
+            load_lane_raw<IN, AT>(io.Y, ((size_t)fn * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
         __syncthreads();
 
-        if (LEARNED && pl.fuse == CDMIMO_FUSE_LEARNED) {
-            // Learned fusion: hidden unit kk of cluster c, z = W1[kk] . phi_c + b1[kk], contributes
-            // w2[kk] relu(z) to logit_c; phi_c = [||h_{u,c}||^2 / B_c (u < U), log10(max(alpha, 1e-6))].
-            const int Hd = learned_ok ? __ldg(&blk->hidden) : 1;
-            const int F = U + 1;
-            const float la = log10f(fmaxf(alpha, 1e-6f));
-            for (int i = tid; i < C * Hd; i += blockDim.x) {
-                const int c = i / Hd, kk = i - c * Hd;
-                const float inv_bc = 1.f / (float)tab[c].size;
-                const unsigned short* w1 = blk->W1 + (size_t)kk * F;
-                float z = __ldg(&blk->b1[kk]);
-                for (int j = 0; j < U; ++j) z = fmaf(bf16_bits_to_float(__ldg(w1 + j)), Ks[j * xs_stride + c * n_sym].x * inv_bc, z);
-                z = fmaf(bf16_bits_to_float(__ldg(w1 + U)), la, z);
-                mlp[i] = bf16_bits_to_float(__ldg(&blk->w2[kk])) * fmaxf(z, 0.f);
+        if (LEARNED) {  // lambda_c from the learned fusion (or from m, below), then a barrier
+            if (pl.fuse == CDMIMO_FUSE_LEARNED) {
+                // Learned fusion: hidden unit kk of cluster c, z = W1[kk] . phi_c + b1[kk], contributes
+                // w2[kk] relu(z) to logit_c; phi_c = [||h_{u,c}||^2 / B_c (u < U), log10(max(alpha, 1e-6))].
+                const int Hd = learned_ok ? __ldg(&blk->hidden) : 1;
+                const int F = U + 1;
+                const float la = log10f(fmaxf(alpha, 1e-6f));
+                for (int i = tid; i < C * Hd; i += blockDim.x) {
+                    const int c = i / Hd, kk = i - c * Hd;
+                    const float inv_bc = 1.f / (float)tab[c].size;
+                    const unsigned short* w1 = blk->W1 + (size_t)kk * F;
+                    float z = __ldg(&blk->b1[kk]);
+                    for (int j = 0; j < U; ++j) z = fmaf(bf16_bits_to_float(__ldg(w1 + j)), Ks[j * xs_stride + c * n_sym].x * inv_bc, z);
+                    z = fmaf(bf16_bits_to_float(__ldg(w1 + U)), la, z);
+                    mlp[i] = bf16_bits_to_float(__ldg(&blk->w2[kk])) * fmaxf(z, 0.f);
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    float lg[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int c = lane + 32 * q;
+                        if (c < C) {
+                            float s = __ldg(&blk->b2);
+                            for (int kk = 0; kk < Hd; ++kk) s += mlp[c * Hd + kk];
+                            lg[q] = s;
+                        }
+                    }
+                    float mx = fmaxf(lg[0], lg[1]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    float ex[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) ex[q] = lane + 32 * q < C ? __expf(lg[q] - mx) : 0.f;
+                    const float tot = warp_sum(ex[0] + ex[1]);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int c = lane + 32 * q;
+                        if (c < C) {
+                            lam[c] = ex[q] / tot;
+                            if (io.lam) io.lam[(size_t)f * C + c] = ex[q] / tot;
+                        }
+                    }
+                }
+            } else if (warp == 0) {
+                // Fusion weights: lambda_c proportional to 1 / sum_u m_{u,c} (a zero m marks a skipped
+                // column, whose (||h||^2 + N0/Ex)^{-1} is infinite).
+                float w[2] = {0.f, 0.f};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < C) {
+                        float s = 0.f;
+                        for (int u = 0; u < U; ++u) {
+                            const float m = Ks[u * xs_stride + c * n_sym].y;  // learned sweeps keep (e, m)
+                            s += m > 0.f ? m : __int_as_float(0x7f800000);
+                        }
+                        w[q] = 1.f / s;
+                    }
+                }
+                const float tot = warp_sum(w[0] + w[1]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < C) {
+                        const float l = (pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f)) ? 1.f / C : w[q] / tot;
+                        lam[c] = l;
+                        if (io.lam) io.lam[(size_t)f * C + c] = l;
+                    }
+                }
             }
             __syncthreads();
-            if (warp == 0) {
-                float lg[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int c = lane + 32 * q;
-                    if (c < C) {
-                        float s = __ldg(&blk->b2);
-                        for (int kk = 0; kk < Hd; ++kk) s += mlp[c * Hd + kk];
-                        lg[q] = s;
-                    }
-                }
-                float mx = fmaxf(lg[0], lg[1]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                float ex[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) ex[q] = lane + 32 * q < C ? __expf(lg[q] - mx) : 0.f;
-                const float tot = warp_sum(ex[0] + ex[1]);
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int c = lane + 32 * q;
-                    if (c < C) {
-                        lam[c] = ex[q] / tot;
-                        if (io.lam) io.lam[(size_t)f * C + c] = ex[q] / tot;
-                    }
-                }
-            }
-        } else if (warp == 0) {
-            // Fusion weights: lambda_c proportional to 1 / sum_u m_{u,c} (a zero m marks a skipped
-            // column, whose (||h||^2 + N0/Ex)^{-1} is infinite).
-            float w[2] = {0.f, 0.f};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int c = lane + 32 * q;
-                if (c < C) {
-                    float s = 0.f;
-                    for (int u = 0; u < U; ++u) {
-                        const float m = LEARNED ? Ks[u * xs_stride + c * n_sym].y : Ks[u * xs_stride + c * n_sym].x;
-                        s += m > 0.f ? m : __int_as_float(0x7f800000);
-                    }
-                    w[q] = 1.f / s;
-                }
-            }
-            const float tot = warp_sum(w[0] + w[1]);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int c = lane + 32 * q;
-                if (c < C) {
-                    const float l = (pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f)) ? 1.f / C : w[q] / tot;
-                    lam[c] = l;
-                    if (io.lam) io.lam[(size_t)f * C + c] = l;
-                }
-            }
         }
-        __syncthreads();
-
-        // Data fusion: xhat = sum_c lambda_c x_c.
+        // Data fusion: xhat = sum_c lambda_c x_c.  Plain fusion: lam holds w_c, so lambda_c = w_c / sum w
+        // (COLNORM) or 1 / C (EQUAL, or no positive weight).
+        float inv = 1.f;
+        bool equal = false;
+        if (!LEARNED) {
+            float tot = 0.f;
+            for (int c = 0; c < C; ++c) tot += lam[c];
+            equal = pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f);
+            inv = equal ? 1.f / (float)C : 1.f / tot;
+            if (io.lam && tid < C) io.lam[(size_t)f * C + tid] = equal ? inv : lam[tid] * inv;
+        }
         for (int i = tid; i < n_sym * U; i += blockDim.x) {
             const int n = i / U, u = i - n * U;
             float2 acc = make_float2(0.f, 0.f);
             for (int c = 0; c < C; ++c) {
-                const float l = lam[c];
+                const float l = LEARNED ? lam[c] : (equal ? inv : lam[c] * inv);
                 const float2 x = Xs[u * xs_stride + c * n_sym + n];
                 acc.x = fmaf(l, x.x, acc.x);
                 acc.y = fmaf(l, x.y, acc.y);
@@ -479,8 +555,13 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             }
             io.Xhat[((size_t)f * n_sym + n) * U + u] = make_float2(acc.x * out_scale, acc.y * out_scale);
         }
-        __syncthreads();
+        // No barrier here: the next writes of Xs, Ks and lam come after the next acquire's barriers,
+        // and the copy into this iteration's channel buffer is issued after the barrier above.
+        ++done;
+        f = fn;
+        fn = nxt[b];
     }
+    sched_finish(io.sched, done, pl.n_sc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -498,7 +579,8 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
     float* Qs = reinterpret_cast<float*>(smem + pl.off_K);    // [U][x_stride] p_{u,c}^2 per tile
     float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);  // [n_sym][U | 1] (odd stride: no bank conflicts)
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);  // [2]
+    int* nxt = reinterpret_cast<int*>(smem + pl.off_bar + 16);       // [2] schedule hand-off
 
     const int tid = threadIdx.x;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
@@ -536,9 +618,12 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
         sv[q] = (i < n_s && f < pl.n_sc) ? __ldg(io.S + (size_t)f * n_s + i) : make_float2(0.f, 0.f);
     }
 
-    for (int k = 0; f < pl.n_sc; f += gridDim.x, ++k) {
+    int fn = f + (int)gridDim.x;  // this CTA's next subcarrier
+    int done = 0;
+    for (int k = 0; f < pl.n_sc; ++k) {
         const int b = k & 1;
-        const int fn = f + gridDim.x;
+        const bool draw = fn < pl.n_sc;
+        const unsigned ticket = sched_draw(io.sched, draw);
         if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
 #pragma unroll
         for (int q = 0; q < kSPrefetch; ++q) {
@@ -549,8 +634,10 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
             }
         }
         if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
-                                 fn + (int)gridDim.x < pl.n_sc))
-            return;
+                                 io.sched != nullptr || fn + (int)gridDim.x < pl.n_sc)) {
+            if (pl.bulk && fn < pl.n_sc && tid == 0) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+            break;
+        }
         // The next subcarrier's s (this one's is in shared memory now).
 #pragma unroll
         for (int q = 0; q < kSPrefetch; ++q) {
@@ -613,8 +700,13 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_pp_kernel(const CdPlan pl, const
                 if (col + 1 < ct.size) out[col + 1] = make_float2(x[i].y * sc, x[i].w * sc);
             }
         }
+        if (tid == 0) nxt[b] = sched_next(io.sched, draw, ticket, fn, pl.n_sc);
         __syncthreads();
+        ++done;
+        f = fn;
+        fn = nxt[b];
     }
+    sched_finish(io.sched, done, pl.n_sc);
 }
 
 }  // namespace cdmimo

@@ -121,6 +121,21 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     pl->n_lanes = lane;
     pl->n_tiles = p->C * p->n_sym;
     if (pl->n_lanes > kMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
+    // Warps: with four or more, a multiple of four with the tiles spread evenly over them, so that
+    // each of the SM's four warp schedulers holds the same number of this CTA's warps and the CTA's
+    // barriers do not wait on one overloaded scheduler (two 7-warp CTAs on one SM split 4/4/3/3 or
+    // worse; two 8-warp CTAs split 4/4/4/4).
+    {
+        int Amax = 1;
+        for (int c = 0; c < p->C; ++c) Amax = std::max(Amax, pl->cl[c].A);
+        const int w_min = (pl->n_lanes + 31) / 32;
+        pl->lpw = 32;
+        if (w_min >= 4) {
+            const int W = (w_min + 3) / 4 * 4;
+            pl->lpw = ((pl->n_lanes + W - 1) / W + Amax - 1) / Amax * Amax;
+        }
+        pl->threads = std::max(64, (pl->n_lanes + pl->lpw - 1) / pl->lpw * 32);
+    }
 
     const unsigned U = p->U, C = p->C;
     const unsigned xs = (unsigned)pl->n_tiles | 1u;
@@ -173,11 +188,11 @@ int build_plan(const cdmimo_params* p, int P, bool detect, const void* H, CdPlan
     }
     pl->off_tab = o;
     o = align16(o + C * (unsigned)sizeof(ClusterTile));
-    pl->off_bar = o;
-    o = align16(o + 16u);
+    pl->off_bar = o;  // two mbarriers, then the two schedule hand-off slots
+    o = align16(o + 32u);
     pl->smem_bytes = o;
     if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
-    if (pl->packed && !detect && p->n_sym * p->U > kSPrefetch * std::max(64, (pl->n_lanes + 31) / 32 * 32))
+    if (pl->packed && !detect && p->n_sym * p->U > kSPrefetch * pl->threads)
         pl->packed = 0;  // the packed precoder prefetches at most kSPrefetch entries of s per thread
 
     return CDMIMO_OK;
@@ -198,7 +213,7 @@ int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
     return rc;
 }
 
-int threads_for(const CdPlan& pl) { return std::max(64, (pl.n_lanes + 31) / 32 * 32); }
+int threads_for(const CdPlan& pl) { return pl.threads; }
 
 // Per-kernel attributes: dynamic shared memory above 48 KB, and the largest shared-memory carveout
 // so that several CTAs of one kernel share an SM.
@@ -309,7 +324,7 @@ int streaming_launch(const cdmimo_params* p, int op, const void* H, const void* 
                      cudaStream_t s);
 
 int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc,
-                float* lam, cudaStream_t s)
+                float* lam, unsigned* sched, cudaStream_t s)
 {
     if (int rc = validate(p)) return rc;
     if (int rc = check_detect_ptrs(p, H, Y, N0, Xhat)) return rc;
@@ -326,7 +341,7 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
     }
     if (pl.learned && !pl.packed) return CDMIMO_ERR_UNSUPPORTED;  // learned sweeps: uniform B_c <= 64
     DetectIO io{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), reinterpret_cast<float2*>(Xc),
-                lam, p->learned};
+                lam, p->learned, sched};
     switch (p->in_dtype) {
     case CDMIMO_C64: return dispatch_detect<CDMIMO_C64>(pl, io, s);
     case CDMIMO_C16F: return dispatch_detect<CDMIMO_C16F>(pl, io, s);
@@ -335,7 +350,7 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
     return CDMIMO_ERR_INVALID_ARG;
 }
 
-int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl, cudaStream_t s)
+int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl, unsigned* sched, cudaStream_t s)
 {
     if (int rc = validate(p)) return rc;
     if (p->n_sc == 0) return CDMIMO_OK;
@@ -347,7 +362,7 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
         if (rc != CDMIMO_ERR_UNSUPPORTED) return rc;
         return streaming_launch(p, CDMIMO_OP_PRECODE, H, S, nullptr, Xdl, s);
     }
-    PrecodeIO io{H, reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
+    PrecodeIO io{H, reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl), sched};
     switch (p->in_dtype) {
     case CDMIMO_C64: return dispatch_precode<CDMIMO_C64>(pl, io, s);
     case CDMIMO_C16F: return dispatch_precode<CDMIMO_C16F>(pl, io, s);
@@ -357,6 +372,21 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
 }
 
 size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Bytes of the optional device workspace of cdmimo_detect / cdmimo_precode: the three schedule
+// counters, padded to one 256-byte line.
+constexpr size_t kSchedBytes = 256;
+
+// The schedule counters in a caller's workspace: NULL -> static schedule; else it must be 16-byte
+// aligned and hold kSchedBytes.
+int sched_from_workspace(void* ws, size_t ws_bytes, unsigned** sched)
+{
+    *sched = nullptr;
+    if (!ws) return CDMIMO_OK;
+    if (!aligned(ws, 16) || ws_bytes < kSchedBytes) return CDMIMO_ERR_WORKSPACE;
+    *sched = static_cast<unsigned*>(ws);
+    return CDMIMO_OK;
+}
 
 }  // namespace
 
@@ -706,17 +736,17 @@ extern "C" {
 int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc_opt,
                   float* lambda_opt, void* workspace, size_t ws_bytes, void* stream)
 {
-    (void)workspace;
-    (void)ws_bytes;
-    return detect_impl(p, H, Y, N0, Xhat, Xc_opt, lambda_opt, static_cast<cudaStream_t>(stream));
+    unsigned* sched;
+    if (int rc = sched_from_workspace(workspace, ws_bytes, &sched)) return rc;
+    return detect_impl(p, H, Y, N0, Xhat, Xc_opt, lambda_opt, sched, static_cast<cudaStream_t>(stream));
 }
 
 int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* Xdl, void* workspace, size_t ws_bytes,
                    void* stream)
 {
-    (void)workspace;
-    (void)ws_bytes;
-    return precode_impl(p, H, S, Xdl, static_cast<cudaStream_t>(stream));
+    unsigned* sched;
+    if (int rc = sched_from_workspace(workspace, ws_bytes, &sched)) return rc;
+    return precode_impl(p, H, S, Xdl, sched, static_cast<cudaStream_t>(stream));
 }
 
 int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* w, int weights_are_lambda, void* Xhat,
@@ -737,7 +767,7 @@ size_t cdmimo_workspace_size(const cdmimo_params* p, int op)
 {
     (void)op;
     (void)p;
-    return 0;
+    return kSchedBytes;
 }
 
 size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op)
@@ -749,10 +779,11 @@ size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op)
         size_t v = hb + round256((size_t)p->n_sc * p->n_sym * p->B * eb) + round256((size_t)p->n_sc * 4) +
                    round256((size_t)p->n_sc * p->n_sym * p->U * 8);
         if (p->in_dtype != CDMIMO_C64) v += 2 * round256((size_t)p->n_sc * 4);
-        return v;
+        return v + kSchedBytes;
     }
     if (op == CDMIMO_OP_PRECODE)
-        return hb + round256((size_t)p->n_sc * p->n_sym * p->U * 8) + round256((size_t)p->n_sc * p->n_sym * p->B * 8);
+        return hb + round256((size_t)p->n_sc * p->n_sym * p->U * 8) + round256((size_t)p->n_sc * p->n_sym * p->B * 8) +
+               kSchedBytes;
     return 0;
 }
 
@@ -774,6 +805,9 @@ int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y
     char* dY = dH + round256(hb);
     char* dN = dY + round256(yb);
     char* dX = dN + round256(nb);
+    // schedule counters: the last kSchedBytes of the workspace, zeroed by every call
+    unsigned* sched = reinterpret_cast<unsigned*>(w + need - kSchedBytes);
+    if (cudaMemsetAsync(sched, 0, 16, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     cdmimo_params q = *p;
     if (cudaMemcpyAsync(dH, H_host, hb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     if (cudaMemcpyAsync(dY, Y_host, yb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
@@ -786,7 +820,8 @@ int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y
         q.h_scale = reinterpret_cast<const float*>(dhs);
         q.y_scale = reinterpret_cast<const float*>(dys);
     }
-    if (int rc = detect_impl(&q, dH, dY, reinterpret_cast<const float*>(dN), dX, nullptr, nullptr, s)) return rc;
+    if (int rc = detect_impl(&q, dH, dY, reinterpret_cast<const float*>(dN), dX, nullptr, nullptr, sched, s))
+        return rc;
     if (cudaMemcpyAsync(Xhat_host, dX, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     return CDMIMO_OK;
 }
@@ -805,9 +840,11 @@ int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* 
     char* dH = static_cast<char*>(dev_ws);
     char* dS = dH + round256(hb);
     char* dX = dS + round256(sb);
+    unsigned* sched = reinterpret_cast<unsigned*>(static_cast<char*>(dev_ws) + need - kSchedBytes);
+    if (cudaMemsetAsync(sched, 0, 16, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     if (cudaMemcpyAsync(dH, H_host, hb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     if (cudaMemcpyAsync(dS, S_host, sb, cudaMemcpyHostToDevice, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
-    if (int rc = precode_impl(p, dH, dS, dX, s)) return rc;
+    if (int rc = precode_impl(p, dH, dS, dX, sched, s)) return rc;
     if (cudaMemcpyAsync(Xdl_host, dX, xb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CDMIMO_ERR_CUDA;
     return CDMIMO_OK;
 }

@@ -31,6 +31,8 @@ struct CdPlan {
     int A_uniform;    // A shared by every cluster (0 if clusters differ); selects the kernel variant
     int h_entries;    // complex entries of the shared-memory channel region
     int n_lanes;      // lanes that run CD tiles: n_sym * sum A_c
+    int lpw;          // tile lanes per warp (whole tiles; the warp's other lanes idle in the sweeps)
+    int threads;      // threads per CTA
     int n_tiles;      // C * n_sym
     int bulk;         // 1: channel rows arrive by cp.async.bulk (c64: every B_c even; 16-bit storage,
                       //    packed kernels only: every B_c a multiple of 4; H 16-byte aligned)
@@ -57,12 +59,14 @@ struct DetectIO {
     float2* Xc;
     float* lam;
     const void* learned;
+    unsigned* sched;  // [3] dynamic-schedule counters in the caller's workspace, or nullptr (static)
 };
 
 struct PrecodeIO {
     const void* H;
     const float2* S;
     float2* Xdl;
+    unsigned* sched;
 };
 
 }  // namespace cdmimo

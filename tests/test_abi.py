@@ -98,9 +98,20 @@ def test_host_workspace_sizes():
     need = L.cdmimo_host_workspace_size(ctypes.byref(p), cdmimo.OP_DETECT)
     assert need >= 1200 * 16 * 256 * 8 + 1200 * 14 * 256 * 8 + 1200 * 4 + 1200 * 14 * 16 * 8
     assert need % 256 == 0
-    assert L.cdmimo_workspace_size(ctypes.byref(p), cdmimo.OP_DETECT) == 0
+    assert L.cdmimo_workspace_size(ctypes.byref(p), cdmimo.OP_DETECT) == 256
+    assert L.cdmimo_workspace_size(ctypes.byref(p), cdmimo.OP_PRECODE) == 256
     assert L.cdmimo_detect_host(ctypes.byref(p), ctypes.c_void_p(1), ctypes.c_void_p(1), ctypes.c_void_p(1),
                                 ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None) == cdmimo.ERR_WORKSPACE
+
+
+def test_schedule_workspace_validation():
+    # misaligned or short schedule workspaces are rejected before anything touches the device
+    L = cdmimo.lib()
+    p, keep = cdmimo.make_params(8, 14, 256, 16, [32] * 8, 3)
+    one = ctypes.c_void_p(256)
+    for ws, nb in ((ctypes.c_void_p(8), 256), (ctypes.c_void_p(4096), 255)):
+        assert L.cdmimo_detect(ctypes.byref(p), one, one, one, one, None, None, ws, nb, None) == cdmimo.ERR_WORKSPACE
+        assert L.cdmimo_precode(ctypes.byref(p), one, one, one, ws, nb, None) == cdmimo.ERR_WORKSPACE
 
 
 def test_learned_block_layout_and_param_count():
