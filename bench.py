@@ -159,8 +159,8 @@ def run_cuda(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        cdmimo.detect(H, Y, N0, CS, K, out=Xhat, stream=stream)
-        cdmimo.precode(Hd, S, CS, K, out=Xdl, stream=stream)
+        cdmimo.detect(H, Y, N0, CS, K, out=Xhat, stream=stream, form=args.form)
+        cdmimo.precode(Hd, S, CS, K, out=Xdl, stream=stream, form=args.form)
 
     for _ in range(args.warmup):
         step()
@@ -179,9 +179,9 @@ def run_cuda(args, rank, world, local_rank):
     for i in range(args.steps):
         e = ev[i]
         e[0].record(stream)
-        cdmimo.detect(H, Y, N0, CS, K, out=Xhat, stream=stream)
+        cdmimo.detect(H, Y, N0, CS, K, out=Xhat, stream=stream, form=args.form)
         e[1].record(stream)
-        cdmimo.precode(Hd, S, CS, K, out=Xdl, stream=stream)
+        cdmimo.precode(Hd, S, CS, K, out=Xdl, stream=stream, form=args.form)
         e[2].record(stream)
         flush.fill_(float(i & 7))  # L2 flush between timed steps, outside the brackets
     torch.cuda.synchronize()
@@ -523,6 +523,29 @@ def run_config5(args, dev):
                      training={k: v for k, v in info.items() if k != "loss"}, gpu_launches=1 * args.steps)
 
 
+def run_profile(args):
+    """Three untimed calls of one direction on the step's workload (the launches an ncu capture of
+    this command selects with -k / -s / -c)."""
+    import torch
+
+    from paper_1902_08653_gb300 import cdmimo
+    from paper_1902_08653_gb300 import workload as wl
+
+    dev = torch.device("cuda:0")
+    up = wl.uplink(20190222, N_SC, N_SYM, B, U, snr_db=wl.sweep_snr(N_SC), M=M)
+    t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
+    H, Y, S = t(up["H"]), t(up["Y"]), t(up["X"])
+    N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
+    for _ in range(3):
+        if args.profile == "detect":
+            cdmimo.detect(H, Y, N0, CS, K, form=args.form)
+        else:
+            cdmimo.precode(H, S, CS, K, form=args.form)
+    torch.cuda.synchronize()
+    assert cdmimo.device_status(clear=True) == 0
+    print("ok", args.profile, args.form)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,6 +555,9 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2 (default): UL detect + DL precode bench line; 1, 3, 4, 5: the other configurations")
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
+    ap.add_argument("--profile", choices=["detect", "precode"], default=None,
+                    help="untimed: three cdmimo_detect or cdmimo_precode calls on the step's workload, for ncu")
+    ap.add_argument("--form", choices=["auto", "residual", "gram"], default="auto", help="CD evaluation form")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -540,6 +566,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.profile:
+        run_profile(args)
         return
     if args.config != 2:
         import torch

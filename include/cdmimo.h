@@ -67,6 +67,22 @@ typedef enum { CDMIMO_C64 = 0, CDMIMO_C16F = 1, CDMIMO_C16BF = 2 } cdmimo_dtype;
 typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARNED = 2 } cdmimo_fuse_rule;
 
 /*
+ * Evaluation form of the CD sweeps (both give the iterates of Algorithms 1 and 2; they differ in
+ * rounding only).
+ *   RESIDUAL  as the algorithms are written: a running residual r = y_c - H_c x (uplink) or the
+ *             beamformer x_c itself (downlink) in registers, 2 U B_c complex MACs per sweep and vector.
+ *   GRAM      through G_c = H_c^H H_c, formed once per subcarrier and shared by its n_sym symbols:
+ *             x_u <- m_u (z_u - sum_{v != u} G_uv x_v) with z = H_c^H y_c (uplink) and
+ *             w_u <- p_u^2 (s_u - sum_{v != u} G_uv w_v), x_c = H_c w (downlink); U^2 complex MACs per
+ *             sweep and vector plus U B_c (z or H_c w) and U^2 B_c / n_sym (G_c).  Requires U <= 16,
+ *             equal lanes per cluster tile (8 < B_c <= 64 for all clusters, or all B_c <= 16, ...:
+ *             the packed-kernel shapes) and no learned block; otherwise CDMIMO_ERR_UNSUPPORTED.
+ *   AUTO      GRAM where it applies, every B_c >= 2 U (so G_c + (N0/Ex) I stays well conditioned
+ *             in FP32) and it needs fewer complex MACs; else RESIDUAL.
+ */
+typedef enum { CDMIMO_FORM_AUTO = 0, CDMIMO_FORM_RESIDUAL = 1, CDMIMO_FORM_GRAM = 2 } cdmimo_form;
+
+/*
  * Problem description shared by detection and precoding.
  *   n_sc, n_sym, B, U, C  dimensions (n_sc >= 0, others >= 1; C <= 64, U <= 64).
  *   cluster_size  HOST array [C] of B_c (each >= 1, sum == B).  Read during the call only.
@@ -84,6 +100,7 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *                 CDMIMO_DEV_BAD_LEARNED and gives NaN output) and fuse may be any rule;
  *                 fuse == CDMIMO_FUSE_LEARNED requires a block.  Learned detection needs equal
  *                 cluster sizes of at most 64 antennas and 64-bit complex storage.
+ *   form          cdmimo_form (0 = AUTO).
  */
 typedef struct {
     int n_sc, n_sym, B, U, C;
@@ -96,6 +113,7 @@ typedef struct {
     const float* h_scale;
     const float* y_scale;
     const void* learned;
+    int form;
 } cdmimo_params;
 
 /* ---------------------------------------------------------------------------------------------- */

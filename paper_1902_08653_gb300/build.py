@@ -1,10 +1,12 @@
 """Builds the CUDA library (libcdmimo.so) in-tree for sm_103a with nvcc.
 
-The library is one translation unit (kernels are header templates included by the C-ABI file),
-compiled with a single -gencode so the build stays well under a minute.
+Each csrc/*.cu file is one translation unit (kernels are header templates instantiated where they
+are launched); the units compile in parallel with a single -gencode and are linked into one
+shared library, so the build stays around a minute.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import glob
 import os
 import shutil
@@ -41,19 +43,39 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
+def _run(cmd):
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
+    return res.stdout + res.stderr
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and up_to_date():
         return OUT
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    tmp = OUT + f".{os.getpid()}.tmp"
-    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-I", CSRC, *extra, "-o", tmp, *sources()]
+    tag = f"{os.getpid()}"
+    common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+              *extra]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
-    os.replace(tmp, OUT)
+        common.insert(1, "-Xptxas=-v")
+    objs, cmds = [], []
+    for src in sources():
+        obj = os.path.join(os.path.dirname(OUT), os.path.basename(src)[:-3] + f".{tag}.o")
+        objs.append(obj)
+        cmds.append([*common, "-c", "-o", obj, src])
+    try:
+        with cf.ThreadPoolExecutor(len(cmds)) as ex:
+            logs = list(ex.map(_run, cmds))
+        tmp = OUT + f".{tag}.tmp"
+        _run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, OUT)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+    if verbose:
+        print("".join(logs))
     return OUT
 
 

@@ -33,6 +33,7 @@ LEARNED_BLOCK_BYTES = 4 * 4 + 16 * 4 * 2 + 64 * 4 + 4 * 4 + 64 * 65 * 2 + 64 * 2
 
 C64, C16F, C16BF = 0, 1, 2
 FUSE = {"equal": 0, "colnorm": 1, "learned": 2}
+FORM = {"auto": 0, "residual": 1, "gram": 2}
 OP_DETECT, OP_PRECODE = 0, 1
 
 
@@ -46,7 +47,8 @@ class Params(ctypes.Structure):
     _fields_ = [("n_sc", ctypes.c_int), ("n_sym", ctypes.c_int), ("B", ctypes.c_int), ("U", ctypes.c_int),
                 ("C", ctypes.c_int), ("cluster_size", ctypes.POINTER(ctypes.c_int)), ("K", ctypes.c_int),
                 ("Ex", ctypes.c_float), ("fuse", ctypes.c_int), ("rho", ctypes.c_float), ("in_dtype", ctypes.c_int),
-                ("h_scale", ctypes.c_void_p), ("y_scale", ctypes.c_void_p), ("learned", ctypes.c_void_p)]
+                ("h_scale", ctypes.c_void_p), ("y_scale", ctypes.c_void_p), ("learned", ctypes.c_void_p),
+                ("form", ctypes.c_int)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -156,14 +158,15 @@ def _need(t, name, dev=True):
 
 
 def make_params(n_sc, n_sym, B, U, cluster_size, K, *, Ex=1.0, fuse="colnorm", rho=1.0, in_dtype=C64,
-                h_scale=None, y_scale=None, learned=None):
+                h_scale=None, y_scale=None, learned=None, form="auto"):
     """Build the C parameter block.  Returns (Params, keepalive) — keep both alive during the call."""
     cs = (ctypes.c_int * len(cluster_size))(*[int(v) for v in cluster_size])
     p = Params(int(n_sc), int(n_sym), int(B), int(U), len(cluster_size), ctypes.cast(cs, ctypes.POINTER(ctypes.c_int)),
                int(K), float(Ex), FUSE[fuse] if isinstance(fuse, str) else int(fuse), float(rho), int(in_dtype),
                h_scale.data_ptr() if h_scale is not None else None,
                y_scale.data_ptr() if y_scale is not None else None,
-               learned.data_ptr() if learned is not None else None)
+               learned.data_ptr() if learned is not None else None,
+               FORM[form] if isinstance(form, str) else int(form))
     return p, cs
 
 
@@ -192,10 +195,11 @@ def _workspace_args(workspace, device, stream):
 
 
 def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y_scale=None, learned=None,
-           out=None, Xc=None, lam=None, workspace=None, stream=None):
+           out=None, Xc=None, lam=None, workspace=None, stream=None, form="auto"):
     """cdmimo_detect: Algorithm 1 + fusion.  Returns Xhat [n_sc, n_sym, U] complex64.
     workspace: None = this binding's per-stream schedule workspace, False = static schedule, or a
-    zero-filled device tensor of cdmimo_workspace_size bytes."""
+    zero-filled device tensor of cdmimo_workspace_size bytes.  form: "auto", "residual" or "gram"
+    (cdmimo_form)."""
     _need(H, "H")
     _need(Y, "Y")
     _need(N0, "N0")
@@ -210,7 +214,7 @@ def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y
         out = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=H.device)
     _need(out, "out")
     p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse=fuse, in_dtype=dt, h_scale=h_scale,
-                          y_scale=y_scale, learned=learned)
+                          y_scale=y_scale, learned=learned, form=form)
     ws, wsb = _workspace_args(workspace, H.device, stream)
     rc = lib().cdmimo_detect(ctypes.byref(p), _ptr(H), _ptr(Y), _ptr(N0), _ptr(out), _ptr(Xc), _ptr(lam),
                              ws, wsb, _stream(stream))
@@ -218,7 +222,7 @@ def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y
     return out
 
 
-def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=None):
+def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=None, form="auto"):
     """cdmimo_precode: Algorithm 2 + per-cluster normalization.  Returns Xdl [n_sc, n_sym, B] complex64.
     workspace as for detect."""
     _need(H, "H")
@@ -231,7 +235,7 @@ def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=
     if out is None:
         out = torch.empty((n_sc, n_sym, B), dtype=torch.complex64, device=H.device)
     _need(out, "out")
-    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, rho=rho, in_dtype=dt)
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, rho=rho, in_dtype=dt, form=form)
     ws, wsb = _workspace_args(workspace, H.device, stream)
     rc = lib().cdmimo_precode(ctypes.byref(p), _ptr(H), _ptr(S), _ptr(out), ws, wsb, _stream(stream))
     _check("cdmimo_precode", rc)

@@ -489,7 +489,7 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
 // ---------------------------------------------------------------------------------------------
 // Standalone fusion (Sec. III): Xhat[f][n][u] = sum_c lambda_c Xc[f][c][n][u].
 // ---------------------------------------------------------------------------------------------
-__global__ void fuse_kernel(int n_sc, int n_sym, int U, int C, const float2* __restrict__ Xc,
+static __global__ void fuse_kernel(int n_sc, int n_sym, int U, int C, const float2* __restrict__ Xc,
                             const float* __restrict__ w, int is_lambda, float2* __restrict__ Xhat)
 {
     const size_t total = (size_t)n_sc * n_sym * U;

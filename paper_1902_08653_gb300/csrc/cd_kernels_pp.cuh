@@ -111,11 +111,7 @@ __device__ __forceinline__ void stage_H_converting(const CdPlan& pl, const Clust
     }
 }
 
-// This lane's antenna pairs q = i*AT + a of a length-`size` vector, pair-planar.  Each half is passed
-// through one packed add, so the values start out in the aligned register pairs that the packed FMAs
-// of the CD loop produce; the loop-carried vector then needs no register moves (measured: it removes
-// a third of the uplink kernel's instructions).
-// The lane's entries of one vector as loaded: (re_j, im_j, re_{j+1}, im_{j+1}) per pair.
+// The lane's antenna pairs q = i*AT + a of a length-`size` vector as loaded: (re_j, im_j, re_{j+1}, im_{j+1}) per pair.
 template <int IN, int AT>
 __device__ __forceinline__ void load_lane_raw(const void* V, size_t base, int size, int a, float4 (&v)[kPairs])
 {
@@ -130,8 +126,9 @@ __device__ __forceinline__ void load_lane_raw(const void* V, size_t base, int si
 }
 
 // To the pair-planar register layout (re_j, re_{j+1}, im_j, im_{j+1}).  The packed adds (of zero)
-// write each pair into an aligned register pair, so the sweeps' packed FMAs need no moves.  Done
-// just before the sweeps, so a prefetch issued one subcarrier earlier is not waited for sooner.
+// write each pair into an aligned register pair, so the loop-carried vector needs no register moves
+// in the sweeps' packed FMAs (measured: a third fewer uplink instructions).  Done just before the
+// sweeps, so a prefetch issued one subcarrier earlier is not waited for sooner.
 __device__ __forceinline__ void raw_to_pairs(float4 (&v)[kPairs])
 {
     const float2 z = make_float2(0.f, 0.f);
@@ -257,6 +254,39 @@ __device__ __forceinline__ void sched_finish(unsigned* sched, int done, int n_sc
         sched[1] = 0u;
         sched[2] = 0u;
         __threadfence();
+    }
+}
+
+// Data fusion of one subcarrier (Sec. III): xhat = sum_c lambda_c x_c from the per-tile estimates
+// Xs[u][c n_sym + n].  FINAL: lam holds lambda_c.  Otherwise lam holds w_c = 1 / sum_u m_{u,c} and
+// lambda_c = w_c / sum_c' w_c' (COLNORM), or 1 / C (EQUAL, or no positive weight).  Optional
+// outputs: the per-cluster estimates io.Xc and the weights io.lam (plain rules; the learned fusion
+// writes its own).
+template <bool FINAL>
+__device__ __forceinline__ void fuse_subcarrier(const CdPlan& pl, const DetectIO& io, int f, const float* lam,
+                                                const float2* Xs, uint32_t xs_stride, float out_scale)
+{
+    const int tid = threadIdx.x, C = pl.C, U = pl.U, n_sym = pl.n_sym;
+    float inv = 1.f;
+    bool equal = false;
+    if (!FINAL) {
+        float tot = 0.f;
+        for (int c = 0; c < C; ++c) tot += lam[c];
+        equal = pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f);
+        inv = equal ? 1.f / (float)C : 1.f / tot;
+        if (io.lam && tid < C) io.lam[(size_t)f * C + tid] = equal ? inv : lam[tid] * inv;
+    }
+    for (int i = tid; i < n_sym * U; i += blockDim.x) {
+        const int n = i / U, u = i - n * U;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int c = 0; c < C; ++c) {
+            const float l = FINAL ? lam[c] : (equal ? inv : lam[c] * inv);
+            const float2 x = Xs[u * xs_stride + c * n_sym + n];
+            acc.x = fmaf(l, x.x, acc.x);
+            acc.y = fmaf(l, x.y, acc.y);
+            if (io.Xc) io.Xc[(((size_t)f * C + c) * n_sym + n) * U + u] = make_float2(x.x * out_scale, x.y * out_scale);
+        }
+        io.Xhat[((size_t)f * n_sym + n) * U + u] = make_float2(acc.x * out_scale, acc.y * out_scale);
     }
 }
 
@@ -532,29 +562,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             }
             __syncthreads();
         }
-        // Data fusion: xhat = sum_c lambda_c x_c.  Plain fusion: lam holds w_c, so lambda_c = w_c / sum w
-        // (COLNORM) or 1 / C (EQUAL, or no positive weight).
-        float inv = 1.f;
-        bool equal = false;
-        if (!LEARNED) {
-            float tot = 0.f;
-            for (int c = 0; c < C; ++c) tot += lam[c];
-            equal = pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f);
-            inv = equal ? 1.f / (float)C : 1.f / tot;
-            if (io.lam && tid < C) io.lam[(size_t)f * C + tid] = equal ? inv : lam[tid] * inv;
-        }
-        for (int i = tid; i < n_sym * U; i += blockDim.x) {
-            const int n = i / U, u = i - n * U;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int c = 0; c < C; ++c) {
-                const float l = LEARNED ? lam[c] : (equal ? inv : lam[c] * inv);
-                const float2 x = Xs[u * xs_stride + c * n_sym + n];
-                acc.x = fmaf(l, x.x, acc.x);
-                acc.y = fmaf(l, x.y, acc.y);
-                if (io.Xc) io.Xc[(((size_t)f * C + c) * n_sym + n) * U + u] = make_float2(x.x * out_scale, x.y * out_scale);
-            }
-            io.Xhat[((size_t)f * n_sym + n) * U + u] = make_float2(acc.x * out_scale, acc.y * out_scale);
-        }
+        fuse_subcarrier<LEARNED>(pl, io, f, lam, Xs, xs_stride, out_scale);
         // No barrier here: the next writes of Xs, Ks and lam come after the next acquire's barriers,
         // and the copy into this iteration's channel buffer is issued after the barrier above.
         ++done;

@@ -17,6 +17,7 @@
 #include "synth_kernels.cuh"
 #include "cdmimo.h"
 #include "plan.h"
+#include "launch.h"
 
 using namespace cdmimo;
 
@@ -62,6 +63,8 @@ int validate(const cdmimo_params* p)
     if (p->in_dtype != CDMIMO_C64 && p->in_dtype != CDMIMO_C16F && p->in_dtype != CDMIMO_C16BF)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->fuse != CDMIMO_FUSE_EQUAL && p->fuse != CDMIMO_FUSE_COLNORM && p->fuse != CDMIMO_FUSE_LEARNED)
+        return CDMIMO_ERR_INVALID_ARG;
+    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_RESIDUAL && p->form != CDMIMO_FORM_GRAM)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
     if (!p->cluster_size || p->C > CDMIMO_MAX_CLUSTERS) return CDMIMO_ERR_BAD_PARTITION;
@@ -213,36 +216,69 @@ int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
     return rc;
 }
 
-int threads_for(const CdPlan& pl) { return pl.threads; }
 
-// Per-kernel attributes: dynamic shared memory above 48 KB, and the largest shared-memory carveout
-// so that several CTAs of one kernel share an SM.
-template <typename Kern>
-int launch_cd(Kern k, const CdPlan& pl, cudaStream_t s)
+
+// Gram-form plan: the packed plan's cluster tiles, channel buffers and staging, then the Gram
+// regions (rows of G_c, energies, per-tile z / x or w, s).  UNSUPPORTED where the form does not
+// apply; with auto_rules also where a cluster has B_c < 2U (conditioning) or where the form would
+// need as many complex MACs as the residual form.
+int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool auto_rules, CdPlan* pl)
 {
-    (void)s;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-        return CDMIMO_ERR_CUDA;
-    if (pl.smem_bytes > 48u * 1024u) {
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_bytes) != cudaSuccess)
-            return CDMIMO_ERR_CUDA;
+    if (p->U > 16 || (detect && p->learned)) return CDMIMO_ERR_UNSUPPORTED;
+    if (int rc = build_plan(p, 16, detect, H, pl)) return rc;
+    if (!pl->packed) return CDMIMO_ERR_UNSUPPORTED;
+    const long U = p->U, n_sym = p->n_sym, K = p->K;
+    if (auto_rules) {
+        long gram = 0, resid = 0;  // complex MACs per subcarrier
+        for (int c = 0; c < p->C; ++c) {
+            const long Bc = p->cluster_size[c];
+            if (Bc < 2 * U) return CDMIMO_ERR_UNSUPPORTED;
+            gram += U * U * Bc + n_sym * U * Bc + n_sym * K * U * U;
+            resid += 2 * n_sym * K * U * Bc;
+        }
+        if (gram >= resid) return CDMIMO_ERR_UNSUPPORTED;
     }
+    const int UT = p->U <= 8 ? 8 : 16;
+    const int AT = pl->A_uniform;
+    const int threads = std::max({gram_phase_threads(p->C, p->n_sym, AT), gram_phase_threads(p->C, p->U, AT),
+                                  gram_phase_threads(p->C, p->n_sym, 1)});
+    if (threads > kMaxSpecializedThreads) return CDMIMO_ERR_UNSUPPORTED;
+    if (!detect && p->n_sym * p->U > kSPrefetch * threads) return CDMIMO_ERR_UNSUPPORTED;
+    const unsigned C = p->C, xs = (unsigned)pl->n_tiles | 1u, UTu = (unsigned)UT;
+    unsigned o = pl->off_K;  // end of the channel buffers / staging of the packed layout
+    pl->off_G = o;
+    o = align16(o + C * UTu * UTu * 8u);
+    pl->off_E = o;
+    o = align16(o + C * UTu * 4u);
+    pl->off_X = o;  // z / x (uplink) or w (downlink) per tile; UT rows (padded steps read z rows >= U)
+    o = align16(o + UTu * xs * 8u);
+    if (!detect) {  // s rows, plus UT zero entries past the last row for the padded steps
+        pl->off_S = o;
+        o = align16(o + ((unsigned)n_sym * ((unsigned)U | 1u) + UTu) * 8u);
+    }
+    pl->off_lam = o;
+    o = align16(o + C * 4u);
+    pl->off_tab = o;
+    o = align16(o + C * (unsigned)sizeof(ClusterTile));
+    pl->off_bar = o;
+    o = align16(o + 32u);
+    pl->smem_bytes = o;
+    if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    pl->gram = 1;
+    pl->UT = UT;
+    pl->threads = threads;
     return CDMIMO_OK;
 }
 
-// Grid: one CTA per subcarrier for the scalar kernels; for the persistent packed kernels, as many
-// CTAs as fit on the device at once (they walk the subcarriers with a grid stride).
-template <typename Kern>
-int grid_for(Kern k, const CdPlan& pl)
+// The plan for p->form: GRAM where requested, or (AUTO) where the Gram form applies and pays,
+// else the residual form.
+int plan_for(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
 {
-    if (!pl.packed) return pl.n_sc;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return pl.n_sc;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads_for(pl), pl.smem_bytes) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    return std::max(1, std::min(pl.n_sc, sms * per_sm));
+    if (p->form != CDMIMO_FORM_RESIDUAL) {
+        const int rc = build_gram_plan(p, detect, H, p->form == CDMIMO_FORM_AUTO, pl);
+        if (rc == CDMIMO_OK || p->form == CDMIMO_FORM_GRAM) return rc;
+    }
+    return plan_auto(p, detect, H, pl);
 }
 
 template <int P, int IN, int AT>
@@ -255,7 +291,7 @@ int launch_detect_t(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
     } else {
         k = cd_detect_kernel<P, IN, 0>;
     }
-    if (int rc = launch_cd(k, pl, s)) return rc;
+    if (int rc = launch_cd(k, pl)) return rc;
     k<<<grid_for(k, pl), threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
@@ -266,7 +302,7 @@ int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
     void (*k)(const CdPlan, const PrecodeIO);
     if constexpr (AT > 0) k = cd_precode_pp_kernel<IN, AT>;
     else k = cd_precode_kernel<P, IN, 0>;
-    if (int rc = launch_cd(k, pl, s)) return rc;
+    if (int rc = launch_cd(k, pl)) return rc;
     k<<<grid_for(k, pl), threads_for(pl), pl.smem_bytes, s>>>(pl, io);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
@@ -276,6 +312,7 @@ int launch_precode_t(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 template <int IN>
 int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 {
+    if (pl.gram) return dispatch_detect_gram(IN, pl, io, s);
     if (pl.packed) {
         switch (pl.A_uniform) {
         case 1: return launch_detect_t<16, IN, 1>(pl, io, s);
@@ -294,6 +331,7 @@ int dispatch_detect(const CdPlan& pl, const DetectIO& io, cudaStream_t s)
 template <int IN>
 int dispatch_precode(const CdPlan& pl, const PrecodeIO& io, cudaStream_t s)
 {
+    if (pl.gram) return dispatch_precode_gram(IN, pl, io, s);
     if (pl.packed) {
         switch (pl.A_uniform) {
         case 1: return launch_precode_t<16, IN, 1>(pl, io, s);
@@ -335,8 +373,8 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
         return p->in_dtype != CDMIMO_C64 ? CDMIMO_ERR_UNSUPPORTED : CDMIMO_ERR_INVALID_ARG;
     if (p->n_sc == 0) return CDMIMO_OK;
     CdPlan pl;
-    if (int rc = plan_auto(p, true, H, &pl)) {
-        if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam) return rc;
+    if (int rc = plan_for(p, true, H, &pl)) {
+        if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam || p->form == CDMIMO_FORM_GRAM) return rc;
         return streaming_launch(p, CDMIMO_OP_DETECT, H, Y, N0, Xhat, s);
     }
     if (pl.learned && !pl.packed) return CDMIMO_ERR_UNSUPPORTED;  // learned sweeps: uniform B_c <= 64
@@ -358,8 +396,8 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
     const size_t ea = p->in_dtype == CDMIMO_C64 ? 8 : 4;
     if (!aligned(H, ea) || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
-    if (int rc = plan_auto(p, false, H, &pl)) {
-        if (rc != CDMIMO_ERR_UNSUPPORTED) return rc;
+    if (int rc = plan_for(p, false, H, &pl)) {
+        if (rc != CDMIMO_ERR_UNSUPPORTED || p->form == CDMIMO_FORM_GRAM) return rc;
         return streaming_launch(p, CDMIMO_OP_PRECODE, H, S, nullptr, Xdl, s);
     }
     PrecodeIO io{H, reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl), sched};
@@ -1038,11 +1076,9 @@ int cdmimo_device_status(int clear)
 {
     if (cudaDeviceSynchronize() != cudaSuccess) return CDMIMO_ERR_CUDA;
     unsigned v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_dev_status, sizeof(v)) != cudaSuccess) return CDMIMO_ERR_CUDA;
-    if (clear) {
-        const unsigned z = 0;
-        if (cudaMemcpyToSymbol(g_dev_status, &z, sizeof(z)) != cudaSuccess) return CDMIMO_ERR_CUDA;
-    }
+    if (module_status(&v, clear) != CDMIMO_OK || gram_detect_module_status(&v, clear) != CDMIMO_OK ||
+        gram_precode_module_status(&v, clear) != CDMIMO_OK)
+        return CDMIMO_ERR_CUDA;
     return (int)v;
 }
 

@@ -38,6 +38,8 @@ struct CdPlan {
                       //    packed kernels only: every B_c a multiple of 4; H 16-byte aligned)
     int padded;       // 1: some B_c < A_c P (zero columns must be written once)
     int packed;       // 1: the packed persistent kernels (uniform A in {1, 2, 4}, P = 16) run this plan
+    int gram;         // 1: the Gram-form persistent kernels run this plan (packed layout, U <= UT)
+    int UT;           // Gram form: users padded to 8 or 16 (compile-time register count of x)
     int fuse;         // cdmimo_fuse_rule
     int learned;      // 1: learned sweeps (and possibly learned fusion) from a cdmimo_learned block
     float inv_Ex;
@@ -45,7 +47,10 @@ struct CdPlan {
     // byte offsets of the shared-memory regions (channel blocks start at 0; the packed kernels keep
     // a second channel buffer at off_H2 and per-tile coefficients at off_K)
     // off_mlp: [C][CDMIMO_MAX_HIDDEN] floats of learned-fusion partial sums (learned plans only)
+    // off_G, off_E: Gram form, [C][UT][UT/2] pair-planar rows of G_c with zero diagonal and [C][UT]
+    // column energies
     unsigned off_H2, off_H3, off_X, off_K, off_coef, off_e, off_lam, off_S, off_mlp, off_tab, off_bar, smem_bytes;
+    unsigned off_G, off_E;
     ClusterTile cl[CDMIMO_MAX_CLUSTERS];
 };
 
@@ -68,5 +73,13 @@ struct PrecodeIO {
     float2* Xdl;
     unsigned* sched;
 };
+
+// Threads a Gram-form phase of C x J tiles of AT lanes needs: its lanes spread over a multiple of
+// four warps (the kernels' gram_lane mapping uses the same formula).
+__host__ __device__ inline int gram_phase_threads(int C, int J, int AT)
+{
+    const int L = C * J * AT;
+    return ((L + 31) / 32 + 3) / 4 * 4 * 32;
+}
 
 }  // namespace cdmimo

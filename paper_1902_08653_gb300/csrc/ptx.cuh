@@ -5,9 +5,10 @@
 
 namespace cdmimo {
 
-// Device-side status word (CDMIMO_DEV_* bits); read and cleared by cdmimo_device_status().
-// Defined here: the library is a single translation unit.
-__device__ unsigned int g_dev_status = 0u;
+// Device-side status word (CDMIMO_DEV_* bits) of this translation unit's kernels.  Each of the
+// library's translation units is its own device module with its own word (internal linkage);
+// cdmimo_device_status() reads and clears all of them (launch.h: module_status).
+static __device__ unsigned int g_dev_status = 0u;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
