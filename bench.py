@@ -37,14 +37,23 @@ BITS = U * 4  # 16-QAM bits per vector
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # FP32 ALU peak (FFMA = 2 flop): SMs x FP32 lanes per SM x 2 x max SM clock.
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# Algorithmic work per vector, residual-form CD (SURVEY / DESIGN): 2 K U B complex MACs x 8 flop.
-FLOP_PER_VEC = 2 * K * U * B * 8
+# Algorithmic work per vector (8 flop per complex MAC), by evaluation form of the CD sweeps:
+#   residual (Algorithms 1 and 2 as written): 2 K U B complex MACs;
+#   gram: K U^2 per cluster (sweeps) + U B (z = H^H y, or x = H w) + U (U+1)/2 B_c per cluster and
+#   subcarrier for the Hermitian G_c, shared by the n_sym symbols.
+FLOP_PER_VEC = {"residual": 2 * K * U * B * 8,
+                "gram": 8 * (K * C * U * U + U * B + C * (U * (U + 1) // 2) * (B // C) / N_SYM)}
+KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
+           "gram": ("cd_detect_gram_kernel", "cd_precode_gram_kernel")}
 # Algorithmic HBM bytes per vector: uplink H/14 + y + xhat; downlink H/14 + s + x.
 UL_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8
 DL_BYTES_PER_VEC = U * B * 8 / N_SYM + U * 8 + B * 8
-# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
-# kernel version named in the key; None until a capture of the current kernel exists.
-NCU_TRAFFIC = {}
+# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one --set full
+# capture of `python bench.py --profile detect|precode`, see profiles/) for the kernel named in the
+# key; a kernel without an entry (or changed since its capture) reports null.  The precoder's
+# 34.4 MB output is still in L2 when the kernel ends, so its DRAM writes are mostly outside the launch.
+NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.801216e6 + 1.029376e6,
+               "cd_precode_gram_kernel": 41.527296e6 + 0.883968e6}
 
 WORKLOAD = ("UL CD detect + fusion, then DL CD ZF precode + normalization; B=256 (C=8 x 32), U=16, "
             "K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, SNR sweep 0-30 dB")
@@ -245,9 +254,14 @@ def run_cuda(args, rank, world, local_rank):
     value = world * vec_step / (ms_step * 1e-3)
     ul_ms = float(np.mean(t_ul))
     dl_ms = float(np.mean(t_dl))
-    dom_ms, dom_name = (ul_ms, "cd_detect_kernel") if ul_ms >= dl_ms else (dl_ms, "cd_precode_kernel")
-    achieved_tflops = FLOP_PER_VEC * vec_step / (dom_ms * 1e-3) / 1e12
-    dom_bytes = (UL_BYTES_PER_VEC if dom_name == "cd_detect_kernel" else DL_BYTES_PER_VEC) * vec_step
+    form_ul = cdmimo.selected_form(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K, form=args.form, H=H)
+    form_dl = cdmimo.selected_form(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K, form=args.form, H=Hd)
+    fl_ul, fl_dl = FLOP_PER_VEC[form_ul], FLOP_PER_VEC[form_dl]
+    if ul_ms >= dl_ms:
+        dom_ms, dom_name, dom_flop, dom_bytes = ul_ms, KERNELS[form_ul][0], fl_ul, UL_BYTES_PER_VEC * vec_step
+    else:
+        dom_ms, dom_name, dom_flop, dom_bytes = dl_ms, KERNELS[form_dl][1], fl_dl, DL_BYTES_PER_VEC * vec_step
+    achieved_tflops = dom_flop * vec_step / (dom_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -268,12 +282,19 @@ def run_cuda(args, rank, world, local_rank):
         "ul": {"ms": ul_ms, "vectors_per_s": world * vec_step / (ul_ms * 1e-3),
                "gbps": world * vec_step * BITS / (ul_ms * 1e-3) / 1e9,
                "hbm_frac": UL_BYTES_PER_VEC * vec_step / (ul_ms * 1e-3) / 1e9 / hbm_peak,
-               "fp32_frac": FLOP_PER_VEC * vec_step / (ul_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
+               "form": form_ul, "flop_per_vector": fl_ul,
+               "fp32_frac": fl_ul * vec_step / (ul_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+               "residual_equivalent_fp32_frac": FLOP_PER_VEC["residual"] * vec_step / (ul_ms * 1e-3) / 1e12
+               / FP32_PEAK_TFLOPS},
         "dl": {"ms": dl_ms, "vectors_per_s": world * vec_step / (dl_ms * 1e-3),
                "gbps": world * vec_step * BITS / (dl_ms * 1e-3) / 1e9,
                "hbm_frac": DL_BYTES_PER_VEC * vec_step / (dl_ms * 1e-3) / 1e9 / hbm_peak,
-               "fp32_frac": FLOP_PER_VEC * vec_step / (dl_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
-        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
+               "form": form_dl, "flop_per_vector": fl_dl,
+               "fp32_frac": fl_dl * vec_step / (dl_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+               "residual_equivalent_fp32_frac": FLOP_PER_VEC["residual"] * vec_step / (dl_ms * 1e-3) / 1e12
+               / FP32_PEAK_TFLOPS},
+        "roofline": {"bound": "alu", "kernel": dom_name, "flop_per_vector": dom_flop,
+                     "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                      "hbm": {"achieved_gbs": dom_bytes / (dom_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,

@@ -364,6 +364,12 @@ size_t cdmimo_workspace_size(const cdmimo_params* p, int op);
  * the schedule counters, which every host call zeroes before its launch). */
 size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
 
+/* The evaluation form (CDMIMO_FORM_RESIDUAL or CDMIMO_FORM_GRAM) that cdmimo_detect (op =
+ * CDMIMO_OP_DETECT) or cdmimo_precode (CDMIMO_OP_PRECODE) would run for p and a channel at H (its
+ * alignment decides the staging path), or a negative status (for example UNSUPPORTED for a forced
+ * GRAM that does not apply).  Host only: nothing is launched. */
+int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H);
+
 /* Static name of a status code. */
 const char* cdmimo_status_string(int status);
 

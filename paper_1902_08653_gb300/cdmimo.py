@@ -87,6 +87,7 @@ def lib():
             "cdmimo_detect_host": ([PP, P, P, P, P, P, S, P], I),
             "cdmimo_precode_host": ([PP, P, P, P, P, S, P], I),
             "cdmimo_workspace_size": ([PP, I], S),
+            "cdmimo_selected_form": ([PP, I, P], I),
             "cdmimo_host_workspace_size": ([PP, I], S),
             "cdmimo_status_string": ([I], ctypes.c_char_p),
             "cdmimo_device_status": ([I], I),
@@ -170,15 +171,39 @@ def make_params(n_sc, n_sym, B, U, cluster_size, K, *, Ex=1.0, fuse="colnorm", r
     return p, cs
 
 
+_PARAMS = {}
+
+
+def _params_cached(*key):
+    """make_params for the hot-path calls, memoized on every field (the parameter block is read by
+    the library during the call only, so one block per distinct argument set can be reused)."""
+    hit = _PARAMS.get(key)
+    if hit is None:
+        if len(_PARAMS) > 256:
+            _PARAMS.clear()
+        (n_sc, n_sym, B, U, cs, K, Ex, fuse, rho, in_dtype, hs, ys, learned, form) = key
+        c = (ctypes.c_int * len(cs))(*cs)
+        p = Params(n_sc, n_sym, B, U, len(cs), ctypes.cast(c, ctypes.POINTER(ctypes.c_int)), K, Ex,
+                   FUSE[fuse] if isinstance(fuse, str) else int(fuse), rho, in_dtype, hs, ys, learned,
+                   FORM[form] if isinstance(form, str) else int(form))
+        hit = _PARAMS[key] = (ctypes.byref(p), p, c)
+    return hit[0]
+
+
 _SCHED = {}
 
 
 def schedule_workspace(device, stream=None):
     """The zero-filled 256-byte schedule workspace this binding passes to cdmimo_detect /
     cdmimo_precode on (device, stream): one per stream, so calls on different streams never share
-    counters.  Pass workspace=False to a call for the static schedule."""
+    counters (what workspace=True selects)."""
     device = torch.device(device)
-    key = (device.index if device.index is not None else torch.cuda.current_device(), _stream(stream).value)
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    return _sched_for(idx, _stream(stream).value, device)
+
+
+def _sched_for(idx, stream_value, device):
+    key = (idx, stream_value)
     ws = _SCHED.get(key)
     if ws is None:
         ws = _SCHED[key] = torch.zeros(int(lib().cdmimo_workspace_size(None, OP_DETECT)), dtype=torch.uint8,
@@ -186,19 +211,23 @@ def schedule_workspace(device, stream=None):
     return ws
 
 
-def _workspace_args(workspace, device, stream):
-    if workspace is False:
+def _workspace_args(workspace, device, st):
+    if workspace is None or workspace is False:
         return None, 0
-    if workspace is None:
-        workspace = schedule_workspace(device, stream)
+    if workspace is True:
+        workspace = _sched_for(device.index, st.value, device)
     return workspace.data_ptr(), workspace.numel() * workspace.element_size()
+
+
+def _dptr(t):
+    return t.data_ptr() if t is not None else None
 
 
 def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y_scale=None, learned=None,
            out=None, Xc=None, lam=None, workspace=None, stream=None, form="auto"):
     """cdmimo_detect: Algorithm 1 + fusion.  Returns Xhat [n_sc, n_sym, U] complex64.
-    workspace: None = this binding's per-stream schedule workspace, False = static schedule, or a
-    zero-filled device tensor of cdmimo_workspace_size bytes.  form: "auto", "residual" or "gram"
+    workspace: None or False = static subcarrier schedule; True = dynamic schedule on this binding's
+    per-stream counters; or a zero-filled device tensor of cdmimo_workspace_size bytes (dynamic).  form: "auto", "residual" or "gram"
     (cdmimo_form)."""
     _need(H, "H")
     _need(Y, "Y")
@@ -213,11 +242,11 @@ def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y
     if out is None:
         out = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=H.device)
     _need(out, "out")
-    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse=fuse, in_dtype=dt, h_scale=h_scale,
-                          y_scale=y_scale, learned=learned, form=form)
-    ws, wsb = _workspace_args(workspace, H.device, stream)
-    rc = lib().cdmimo_detect(ctypes.byref(p), _ptr(H), _ptr(Y), _ptr(N0), _ptr(out), _ptr(Xc), _ptr(lam),
-                             ws, wsb, _stream(stream))
+    st = _stream(stream)
+    pp = _params_cached(int(n_sc), int(n_sym), int(B), int(U), tuple(int(v) for v in cluster_size), int(K), float(Ex),
+                        fuse, 1.0, dt, _dptr(h_scale), _dptr(y_scale), _dptr(learned), form)
+    ws, wsb = _workspace_args(workspace, H.device, st)
+    rc = lib().cdmimo_detect(pp, _ptr(H), _ptr(Y), _ptr(N0), _ptr(out), _ptr(Xc), _ptr(lam), ws, wsb, st)
     _check("cdmimo_detect", rc)
     return out
 
@@ -235,9 +264,11 @@ def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=
     if out is None:
         out = torch.empty((n_sc, n_sym, B), dtype=torch.complex64, device=H.device)
     _need(out, "out")
-    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, rho=rho, in_dtype=dt, form=form)
-    ws, wsb = _workspace_args(workspace, H.device, stream)
-    rc = lib().cdmimo_precode(ctypes.byref(p), _ptr(H), _ptr(S), _ptr(out), ws, wsb, _stream(stream))
+    st = _stream(stream)
+    pp = _params_cached(int(n_sc), int(n_sym), int(B), int(U), tuple(int(v) for v in cluster_size), int(K), 1.0,
+                        "colnorm", float(rho), dt, None, None, None, form)
+    ws, wsb = _workspace_args(workspace, H.device, st)
+    rc = lib().cdmimo_precode(pp, _ptr(H), _ptr(S), _ptr(out), ws, wsb, st)
     _check("cdmimo_precode", rc)
     return out
 
@@ -253,6 +284,15 @@ def fuse(Xc, w, *, weights_are_lambda=False, out=None, stream=None):
                            _stream(stream))
     _check("cdmimo_fuse", rc)
     return out
+
+
+def selected_form(op, n_sc, n_sym, B, U, cluster_size, K, *, in_dtype=C64, form="auto", H=None):
+    """cdmimo_selected_form: "residual" or "gram", the form a call with these arguments runs."""
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, in_dtype=in_dtype, form=form)
+    rc = lib().cdmimo_selected_form(ctypes.byref(p), op, _ptr(H) if H is not None else ctypes.c_void_p(256))
+    if rc < 0:
+        raise CdmimoError("cdmimo_selected_form", rc)
+    return {v: k for k, v in FORM.items()}[rc]
 
 
 def host_workspace_size(op, n_sc, n_sym, B, U, cluster_size, K, in_dtype=C64):

@@ -801,6 +801,17 @@ int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* 
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
+int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
+{
+    if (int rc = validate(p)) return rc;
+    if (op != CDMIMO_OP_DETECT && op != CDMIMO_OP_PRECODE) return CDMIMO_ERR_INVALID_ARG;
+    CdPlan pl;
+    const int rc = plan_for(p, op == CDMIMO_OP_DETECT, H, &pl);
+    if (rc == CDMIMO_ERR_UNSUPPORTED && p->form != CDMIMO_FORM_GRAM) return CDMIMO_FORM_RESIDUAL;  // streaming
+    if (rc) return rc;
+    return pl.gram ? CDMIMO_FORM_GRAM : CDMIMO_FORM_RESIDUAL;
+}
+
 size_t cdmimo_workspace_size(const cdmimo_params* p, int op)
 {
     (void)op;

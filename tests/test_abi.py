@@ -104,6 +104,17 @@ def test_host_workspace_sizes():
                                 ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None) == cdmimo.ERR_WORKSPACE
 
 
+def test_form_validation_and_query():
+    L = cdmimo.lib()
+    p, keep = cdmimo.make_params(8, 14, 256, 16, [32] * 8, 3, form=7)
+    one = ctypes.c_void_p(256)
+    assert L.cdmimo_detect(ctypes.byref(p), one, one, one, one, None, None, None, 0, None) == cdmimo.ERR_INVALID_ARG
+    assert L.cdmimo_selected_form(ctypes.byref(p), cdmimo.OP_DETECT, one) == cdmimo.ERR_INVALID_ARG
+    p, keep = cdmimo.make_params(8, 14, 256, 16, [32] * 8, 3, form="residual")
+    assert L.cdmimo_selected_form(ctypes.byref(p), cdmimo.OP_DETECT, one) == cdmimo.FORM["residual"]
+    assert L.cdmimo_selected_form(ctypes.byref(p), 9, one) == cdmimo.ERR_INVALID_ARG
+
+
 def test_schedule_workspace_validation():
     # misaligned or short schedule workspaces are rejected before anything touches the device
     L = cdmimo.lib()

@@ -142,12 +142,12 @@ def test_gram_full_size_schedules_and_auto(dev):
     Y32, Y64 = wl.as_c64(d["Y"])
     N0 = d["N0"].astype(np.float32)
     Ht, Yt, Nt = t(H32, dev), t(Y32, dev), t(N0, dev)
-    a = cdmimo.detect(Ht, Yt, Nt, cs, K, form="gram")
+    a = cdmimo.detect(Ht, Yt, Nt, cs, K, form="gram", workspace=True)
     b = cdmimo.detect(Ht, Yt, Nt, cs, K, form="gram", workspace=False)
     c = cdmimo.detect(Ht, Yt, Nt, cs, K)
     S32, S64 = wl.as_c64(d["X"])
     St = t(S32, dev)
-    pa = cdmimo.precode(Ht, St, cs, K, form="gram")
+    pa = cdmimo.precode(Ht, St, cs, K, form="gram", workspace=True)
     pb = cdmimo.precode(Ht, St, cs, K, form="gram", workspace=False)
     pc = cdmimo.precode(Ht, St, cs, K)
     torch.cuda.synchronize()
@@ -179,3 +179,15 @@ def test_selector_rules(dev):
     assert e.value.status == cdmimo.ERR_UNSUPPORTED
     torch.cuda.synchronize()
     assert cdmimo.device_status(clear=True) == 0
+
+
+def test_selected_form_query(dev):
+    H = torch.zeros((4, 16, 256), dtype=torch.complex64, device=dev)
+    q = lambda op, **kw: cdmimo.selected_form(op, 4, 14, 256, 16, [32] * 8, 3, H=H, **kw)
+    assert q(cdmimo.OP_DETECT) == "gram" and q(cdmimo.OP_PRECODE) == "gram"
+    assert q(cdmimo.OP_DETECT, form="residual") == "residual"
+    # one OFDM symbol per subcarrier: the Gram matrix does not pay for itself
+    assert cdmimo.selected_form(cdmimo.OP_DETECT, 4, 1, 256, 16, [32] * 8, 3, H=H) == "residual"
+    # square clusters (B_c < 2U): AUTO keeps the residual form
+    Hs = torch.zeros((4, 16, 128), dtype=torch.complex64, device=dev)
+    assert cdmimo.selected_form(cdmimo.OP_DETECT, 4, 14, 128, 16, [16] * 8, 3, H=Hs) == "residual"

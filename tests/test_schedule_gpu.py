@@ -49,14 +49,15 @@ def test_dynamic_equals_static_and_counters_reset(data):
     assert torch.equal(Xd, Xs)
     assert torch.equal(Pd, Ps)
     assert cdmimo.device_status(clear=True) == 0
-    # the binding's default (per-stream workspace) is the dynamic schedule
+    # the binding's own per-stream counters (workspace=True) and its default (static)
+    assert torch.equal(cdmimo.detect(d["H"], d["Y"], d["N0"], CS, K, workspace=True), Xs)
     assert torch.equal(cdmimo.detect(d["H"], d["Y"], d["N0"], CS, K), Xs)
 
 
 def test_counter_handed_subcarriers_match_oracle(data):
     d = data
-    X = cdmimo.detect(d["H"], d["Y"], d["N0"], CS, K).cpu().numpy()
-    P = cdmimo.precode(d["Hd"], d["S"], CS, K).cpu().numpy()
+    X = cdmimo.detect(d["H"], d["Y"], d["N0"], CS, K, workspace=True).cpu().numpy()
+    P = cdmimo.precode(d["Hd"], d["S"], CS, K, workspace=True).cpu().numpy()
     # indices past 2 x (152 SMs x 2 CTAs) come from the counter; the last ones are taken last
     idx = np.r_[0:4, 608:616, N_SC - 8:N_SC]
     H64, Y64 = wl.as_c64(d["up"]["H"])[1][idx], wl.as_c64(d["up"]["Y"])[1][idx]
@@ -76,9 +77,9 @@ def test_low_precision_storage_dynamic_equals_static(data):
         Ht = torch.from_numpy(qH.view(np.int16)).to(d["dev"]).view(tdt)
         Yt = torch.from_numpy(qY.view(np.int16)).to(d["dev"]).view(tdt)
         sHt, sYt = torch.from_numpy(sH).to(d["dev"]), torch.from_numpy(sY).to(d["dev"])
-        a = cdmimo.detect(Ht, Yt, d["N0"], CS, K, h_scale=sHt, y_scale=sYt)
+        a = cdmimo.detect(Ht, Yt, d["N0"], CS, K, h_scale=sHt, y_scale=sYt, workspace=True)
         b = cdmimo.detect(Ht, Yt, d["N0"], CS, K, h_scale=sHt, y_scale=sYt, workspace=False)
-        pa = cdmimo.precode(Ht, d["S"], CS, K)
+        pa = cdmimo.precode(Ht, d["S"], CS, K, workspace=True)
         pb = cdmimo.precode(Ht, d["S"], CS, K, workspace=False)
         torch.cuda.synchronize()
         assert torch.equal(a, b), kind
