@@ -127,8 +127,7 @@ __device__ __forceinline__ void load_lane_raw(const void* V, size_t base, int si
 
 // To the pair-planar register layout (re_j, re_{j+1}, im_j, im_{j+1}).  The packed adds (of zero)
 // write each pair into an aligned register pair, so the loop-carried vector needs no register moves
-// in the sweeps' packed FMAs (measured: a third fewer uplink instructions).  Done just before the
-// sweeps, so a prefetch issued one subcarrier earlier is not waited for sooner.
+// in the sweeps' packed FMAs (measured: a third fewer uplink instructions).
 __device__ __forceinline__ void raw_to_pairs(float4 (&v)[kPairs])
 {
     const float2 z = make_float2(0.f, 0.f);
@@ -356,8 +355,10 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
     __syncthreads();
     if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, io.H, f, Dst(0), &bar[0]);
     float4 r[kPairs];
-    if (lt.active && f < pl.n_sc)
+    if (lt.active && f < pl.n_sc) {
         load_lane_raw<IN, AT>(io.Y, ((size_t)f * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
+        raw_to_pairs(r);
+    }
 
     int fn = f + (int)gridDim.x;  // this CTA's next subcarrier
     int done = 0;
@@ -386,7 +387,6 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
             if (pl.bulk && fn < pl.n_sc && tid == 0) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
             break;
         }
-        if (lt.active) raw_to_pairs(r);
 
         if (LEARNED && lt.active && pl.K > 0) {
             // Learned sweeps: x_u <- a1 h^H r + a2 x_u with a1 = tau_t / (e + gamma_t alpha),
@@ -485,8 +485,10 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
         }
         if (tid == 0) nxt[b] = sched_next(io.sched, draw, ticket, fn, pl.n_sc);
         // Prefetch the next subcarrier's receive vector (r is dead from here on).
-        if (lt.active && fn < pl.n_sc)
+        if (lt.active && fn < pl.n_sc) {
             load_lane_raw<IN, AT>(io.Y, ((size_t)fn * n_sym + lt.n) * pl.B + ct.off, ct.size, lt.a, r);
+            raw_to_pairs(r);  // at load: deferring it to the sweeps costs the 16-bit kernels 20% (measured)
+        }
         __syncthreads();
 
         if (LEARNED) {  // lambda_c from the learned fusion (or from m, below), then a barrier
