@@ -162,6 +162,17 @@ int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* X
                    size_t ws_bytes, void* stream);
 
 /*
+ * One TDD frame on one channel: cdmimo_detect on (H, Y) followed by cdmimo_precode of S on the same
+ * H (the downlink channel is the transpose of the uplink one, Sec. IV; precoding uses p->rho),
+ * with the same arguments, outputs and results as those two calls (no Xc_opt / lambda_opt).
+ * Where the Gram form applies (see cdmimo_form; p->form AUTO or GRAM) one kernel does both and
+ * shares the channel copy and G_c between the directions; otherwise (or with p->form RESIDUAL) it
+ * enqueues the two calls.  workspace as for cdmimo_detect.
+ */
+int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
+                          const void* S, void* Xdl, void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * Standalone fusion (Sec. III): Xhat[f][n][u] = sum_c lambda[f][c] Xc[f][c][n][u].
  * If weights_are_lambda != 0, w is lambda itself; otherwise w holds sigma_c^2 and
  * lambda_c = sigma_c^{-2} / sum_c' sigma_c'^{-2} (a zero sigma^2 gives that cluster all the weight;

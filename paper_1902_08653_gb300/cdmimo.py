@@ -88,6 +88,7 @@ def lib():
             "cdmimo_precode_host": ([PP, P, P, P, P, S, P], I),
             "cdmimo_workspace_size": ([PP, I], S),
             "cdmimo_selected_form": ([PP, I, P], I),
+            "cdmimo_detect_precode": ([PP, P, P, P, P, P, P, P, S, P], I),
             "cdmimo_host_workspace_size": ([PP, I], S),
             "cdmimo_status_string": ([I], ctypes.c_char_p),
             "cdmimo_device_status": ([I], I),
@@ -271,6 +272,36 @@ def precode(H, S, cluster_size, K, *, rho=1.0, out=None, workspace=None, stream=
     rc = lib().cdmimo_precode(pp, _ptr(H), _ptr(S), _ptr(out), ws, wsb, st)
     _check("cdmimo_precode", rc)
     return out
+
+
+def detect_precode(H, Y, N0, S, cluster_size, K, *, Ex=1.0, fuse="colnorm", rho=1.0, h_scale=None, y_scale=None,
+                   out=None, out_dl=None, workspace=None, stream=None, form="auto"):
+    """cdmimo_detect_precode: one TDD frame on channel H (uplink detection of Y, downlink precoding
+    of S).  Returns (Xhat [n_sc, n_sym, U], Xdl [n_sc, n_sym, B]) complex64."""
+    _need(H, "H")
+    _need(Y, "Y")
+    _need(N0, "N0")
+    _need(S, "S")
+    dt = _dtype_of(H)
+    if _dtype_of(Y) != dt:
+        raise TypeError("H and Y must use the same storage dtype")
+    if S.dtype != torch.complex64 or N0.dtype != torch.float32:
+        raise TypeError("S must be complex64 and N0 float32")
+    n_sc, U, B = H.shape[:3]
+    n_sym = Y.shape[1]
+    if out is None:
+        out = torch.empty((n_sc, n_sym, U), dtype=torch.complex64, device=H.device)
+    if out_dl is None:
+        out_dl = torch.empty((n_sc, n_sym, B), dtype=torch.complex64, device=H.device)
+    _need(out, "out")
+    _need(out_dl, "out_dl")
+    st = _stream(stream)
+    pp = _params_cached(int(n_sc), int(n_sym), int(B), int(U), tuple(int(v) for v in cluster_size), int(K), float(Ex),
+                        fuse, float(rho), dt, _dptr(h_scale), _dptr(y_scale), None, form)
+    ws, wsb = _workspace_args(workspace, H.device, st)
+    rc = lib().cdmimo_detect_precode(pp, _ptr(H), _ptr(Y), _ptr(N0), _ptr(out), _ptr(S), _ptr(out_dl), ws, wsb, st)
+    _check("cdmimo_detect_precode", rc)
+    return out, out_dl
 
 
 def fuse(Xc, w, *, weights_are_lambda=False, out=None, stream=None):

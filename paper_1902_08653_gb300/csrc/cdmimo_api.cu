@@ -222,7 +222,8 @@ int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
 // regions (rows of G_c, energies, per-tile z / x or w, s).  UNSUPPORTED where the form does not
 // apply; with auto_rules also where a cluster has B_c < 2U (conditioning) or where the form would
 // need as many complex MACs as the residual form.
-int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool auto_rules, CdPlan* pl)
+int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool auto_rules, CdPlan* pl,
+                    bool frame = false)
 {
     if (p->U > 16 || (detect && p->learned)) return CDMIMO_ERR_UNSUPPORTED;
     if (int rc = build_plan(p, 16, detect, H, pl)) return rc;
@@ -241,7 +242,7 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
     const int UT = p->U <= 8 ? 8 : 16;
     const int AT = pl->A_uniform;
     const int threads = std::max({gram_phase_threads(p->C, p->n_sym, AT), gram_phase_threads(p->C, p->U, AT),
-                                  gram_phase_threads(p->C, p->n_sym, 1)});
+                                  gram_phase_threads(p->C, (frame ? 2 : 1) * p->n_sym, 1)});
     if (threads > kMaxSpecializedThreads) return CDMIMO_ERR_UNSUPPORTED;
     if (!detect && p->n_sym * p->U > kSPrefetch * threads) return CDMIMO_ERR_UNSUPPORTED;
     const unsigned C = p->C, xs = (unsigned)pl->n_tiles | 1u, UTu = (unsigned)UT;
@@ -255,6 +256,12 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
     if (!detect) {  // s rows, plus UT zero entries past the last row for the padded steps
         pl->off_S = o;
         o = align16(o + ((unsigned)n_sym * ((unsigned)U | 1u) + UTu) * 8u);
+    }
+    if (frame) {  // the downlink's w per tile and p_u^2 (s is read from global memory)
+        pl->off_W = o;
+        o = align16(o + (unsigned)U * xs * 8u);
+        pl->off_E2 = o;
+        o = align16(o + C * UTu * 4u);
     }
     pl->off_lam = o;
     o = align16(o + C * 4u);
@@ -787,6 +794,28 @@ int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* X
     return precode_impl(p, H, S, Xdl, sched, static_cast<cudaStream_t>(stream));
 }
 
+int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
+                          const void* S, void* Xdl, void* workspace, size_t ws_bytes, void* stream)
+{
+    unsigned* sched;
+    if (int rc = sched_from_workspace(workspace, ws_bytes, &sched)) return rc;
+    if (int rc = validate(p)) return rc;
+    if (int rc = check_detect_ptrs(p, H, Y, N0, Xhat)) return rc;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!S || !Xdl || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CdPlan pl;
+    if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
+        build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK) {
+        FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr, nullptr, sched},
+                   reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
+        return dispatch_frame_gram(p->in_dtype, pl, io, s);
+    }
+    // otherwise the two calls, each in the form it selects
+    if (int rc = detect_impl(p, H, Y, N0, Xhat, nullptr, nullptr, sched, s)) return rc;
+    return precode_impl(p, H, S, Xdl, sched, s);
+}
+
 int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* w, int weights_are_lambda, void* Xhat,
                 void* stream)
 {
@@ -1088,7 +1117,7 @@ int cdmimo_device_status(int clear)
     if (cudaDeviceSynchronize() != cudaSuccess) return CDMIMO_ERR_CUDA;
     unsigned v = 0;
     if (module_status(&v, clear) != CDMIMO_OK || gram_detect_module_status(&v, clear) != CDMIMO_OK ||
-        gram_precode_module_status(&v, clear) != CDMIMO_OK)
+        gram_precode_module_status(&v, clear) != CDMIMO_OK || gram_frame_module_status(&v, clear) != CDMIMO_OK)
         return CDMIMO_ERR_CUDA;
     return (int)v;
 }

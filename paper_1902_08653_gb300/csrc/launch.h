@@ -65,10 +65,12 @@ static inline int module_status(unsigned* v, int clear)
     return CDMIMO_OK;
 }
 
-// Entry points of the Gram-form translation units (gram_detect.cu, gram_precode.cu).
+// Entry points of the Gram-form translation units (gram_detect.cu, gram_precode.cu, gram_frame.cu).
 int dispatch_detect_gram(int in_dtype, const CdPlan& pl, const DetectIO& io, cudaStream_t s);
 int dispatch_precode_gram(int in_dtype, const CdPlan& pl, const PrecodeIO& io, cudaStream_t s);
 int gram_detect_module_status(unsigned* v, int clear);
 int gram_precode_module_status(unsigned* v, int clear);
+int dispatch_frame_gram(int in_dtype, const CdPlan& pl, const FusedIO& io, cudaStream_t s);
+int gram_frame_module_status(unsigned* v, int clear);
 
 }  // namespace cdmimo

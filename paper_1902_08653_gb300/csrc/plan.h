@@ -51,6 +51,7 @@ struct CdPlan {
     // column energies
     unsigned off_H2, off_H3, off_X, off_K, off_coef, off_e, off_lam, off_S, off_mlp, off_tab, off_bar, smem_bytes;
     unsigned off_G, off_E;
+    unsigned off_W, off_E2;  // fused uplink + downlink: w per tile, and p_u^2 beside m_u at off_E
     ClusterTile cl[CDMIMO_MAX_CLUSTERS];
 };
 
@@ -72,6 +73,13 @@ struct PrecodeIO {
     const float2* S;
     float2* Xdl;
     unsigned* sched;
+};
+
+// Fused uplink detection + downlink precoding on one channel (d.H); d.sched drives the schedule.
+struct FusedIO {
+    DetectIO d;
+    const float2* S;
+    float2* Xdl;
 };
 
 // Threads a Gram-form phase of C x J tiles of AT lanes needs: its lanes spread over a multiple of
