@@ -1,14 +1,17 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the decentralized CD hot path on GB300.
 
-Workload (one "step"): uplink CD detection with feedforward fusion (Algorithm 1, Sec. III) followed
-by downlink CD ZF precoding with per-cluster power normalization (Algorithm 2, Sec. IV-B), over one
-batch of 1200 subcarriers x 14 OFDM symbols, B = 256 antennas in C = 8 clusters of 32, U = 16 users,
-K = 3 sweeps, i.i.d. CN(0,1) channels fixed per subcarrier, 16-QAM, SNR swept 0..30 dB across
-subcarriers.  Inputs are resident in HBM; L2 is flushed (256 MB write) between timed steps, outside
-the timed brackets.  value = vectors (subcarrier-symbol pairs, each detected and precoded) per second.
+Workload (one "step"): one TDD frame over a batch of 1200 subcarriers x 14 OFDM symbols, B = 256
+antennas in C = 8 clusters of 32, U = 16 users, K = 3 sweeps, i.i.d. CN(0,1) channels fixed per
+subcarrier, 16-QAM, SNR swept 0..30 dB across subcarriers: uplink CD detection with feedforward
+fusion (Algorithm 1, Sec. III) and downlink CD ZF precoding with per-cluster normalization
+(Algorithm 2, Sec. IV-B) on the same channel (the downlink channel is the transpose of the uplink
+one), through cdmimo_detect_precode.  --step separate times cdmimo_detect and cdmimo_precode on two
+independent channels instead.  Inputs are resident in HBM; L2 is flushed (256 MB write) between
+timed steps, outside the timed brackets.  value = vectors (subcarrier-symbol pairs, each detected
+and precoded) per second.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--step frame|separate]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
 workload (the oracle is the reference implementation of this path).  Under torchrun (N > 1) every
@@ -37,26 +40,33 @@ BITS = U * 4  # 16-QAM bits per vector
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # FP32 ALU peak (FFMA = 2 flop): SMs x FP32 lanes per SM x 2 x max SM clock.
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# Algorithmic work per vector (8 flop per complex MAC), by evaluation form of the CD sweeps:
+# Algorithmic work per vector (8 flop per complex MAC) and direction, by evaluation form:
 #   residual (Algorithms 1 and 2 as written): 2 K U B complex MACs;
 #   gram: K U^2 per cluster (sweeps) + U B (z = H^H y, or x = H w) + U (U+1)/2 B_c per cluster and
-#   subcarrier for the Hermitian G_c, shared by the n_sym symbols.
-FLOP_PER_VEC = {"residual": 2 * K * U * B * 8,
-                "gram": 8 * (K * C * U * U + U * B + C * (U * (U + 1) // 2) * (B // C) / N_SYM)}
+#   subcarrier for the Hermitian G_c, shared by the n_sym symbols (and by both directions of a frame).
+GRAM_G = C * (U * (U + 1) // 2) * (B // C) / N_SYM
+FLOP_PER_VEC = {"residual": 2 * K * U * B * 8, "gram": 8 * (K * C * U * U + U * B + GRAM_G)}
+FRAME_FLOP_PER_VEC = {"residual": 2 * FLOP_PER_VEC["residual"], "gram": 8 * (2 * K * C * U * U + 2 * U * B + GRAM_G)}
 KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
            "gram": ("cd_detect_gram_kernel", "cd_precode_gram_kernel")}
-# Algorithmic HBM bytes per vector: uplink H/14 + y + xhat; downlink H/14 + s + x.
+# Algorithmic HBM bytes per vector: uplink H/14 + y + xhat; downlink H/14 + s + x; frame H/14 once.
 UL_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8
 DL_BYTES_PER_VEC = U * B * 8 / N_SYM + U * 8 + B * 8
+FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one --set full
-# capture of `python bench.py --profile detect|precode`, see profiles/) for the kernel named in the
-# key; a kernel without an entry (or changed since its capture) reports null.  The precoder's
-# 34.4 MB output is still in L2 when the kernel ends, so its DRAM writes are mostly outside the launch.
+# capture of `python bench.py --profile detect|precode|frame`, see profiles/) for the kernel named in
+# the key; a kernel without an entry (or changed since its capture) reports null.  Outputs still in
+# L2 when a kernel ends are written back after it, outside the launch.
 NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.801216e6 + 1.029376e6,
-               "cd_precode_gram_kernel": 41.527296e6 + 0.883968e6}
+               "cd_precode_gram_kernel": 41.527296e6 + 0.883968e6,
+               "cd_frame_gram_kernel": 76.330240e6 + 4.294144e6}
 
-WORKLOAD = ("UL CD detect + fusion, then DL CD ZF precode + normalization; B=256 (C=8 x 32), U=16, "
-            "K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, SNR sweep 0-30 dB")
+WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
+            "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
+            "SNR sweep 0-30 dB")
+WORKLOAD_SEPARATE = ("UL CD detect + fusion, then DL CD ZF precode + normalization on an independent channel; "
+                     "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
+                     "SNR sweep 0-30 dB")
 
 
 def load_peaks():
@@ -153,26 +163,35 @@ def run_cuda(args, rank, world, local_rank):
     from paper_1902_08653_gb300 import cdmimo
     from paper_1902_08653_gb300 import workload as wl
 
+    frame = args.step == "frame"
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     cdmimo.lib()
     up, dl = make_inputs(20190222 + rank)
-    H = torch.from_numpy(wl.as_c64(up["H"])[0]).to(dev)
-    Y = torch.from_numpy(wl.as_c64(up["Y"])[0]).to(dev)
+    t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
+    H, Y, S = t(up["H"]), t(up["Y"]), t(dl["S"])
+    Hd = H if frame else t(dl["H"])
     N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
-    Hd = torch.from_numpy(wl.as_c64(dl["H"])[0]).to(dev)
-    S = torch.from_numpy(wl.as_c64(dl["S"])[0]).to(dev)
     Xhat = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64, device=dev)
     Xdl = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def ul():
         cdmimo.detect(H, Y, N0, CS, K, out=Xhat, stream=stream, form=args.form)
+
+    def dl_():
         cdmimo.precode(Hd, S, CS, K, out=Xdl, stream=stream, form=args.form)
 
+    def frm():
+        cdmimo.detect_precode(H, Y, N0, S, CS, K, out=Xhat, out_dl=Xdl, stream=stream, form=args.form)
+
     for _ in range(args.warmup):
-        step()
+        if frame:
+            frm()
+        else:
+            ul()
+            dl_()
         flush.fill_(1.0)
     torch.cuda.synchronize()
     cdmimo.device_status(clear=True)
@@ -188,9 +207,13 @@ def run_cuda(args, rank, world, local_rank):
     for i in range(args.steps):
         e = ev[i]
         e[0].record(stream)
-        cdmimo.detect(H, Y, N0, CS, K, out=Xhat, stream=stream, form=args.form)
-        e[1].record(stream)
-        cdmimo.precode(Hd, S, CS, K, out=Xdl, stream=stream, form=args.form)
+        if frame:
+            frm()
+            e[1].record(stream)
+        else:
+            ul()
+            e[1].record(stream)
+            dl_()
         e[2].record(stream)
         flush.fill_(float(i & 7))  # L2 flush between timed steps, outside the brackets
     torch.cuda.synchronize()
@@ -198,34 +221,50 @@ def run_cuda(args, rank, world, local_rank):
         torch.distributed.barrier()
     wall = time.perf_counter() - t0
     clocks = sampler.stop() if rank == 0 else None
-    t_ul = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    t_dl = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    dev_ms = float(np.sum(t_ul) + np.sum(t_dl))
+    t_a = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    t_b = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    dev_ms = float(np.sum(t_a) + np.sum(t_b))
     st = cdmimo.device_status(clear=True)
     if st != 0:
         raise RuntimeError(f"device status {st:#x} after the timed loop")
-
     if world > 1:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_ms = float(t.item())
+        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        dev_ms = float(tt.item())
 
-    # End to end: host (pinned) buffers through the C ABI, copies inside the timed region.
+    # End to end through the public API: every step copies the inputs from pinned host memory to the
+    # device and the results back, inside the timed region.  Frame: device buffers + one
+    # cdmimo_detect_precode; separate: the host-buffer entry points (copies inside the calls).
     Hh = torch.from_numpy(wl.as_c64(up["H"])[0]).pin_memory()
     Yh = torch.from_numpy(wl.as_c64(up["Y"])[0]).pin_memory()
     N0h = torch.from_numpy(up["N0"].astype(np.float32)).pin_memory()
-    Hdh = torch.from_numpy(wl.as_c64(dl["H"])[0]).pin_memory()
     Sh = torch.from_numpy(wl.as_c64(dl["S"])[0]).pin_memory()
+    Hdh = Hh if frame else torch.from_numpy(wl.as_c64(dl["H"])[0]).pin_memory()
     Xh = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64).pin_memory()
     Xdh = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64).pin_memory()
-    ws_ul = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K), dtype=torch.uint8,
-                        device=dev)
-    ws_dl = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K), dtype=torch.uint8,
-                        device=dev)
+    if frame:
+        Hb, Yb, Nb, Sb = torch.empty_like(H), torch.empty_like(Y), torch.empty_like(N0), torch.empty_like(S)
+
+        def e2e_step():
+            Hb.copy_(Hh, non_blocking=True)
+            Yb.copy_(Yh, non_blocking=True)
+            Nb.copy_(N0h, non_blocking=True)
+            Sb.copy_(Sh, non_blocking=True)
+            cdmimo.detect_precode(Hb, Yb, Nb, Sb, CS, K, out=Xhat, out_dl=Xdl, stream=stream, form=args.form)
+            Xh.copy_(Xhat, non_blocking=True)
+            Xdh.copy_(Xdl, non_blocking=True)
+    else:
+        ws_ul = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K),
+                            dtype=torch.uint8, device=dev)
+        ws_dl = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K),
+                            dtype=torch.uint8, device=dev)
+
+        def e2e_step():
+            cdmimo.detect_host(Hh, Yh, N0h, CS, K, Xh, ws_ul, stream=stream)
+            cdmimo.precode_host(Hdh, Sh, CS, K, Xdh, ws_dl, stream=stream)
     e2e_steps = max(3, min(50, args.steps))
     for _ in range(2):
-        cdmimo.detect_host(Hh, Yh, N0h, CS, K, Xh, ws_ul, stream=stream)
-        cdmimo.precode_host(Hdh, Sh, CS, K, Xdh, ws_dl, stream=stream)
+        e2e_step()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -233,16 +272,15 @@ def run_cuda(args, rank, world, local_rank):
         torch.distributed.barrier()
     e0.record(stream)
     for _ in range(e2e_steps):
-        cdmimo.detect_host(Hh, Yh, N0h, CS, K, Xh, ws_ul, stream=stream)
-        cdmimo.precode_host(Hdh, Sh, CS, K, Xdh, ws_dl, stream=stream)
+        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    h2d = (Hh.numel() * 8 + Yh.numel() * 8 + N0h.numel() * 4) + (Hdh.numel() * 8 + Sh.numel() * 8)
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = Hh.numel() * 8 + Yh.numel() * 8 + N0h.numel() * 4 + Sh.numel() * 8 + (0 if frame else Hdh.numel() * 8)
     d2h = Xh.numel() * 8 + Xdh.numel() * 8
 
     if rank != 0:
@@ -252,16 +290,27 @@ def run_cuda(args, rank, world, local_rank):
     ms_step = dev_ms / args.steps
     vec_step = N_SC * N_SYM
     value = world * vec_step / (ms_step * 1e-3)
-    ul_ms = float(np.mean(t_ul))
-    dl_ms = float(np.mean(t_dl))
     form_ul = cdmimo.selected_form(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K, form=args.form, H=H)
     form_dl = cdmimo.selected_form(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K, form=args.form, H=Hd)
-    fl_ul, fl_dl = FLOP_PER_VEC[form_ul], FLOP_PER_VEC[form_dl]
-    if ul_ms >= dl_ms:
-        dom_ms, dom_name, dom_flop, dom_bytes = ul_ms, KERNELS[form_ul][0], fl_ul, UL_BYTES_PER_VEC * vec_step
+
+    def kernel_line(name, form, ms, flop, nbytes):
+        return {"kernel": name, "form": form, "ms": ms, "flop_per_vector": flop,
+                "fp32_frac": flop * vec_step / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                "hbm_frac": nbytes * vec_step / (ms * 1e-3) / 1e9 / hbm_peak}
+
+    if frame:
+        fused = form_ul == "gram" and form_dl == "gram"
+        name = "cd_frame_gram_kernel" if fused else "+".join(KERNELS[form_ul][:1] + KERNELS[form_dl][1:])
+        fl = FRAME_FLOP_PER_VEC["gram"] if fused else FLOP_PER_VEC[form_ul] + FLOP_PER_VEC[form_dl]
+        kernels = [kernel_line(name, "gram" if fused else form_ul, float(np.mean(t_a)), fl, FRAME_BYTES_PER_VEC)]
+        dom = kernels[0]
+        dom_bytes = FRAME_BYTES_PER_VEC * vec_step
     else:
-        dom_ms, dom_name, dom_flop, dom_bytes = dl_ms, KERNELS[form_dl][1], fl_dl, DL_BYTES_PER_VEC * vec_step
-    achieved_tflops = dom_flop * vec_step / (dom_ms * 1e-3) / 1e12
+        kernels = [kernel_line(KERNELS[form_ul][0], form_ul, float(np.mean(t_a)), FLOP_PER_VEC[form_ul], UL_BYTES_PER_VEC),
+                   kernel_line(KERNELS[form_dl][1], form_dl, float(np.mean(t_b)), FLOP_PER_VEC[form_dl], DL_BYTES_PER_VEC)]
+        dom = max(kernels, key=lambda k: k["ms"])
+        dom_bytes = (UL_BYTES_PER_VEC if dom is kernels[0] else DL_BYTES_PER_VEC) * vec_step
+    achieved = dom["flop_per_vector"] * vec_step / (dom["ms"] * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -275,44 +324,32 @@ def run_cuda(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded i.i.d. Rayleigh, 16-QAM, AWGN)",
-        "config": {"workload": WORKLOAD, "n_sc": N_SC, "n_sym": N_SYM, "B": B, "C": C, "B_c": B // C, "U": U, "K": K,
-                   "fusion": "colnorm", "qam": M, "l2": "flushed between timed steps (256 MB write, untimed)",
+        "config": {"workload": WORKLOAD if frame else WORKLOAD_SEPARATE, "step": args.step, "n_sc": N_SC,
+                   "n_sym": N_SYM, "B": B, "C": C, "B_c": B // C, "U": U, "K": K, "fusion": "colnorm", "qam": M,
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gbps": value * BITS / 1e9,
-        "ul": {"ms": ul_ms, "vectors_per_s": world * vec_step / (ul_ms * 1e-3),
-               "gbps": world * vec_step * BITS / (ul_ms * 1e-3) / 1e9,
-               "hbm_frac": UL_BYTES_PER_VEC * vec_step / (ul_ms * 1e-3) / 1e9 / hbm_peak,
-               "form": form_ul, "flop_per_vector": fl_ul,
-               "fp32_frac": fl_ul * vec_step / (ul_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-               "residual_equivalent_fp32_frac": FLOP_PER_VEC["residual"] * vec_step / (ul_ms * 1e-3) / 1e12
-               / FP32_PEAK_TFLOPS},
-        "dl": {"ms": dl_ms, "vectors_per_s": world * vec_step / (dl_ms * 1e-3),
-               "gbps": world * vec_step * BITS / (dl_ms * 1e-3) / 1e9,
-               "hbm_frac": DL_BYTES_PER_VEC * vec_step / (dl_ms * 1e-3) / 1e9 / hbm_peak,
-               "form": form_dl, "flop_per_vector": fl_dl,
-               "fp32_frac": fl_dl * vec_step / (dl_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-               "residual_equivalent_fp32_frac": FLOP_PER_VEC["residual"] * vec_step / (dl_ms * 1e-3) / 1e12
-               / FP32_PEAK_TFLOPS},
-        "roofline": {"bound": "alu", "kernel": dom_name, "flop_per_vector": dom_flop,
-                     "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+        "kernels": kernels,
+        "roofline": {"bound": "alu", "kernel": dom["kernel"], "flop_per_vector": dom["flop_per_vector"],
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                     "hbm": {"achieved_gbs": dom_bytes / (dom_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
-                             "frac": dom_bytes / (dom_ms * 1e-3) / 1e9 / hbm_peak, "peak_source": peak_src},
-                     "traffic": NCU_TRAFFIC.get(dom_name)},
+                     "hbm": {"achieved_gbs": dom_bytes / (dom["ms"] * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                             "frac": dom_bytes / (dom["ms"] * 1e-3) / 1e9 / hbm_peak, "peak_source": peak_src},
+                     "traffic": NCU_TRAFFIC.get(dom["kernel"])},
         "mse_vs_mmse": mse,
         "ber": ber,
         "e2e": {"value": world * vec_step / (e2e_ms * 1e-3), "unit": "vectors/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (1 if frame and kernels[0]["kernel"] == "cd_frame_gram_kernel" else 2) * args.steps,
         "clocks": clocks,
         "wall_s": wall,
     }
-    line["cpu_baseline"] = cpu_baseline(up, dl) if world == 1 else None
+    line["cpu_baseline"] = cpu_baseline(up, dl, frame) if world == 1 else None
     return line
 
 
-def cpu_baseline(up, dl, min_seconds=10.0, threads=None):
+def cpu_baseline(up, dl, frame=True, min_seconds=10.0, threads=None):
     """The FP64 oracle as it stands, on the host cores: the whole batch (UL detect + DL precode),
     repeated until about `min_seconds` of wall time have been spent."""
     import oracle
@@ -323,7 +360,7 @@ def cpu_baseline(up, dl, min_seconds=10.0, threads=None):
     t0 = time.perf_counter()
     while True:
         oracle.detect(up["H"], up["Y"], up["N0"], CS, K, threads=threads)
-        oracle.precode(dl["H"], dl["S"], CS, K, threads=threads)
+        oracle.precode(up["H"] if frame else dl["H"], dl["S"], CS, K, threads=threads)
         reps += 1
         dt = time.perf_counter() - t0
         if dt >= min_seconds or reps >= 500:
@@ -348,7 +385,7 @@ def run_reference(args):
         sl = slice(f0, f0 + n_sub)
         t0 = time.perf_counter()
         oracle.detect(up["H"][sl], up["Y"][sl], up["N0"][sl], CS, K, threads=threads)
-        oracle.precode(dl["H"][sl], dl["S"][sl], CS, K, threads=threads)
+        oracle.precode((up if args.step == "frame" else dl)["H"][sl], dl["S"][sl], CS, K, threads=threads)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = n_sub * N_SYM / (ms * 1e-3)
@@ -356,7 +393,8 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded i.i.d. Rayleigh)",
-            "config": {"workload": WORKLOAD, "n_sc": N_SC, "n_sym": N_SYM, "B": B, "C": C, "U": U, "K": K},
+            "config": {"workload": WORKLOAD if args.step == "frame" else WORKLOAD_SEPARATE, "step": args.step,
+                       "n_sc": N_SC, "n_sym": N_SYM, "B": B, "C": C, "U": U, "K": K},
             "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -560,8 +598,10 @@ def run_profile(args):
     for _ in range(3):
         if args.profile == "detect":
             cdmimo.detect(H, Y, N0, CS, K, form=args.form)
-        else:
+        elif args.profile == "precode":
             cdmimo.precode(H, S, CS, K, form=args.form)
+        else:
+            cdmimo.detect_precode(H, Y, N0, S, CS, K, form=args.form)
     torch.cuda.synchronize()
     assert cdmimo.device_status(clear=True) == 0
     print("ok", args.profile, args.form)
@@ -576,9 +616,11 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2 (default): UL detect + DL precode bench line; 1, 3, 4, 5: the other configurations")
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
-    ap.add_argument("--profile", choices=["detect", "precode"], default=None,
-                    help="untimed: three cdmimo_detect or cdmimo_precode calls on the step's workload, for ncu")
+    ap.add_argument("--profile", choices=["detect", "precode", "frame"], default=None,
+                    help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu")
     ap.add_argument("--form", choices=["auto", "residual", "gram"], default="auto", help="CD evaluation form")
+    ap.add_argument("--step", choices=["frame", "separate"], default="frame",
+                    help="frame (default): UL + DL on one channel, one call; separate: two calls, two channels")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
