@@ -128,6 +128,28 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (each rank's own timing; world 1: x itself)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(vectors_per_rank, world, max_ms):
+    """Weak scaling: every rank processes its own batch; the job's throughput is all ranks' vectors
+    over the slowest rank's time."""
+    return world * vectors_per_rank / (max_ms * 1e-3)
+
+
+def rank_seed(rank):
+    """Each rank's batch seed (independent synthetic batches, the same shape)."""
+    return 20190222 + rank
+
+
 def make_inputs(seed):
     from paper_1902_08653_gb300 import workload as wl
 
@@ -167,7 +189,7 @@ def run_cuda(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     cdmimo.lib()
-    up, dl = make_inputs(20190222 + rank)
+    up, dl = make_inputs(rank_seed(rank))
     t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
     H, Y, S = t(up["H"]), t(up["Y"]), t(dl["S"])
     Hd = H if frame else t(dl["H"])
@@ -227,10 +249,7 @@ def run_cuda(args, rank, world, local_rank):
     st = cdmimo.device_status(clear=True)
     if st != 0:
         raise RuntimeError(f"device status {st:#x} after the timed loop")
-    if world > 1:
-        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        dev_ms = float(tt.item())
+    dev_ms = max_over_ranks(dev_ms, world, dev)
 
     # End to end through the public API: every step copies the inputs from pinned host memory to the
     # device and the results back, inside the timed region.  Frame: device buffers + one
@@ -276,10 +295,7 @@ def run_cuda(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     h2d = Hh.numel() * 8 + Yh.numel() * 8 + N0h.numel() * 4 + Sh.numel() * 8 + (0 if frame else Hdh.numel() * 8)
     d2h = Xh.numel() * 8 + Xdh.numel() * 8
 
@@ -289,7 +305,7 @@ def run_cuda(args, rank, world, local_rank):
     hbm_peak, peak_src = load_peaks()
     ms_step = dev_ms / args.steps
     vec_step = N_SC * N_SYM
-    value = world * vec_step / (ms_step * 1e-3)
+    value = whole_job_value(vec_step, world, ms_step)
     form_ul = cdmimo.selected_form(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K, form=args.form, H=H)
     form_dl = cdmimo.selected_form(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K, form=args.form, H=Hd)
 
@@ -339,7 +355,7 @@ def run_cuda(args, rank, world, local_rank):
                      "traffic": NCU_TRAFFIC.get(dom["kernel"])},
         "mse_vs_mmse": mse,
         "ber": ber,
-        "e2e": {"value": world * vec_step / (e2e_ms * 1e-3), "unit": "vectors/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": whole_job_value(vec_step, world, e2e_ms), "unit": "vectors/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": (1 if frame and kernels[0]["kernel"] == "cd_frame_gram_kernel" else 2) * args.steps,
         "clocks": clocks,
