@@ -443,150 +443,3 @@ __global__ void __maxnreg__(kPPRegs) cd_precode_gram_kernel(const CdPlan pl, con
 
 }  // namespace cdmimo
 
-namespace cdmimo {
-
-// ---------------------------------------------------------------------------------------------
-// TDD frame on one channel (the downlink channel is the transpose of the uplink one, Sec. IV):
-// Algorithm 1 + fusion on (H, y) and Algorithm 2 + normalization on (H, s), both in Gram form,
-// sharing one channel copy and one G_c per subcarrier.  Phase B runs the uplink sweeps (on x, with
-// m_u) and the downlink sweeps (on w, with p_u^2) side by side: tile (c, j) is uplink symbol j for
-// j < n_sym and downlink symbol j - n_sym otherwise, so one warp holds both kinds of tiles of a
-// cluster and they read the same rows of G_c.
-// ---------------------------------------------------------------------------------------------
-template <int IN, int AT, int UT>
-__global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const FusedIO io)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    auto Hbuf = [&](int j) { return reinterpret_cast<float2*>(smem + ((IN == CDMIMO_C64 && j) ? pl.off_H2 : 0u)); };
-    auto Stg = [&](int j) { return reinterpret_cast<void*>(smem + (j ? pl.off_H3 : pl.off_H2)); };
-    auto Dst = [&](int j) { return IN == CDMIMO_C64 ? reinterpret_cast<void*>(Hbuf(j)) : Stg(j); };
-    float4* Gs = reinterpret_cast<float4*>(smem + pl.off_G);  // [C][UT][UT/2]
-    float* Dm = reinterpret_cast<float*>(smem + pl.off_E);    // [C][UT] m_u
-    float* Dp = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] p_u^2
-    float2* Zs = reinterpret_cast<float2*>(smem + pl.off_X);  // [U][x_stride]: z, then each tile's x
-    float2* Ws = reinterpret_cast<float2*>(smem + pl.off_W);  // [U][x_stride]: w per tile
-    float* lam = reinterpret_cast<float*>(smem + pl.off_lam);
-    ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
-    int* nxt = reinterpret_cast<int*>(smem + pl.off_bar + 16);
-    const DetectIO& d = io.d;
-
-    const int tid = threadIdx.x;
-    const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
-    const uint32_t xs_stride = x_stride(pl);
-    constexpr int LP = AT * kPairs;
-    gram_setup<IN, UT>(pl, smem, tab, bar, true);
-    const GLane gz = gram_lane(C, n_sym, AT);     // phase A (y in registers); phase C (x_c = H_c w)
-    const GLane gg = gram_lane(C, U, AT);         // phase A: Gram columns
-    const GLane gb = gram_lane(C, 2 * n_sym, 1);  // phase B: uplink and downlink tiles of each cluster
-    const ClusterTile ctz = tab[gz.c];
-
-    int f = blockIdx.x;
-    if (pl.bulk && tid == 0) {
-        if (f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
-        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy<IN>(pl, &bar[1]);
-    }
-    __syncthreads();
-    if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, f, Dst(0), &bar[0]);
-    float4 r[kPairs];
-    if (gz.active && f < pl.n_sc)
-        load_lane_raw<IN, AT>(d.Y, ((size_t)f * n_sym + gz.j) * pl.B + ctz.off, ctz.size, gz.a, r);
-
-    int fn = f + (int)gridDim.x;
-    int done = 0;
-    for (int k = 0; f < pl.n_sc; ++k) {
-        const int b = k & 1;
-        const bool draw = fn < pl.n_sc;
-        const unsigned ticket = sched_draw(d.sched, draw);
-        if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
-
-        float alpha = __ldg(d.N0 + f) * pl.inv_Ex;
-        float out_scale = 1.f;
-        if (IN != CDMIMO_C64) {
-            const float hs = __ldg(d.h_scale + f), ys = __ldg(d.y_scale + f);
-            alpha = alpha / (hs * hs);
-            out_scale = ys / hs;
-        }
-        if (!(alpha >= 0.f)) {
-            if (tid == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_N0);
-            out_scale = __int_as_float(0x7fc00000);
-            alpha = 0.f;
-        }
-        if (!acquire_channel<IN>(pl, tab, d.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
-                                 d.sched != nullptr || fn + (int)gridDim.x < pl.n_sc)) {
-            if (pl.bulk && fn < pl.n_sc && tid == 0) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
-            break;
-        }
-
-        // Phase A: z = H_c^H y, the Gram columns, m_u and p_u^2.
-        if (gz.active) {
-            raw_to_pairs(r);
-            gram_rhs<AT>(gz, U, n_sym, xs_stride, tab, Hbuf(b), r, Zs);
-        }
-        gram_columns<AT, UT>(gg, U, tab, Hbuf(b), alpha, Gs, Dm, Dp);
-        if (tid == 0) nxt[b] = sched_next(d.sched, draw, ticket, fn, pl.n_sc);
-        if (gz.active && fn < pl.n_sc)
-            load_lane_raw<IN, AT>(d.Y, ((size_t)fn * n_sym + gz.j) * pl.B + ctz.off, ctz.size, gz.a, r);
-        __syncthreads();
-
-        // Phase B: uplink sweeps on x (right-hand side z from shared memory) and downlink sweeps on w
-        // (s read from global memory, cached after the first sweep).
-        if (gb.active) {
-            const bool ul = gb.j < n_sym;
-            const int n = ul ? gb.j : gb.j - n_sym;
-            const int tile = gb.c * n_sym + n;
-            const float* dd = (ul ? Dm : Dp) + gb.c * UT;
-            const float2* rhs = ul ? Zs + tile : io.S + ((size_t)f * n_sym + n) * U;
-            float4 x[UT / 2];
-            gram_sweeps<UT, 1>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, rhs, ul ? xs_stride : 1u, 0, gb.mask, x);
-            float2* dst = (ul ? Zs : Ws) + tile;
-#pragma unroll
-            for (int u = 0; u < UT; ++u)
-                if (u < U) dst[u * xs_stride] = slice_entry<UT, 1>(x, u);
-            if (ul && n == 0) {
-                float msum = 0.f;
-                for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
-                lam[gb.c] = 1.f / msum;
-            }
-        }
-        __syncthreads();
-
-        // Phase C: uplink fusion, then downlink x_c = H_c w and the per-cluster normalization.
-        fuse_subcarrier<false>(pl, d, f, lam, Zs, xs_stride, out_scale);
-        if (gz.active) {
-            const ClusterTile ct = tab[gz.c];
-            const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ct.soff) + gz.a;
-            const float2* wt = Ws + gz.c * n_sym + gz.j;
-            float4 x[kPairs];
-#pragma unroll
-            for (int i = 0; i < kPairs; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 2
-            for (int v = 0; v < U; ++v) {
-                float4 h[kPairs];
-                pp_load_h<AT>(hb + v * LP, h);
-                const float2 wv = wt[v * xs_stride];
-                pp_update(h, make_float2(-wv.x, -wv.y), x);  // x += h_v w_v
-            }
-            float nr = 0.f;
-#pragma unroll
-            for (int i = 0; i < kPairs; ++i)
-                nr = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, fmaf(x[i].z, x[i].z, fmaf(x[i].w, x[i].w, nr))));
-            nr = tile_sum_c<AT>(nr, gz.mask);
-            const float sc = nr > 0.f ? pl.rho_c * rsqrtf(nr) : 0.f;
-            float2* out = io.Xdl + ((size_t)f * n_sym + gz.j) * pl.B + ct.off;
-#pragma unroll
-            for (int i = 0; i < kPairs; ++i) {
-                const int col = 2 * (i * AT + gz.a);
-                if (col < ct.size) out[col] = make_float2(x[i].x * sc, x[i].z * sc);
-                if (col + 1 < ct.size) out[col + 1] = make_float2(x[i].y * sc, x[i].w * sc);
-            }
-        }
-        __syncthreads();  // this channel buffer receives the copy issued at the next iteration's start
-        ++done;
-        f = fn;
-        fn = nxt[b];
-    }
-    sched_finish(d.sched, done, pl.n_sc);
-}
-
-}  // namespace cdmimo

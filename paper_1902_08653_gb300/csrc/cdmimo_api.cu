@@ -241,8 +241,13 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
     }
     const int UT = p->U <= 8 ? 8 : 16;
     const int AT = pl->A_uniform;
-    const int threads = std::max({gram_phase_threads(p->C, p->n_sym, AT), gram_phase_threads(p->C, p->U, AT),
-                                  gram_phase_threads(p->C, (frame ? 2 : 1) * p->n_sym, 1)});
+    // frame: phase A runs symbol pairs and Gram column pairs on disjoint warps; phase B one lane per
+    // (cluster, symbol); separate kernels: one phase after the other on the same warps
+    const int threads = frame ? std::max(gram_phase_threads(p->C, (p->n_sym + 1) / 2, AT) +
+                                             gram_phase_threads(p->C, (p->U + 1) / 2, AT),
+                                         gram_phase_threads(p->C, p->n_sym, 1))
+                              : std::max({gram_phase_threads(p->C, p->n_sym, AT), gram_phase_threads(p->C, p->U, AT),
+                                          gram_phase_threads(p->C, p->n_sym, 1)});
     if (threads > kMaxSpecializedThreads) return CDMIMO_ERR_UNSUPPORTED;
     if (!detect && p->n_sym * p->U > kSPrefetch * threads) return CDMIMO_ERR_UNSUPPORTED;
     const unsigned C = p->C, xs = (unsigned)pl->n_tiles | 1u, UTu = (unsigned)UT;

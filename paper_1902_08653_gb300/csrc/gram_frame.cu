@@ -1,6 +1,6 @@
 // Gram-form uplink + downlink frame kernels' translation unit: template instantiation and dispatch
 // over storage type, lanes per tile (AT in {1, 2, 4}) and padded users (UT in {8, 16}).
-#include "cd_gram.cuh"
+#include "cd_frame.cuh"
 #include "launch.h"
 
 namespace cdmimo {

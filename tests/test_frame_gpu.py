@@ -2,9 +2,9 @@
 precoding on one channel in one kernel (Gram form), or as two calls where that kernel does not
 apply.
 
-The fused kernel evaluates exactly the operations of the separate Gram-form kernels (same Gram
-columns, right-hand sides, sweeps, fusion and H w), so its outputs must equal theirs bit for bit;
-both are also compared with the FP64 oracle (1e-4 relative L2 per vector).
+The fused kernel evaluates the operations of the separate Gram-form kernels with each loaded value
+feeding two vectors (a different summation order), so its outputs agree with theirs to FP32
+rounding (2e-5 relative L2 per vector); both are compared with the FP64 oracle (1e-4).
 """
 import zlib
 
@@ -47,7 +47,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_frame_matches_separate_gram_calls_and_oracle(dev, name):
+def test_frame_matches_separate_calls_and_oracle(dev, name):
     n_sc, n_sym, cs, U, K, fuse, snr = CASES[name]
     snr = wl.sweep_snr(n_sc) if snr == "sweep" else snr
     d = wl.uplink(zlib.crc32(name.encode()) % 1000, n_sc, n_sym, sum(cs), U, snr_db=snr)
@@ -60,8 +60,8 @@ def test_frame_matches_separate_gram_calls_and_oracle(dev, name):
     Xs = cdmimo.detect(Ht, Yt, Nt, cs, K, fuse=fuse, form="gram")
     Ps = cdmimo.precode(Ht, St, cs, K, form="gram")
     torch.cuda.synchronize()
-    assert torch.equal(X, Xs)
-    assert torch.equal(P, Ps)
+    assert_vectors_close(X.cpu().numpy(), Xs.cpu().numpy(), 2e-5, "frame vs separate Xhat")
+    assert_vectors_close(P.cpu().numpy(), Ps.cpu().numpy(), 2e-5, "frame vs separate Xdl")
     Xo, _, _ = orc.detect(H64, Y64, N0.astype(np.float64), cs, K, fuse=fuse, threads=8)
     Po = orc.precode(H64, S64, cs, K, threads=8)
     assert_vectors_close(X.cpu().numpy(), Xo, TOL, "frame Xhat")
