@@ -9,8 +9,8 @@
 // loaded pair for one vector run at half the FP32 rate.  Here every loaded value feeds two vectors:
 //   phase A  one lane set correlates h_u with two receive vectors (two symbols) for z, while the
 //            other half of the CTA correlates h_u with two channel columns for G_c;
-//   phase B  one lane per (cluster, symbol) sweeps the uplink x and the downlink w together: each
-//            row of G_c read from shared memory serves both (the same G_c, two right-hand sides);
+//   phase B  one lane per uplink or downlink (cluster, symbol) runs the sweeps (latency-bound: here
+//            one vector per lane on every warp beats two vectors per lane on half of them);
 //   phase C  x_c = H_c w for two symbols per lane, while the other half of the CTA fuses the uplink
 //            estimates.
 #pragma once
@@ -61,76 +61,6 @@ __device__ __forceinline__ void corr2(const float4* hr, const float4 (&v0)[kPair
     }
     s0 = make_float2(R0.x + R0.y, (I0.x + I0.y) - (J0.x + J0.y));
     s1 = make_float2(R1.x + R1.y, (I1.x + I1.y) - (J1.x + J1.y));
-}
-
-// Phase B for one (cluster, symbol): K sweeps of the uplink x_u <- m_u (z_u - sum_{v != u} G_uv x_v)
-// and of the downlink w_u <- p_u^2 (s_u - sum_{v != u} G_uv w_v) together, G_c rows (zero diagonal)
-// read once for both; x and w pair-planar in registers.
-template <int UT>
-__device__ __forceinline__ void sweeps2(int U, int K, const float4* Grow, const float* dm, const float2* z,
-                                        uint32_t zs, const float* dp, const float2* s, float4 (&x)[UT / 2],
-                                        float4 (&w)[UT / 2])
-{
-    constexpr int NP = UT / 2;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        w[i] = x[i];
-    }
-#pragma unroll 1
-    for (int t = 0; t < K; ++t) {
-#pragma unroll
-        for (int u = 0; u < UT; ++u) {
-            if (u < U) {
-                const float4* gr = Grow + u * NP;
-                const float2 zero = make_float2(0.f, 0.f);
-                float2 Ra = zero, Ia = zero, Ja = zero, Rb = zero, Ib = zero, Jb = zero;  // x
-                float2 Rc = zero, Ic = zero, Jc = zero, Rd = zero, Id = zero, Jd = zero;  // w
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float4 g = gr[i];
-                    if (i & 1) {
-                        Rb = ffma2(lo2(g), lo2(x[i]), Rb);
-                        Jb = ffma2(hi2(g), hi2(x[i]), Jb);
-                        Ib = ffma2(lo2(g), hi2(x[i]), Ib);
-                        Ib = ffma2(hi2(g), lo2(x[i]), Ib);
-                        Rd = ffma2(lo2(g), lo2(w[i]), Rd);
-                        Jd = ffma2(hi2(g), hi2(w[i]), Jd);
-                        Id = ffma2(lo2(g), hi2(w[i]), Id);
-                        Id = ffma2(hi2(g), lo2(w[i]), Id);
-                    } else {
-                        Ra = ffma2(lo2(g), lo2(x[i]), Ra);
-                        Ja = ffma2(hi2(g), hi2(x[i]), Ja);
-                        Ia = ffma2(lo2(g), hi2(x[i]), Ia);
-                        Ia = ffma2(hi2(g), lo2(x[i]), Ia);
-                        Rc = ffma2(lo2(g), lo2(w[i]), Rc);
-                        Jc = ffma2(hi2(g), hi2(w[i]), Jc);
-                        Ic = ffma2(lo2(g), hi2(w[i]), Ic);
-                        Ic = ffma2(hi2(g), lo2(w[i]), Ic);
-                    }
-                }
-                const float2 RX = __fadd2_rn(Ra, Rb), JX = __fadd2_rn(Ja, Jb), IX = __fadd2_rn(Ia, Ib);
-                const float2 RW = __fadd2_rn(Rc, Rd), JW = __fadd2_rn(Jc, Jd), IW = __fadd2_rn(Ic, Id);
-                const float2 zu = z[u * zs], su = s[u];
-                const float mu = dm[u], pu = dp[u];
-                const float xr = mu * (zu.x - ((RX.x + RX.y) - (JX.x + JX.y))), xi = mu * (zu.y - (IX.x + IX.y));
-                const float wr = pu * (su.x - ((RW.x + RW.y) - (JW.x + JW.y))), wi = pu * (su.y - (IW.x + IW.y));
-                float4& xp = x[u >> 1];
-                float4& wp = w[u >> 1];
-                if (u & 1) {
-                    xp.y = xr;
-                    xp.w = xi;
-                    wp.y = wr;
-                    wp.w = wi;
-                } else {
-                    xp.x = xr;
-                    xp.z = xi;
-                    wp.x = wr;
-                    wp.z = wi;
-                }
-            }
-        }
-    }
 }
 
 // Data fusion (Sec. III) of one subcarrier on the CTA's threads [t0, t0 + nt): lam holds
@@ -230,7 +160,11 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
     const int t_g = 32 * frame_warps(C * NS2 * AT);  // first thread of the Gram-column lanes
     const GLane gz = frame_lane(0, C, NS2, AT);     // symbol pairs: z (phase A), H w (phase C)
     const GLane gg = frame_lane(t_g, C, NU2, AT);   // column pairs of G_c (phase A); fusion (phase C)
-    const GLane gb = frame_lane(0, C, n_sym, 1);    // (cluster, symbol): uplink and downlink sweeps
+    // phase B: one lane per uplink or downlink tile; tile (c, j) is uplink symbol j for j < n_sym and
+    // downlink symbol j - n_sym otherwise, so one warp holds both kinds of tiles of a cluster and they
+    // read the same rows of G_c.  (One lane sweeping both x and w halves the row loads but leaves half
+    // the warps idle; the sweeps are latency-bound and that measured slower.)
+    const GLane gb = frame_lane(0, C, 2 * n_sym, 1);
     const ClusterTile ctz = tab[gz.c];
     const int zn0 = 2 * gz.j, zn1 = zn0 + 1;
 
@@ -338,25 +272,23 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
         if (tid == 0) nxt[b] = sched_next(d.sched, draw, ticket, fn, pl.n_sc);
         __syncthreads();
 
-        // Phase B: uplink and downlink sweeps of one (cluster, symbol) per lane.
+        // Phase B: uplink sweeps on x (right-hand side z in shared memory) and downlink sweeps on w
+        // (s read from global memory, cached after the first sweep).
         if (gb.active) {
-            const int n = gb.j, tile = gb.c * n_sym + n;
-            float4 x[UT / 2], w[UT / 2];
-            sweeps2<UT>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), Dm + gb.c * UT, Zs + tile, xs, Dp + gb.c * UT,
-                        io.S + ((size_t)f * n_sym + n) * U, x, w);
+            const bool ul = gb.j < n_sym;
+            const int n = ul ? gb.j : gb.j - n_sym;
+            const int tile = gb.c * n_sym + n;
+            const float* dd = (ul ? Dm : Dp) + gb.c * UT;
+            const float2* rhs = ul ? Zs + tile : io.S + ((size_t)f * n_sym + n) * U;
+            float4 x[UT / 2];
+            gram_sweeps<UT, 1>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, rhs, ul ? xs : 1u, 0, gb.mask, x);
+            float2* dst = (ul ? Zs : Ws) + tile;
 #pragma unroll
-            for (int u = 0; u < UT; ++u) {
-                if (u < U) {
-                    const float4& xp = x[u >> 1];
-                    const float4& wp = w[u >> 1];
-                    Zs[u * xs + tile] = (u & 1) ? make_float2(xp.y, xp.w) : make_float2(xp.x, xp.z);
-                    Ws[u * xs + tile] = (u & 1) ? make_float2(wp.y, wp.w) : make_float2(wp.x, wp.z);
-                }
-            }
-            if (n == 0) {
-                const float* dm = Dm + gb.c * UT;
+            for (int u = 0; u < UT; ++u)
+                if (u < U) dst[u * xs] = slice_entry<UT, 1>(x, u);
+            if (ul && n == 0) {
                 float msum = 0.f;
-                for (int u = 0; u < U; ++u) msum += dm[u] > 0.f ? dm[u] : __int_as_float(0x7f800000);
+                for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
                 lam[gb.c] = 1.f / msum;
             }
         }

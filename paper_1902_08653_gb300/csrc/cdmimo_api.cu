@@ -245,7 +245,7 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
     // (cluster, symbol); separate kernels: one phase after the other on the same warps
     const int threads = frame ? std::max(gram_phase_threads(p->C, (p->n_sym + 1) / 2, AT) +
                                              gram_phase_threads(p->C, (p->U + 1) / 2, AT),
-                                         gram_phase_threads(p->C, p->n_sym, 1))
+                                         gram_phase_threads(p->C, 2 * p->n_sym, 1))
                               : std::max({gram_phase_threads(p->C, p->n_sym, AT), gram_phase_threads(p->C, p->U, AT),
                                           gram_phase_threads(p->C, p->n_sym, 1)});
     if (threads > kMaxSpecializedThreads) return CDMIMO_ERR_UNSUPPORTED;
