@@ -190,6 +190,11 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
         const bool draw = fn < pl.n_sc;
         const unsigned ticket = sched_draw(d.sched, draw);
         if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
+        if (tid == 32 && fn < pl.n_sc) {  // the next subcarrier's y and s into L2 (read in its phases A, B)
+            constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
+            bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * eb, (uint32_t)n_sym * pl.B * eb);
+            bulk_prefetch_l2(io.S + (size_t)fn * n_sym * U, (uint32_t)(n_sym * U * 8));
+        }
 
         float alpha = __ldg(d.N0 + f) * pl.inv_Ex;
         float out_scale = 1.f;

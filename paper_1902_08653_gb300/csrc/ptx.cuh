@@ -43,6 +43,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// Asks the TMA engine to bring [src, src + bytes) into L2 (no registers, no completion to wait for).
+// src 16-byte aligned, bytes a multiple of 16; otherwise nothing is issued.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes)
+{
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) != 0u || (bytes & 15u) != 0u || bytes == 0u) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
