@@ -59,7 +59,7 @@ FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
 # L2 when a kernel ends are written back after it, outside the launch.
 NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.801216e6 + 1.029376e6,
                "cd_precode_gram_kernel": 41.527296e6 + 0.883968e6,
-               "cd_frame_gram_kernel": 76.330240e6 + 4.294144e6}
+               "cd_frame_gram_kernel": 75.962880e6 + 3.199744e6}
 
 WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
             "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
