@@ -168,11 +168,13 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
     const ClusterTile ctz = tab[gz.c];
     const int zn0 = 2 * gz.j, zn1 = zn0 + 1;
 
+    // Schedule: CTA i starts with subcarrier i; its next one is decided during the sweeps of the
+    // current one (static: + gridDim; dynamic: gridDim + a ticket drawn from the workspace counter),
+    // and that channel's copy is issued at the start of phase C into the other buffer, to be waited
+    // for at the next acquire.  Deciding this late lets a CTA that runs faster than its SM partner
+    // take more of the remaining subcarriers.
     int f = blockIdx.x;
-    if (pl.bulk && tid == 0) {
-        if (f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
-        if (f + (int)gridDim.x < pl.n_sc) arm_channel_copy<IN>(pl, &bar[1]);
-    }
+    if (pl.bulk && tid == 0 && f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
     __syncthreads();
     if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, f, Dst(0), &bar[0]);
     float4 y0[kPairs], y1[kPairs];
@@ -183,18 +185,9 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
         else load_lane_raw<IN, AT>(d.Y, base, 0, gz.a, y1);  // size 0: zeros
     };
 
-    int fn = f + (int)gridDim.x;
     int done = 0;
     for (int k = 0; f < pl.n_sc; ++k) {
         const int b = k & 1;
-        const bool draw = fn < pl.n_sc;
-        const unsigned ticket = sched_draw(d.sched, draw);
-        if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
-        if (tid == 32 && fn < pl.n_sc) {  // the next subcarrier's y and s into L2 (read in its phases A, B)
-            constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
-            bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * eb, (uint32_t)n_sym * pl.B * eb);
-            bulk_prefetch_l2(io.S + (size_t)fn * n_sym * U, (uint32_t)(n_sym * U * 8));
-        }
 
         float alpha = __ldg(d.N0 + f) * pl.inv_Ex;
         float out_scale = 1.f;
@@ -208,9 +201,9 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
             out_scale = __int_as_float(0x7fc00000);
             alpha = 0.f;
         }
-        if (!acquire_channel<IN>(pl, tab, d.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
-                                 d.sched != nullptr || fn + (int)gridDim.x < pl.n_sc)) {
-            if (pl.bulk && fn < pl.n_sc && tid == 0) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+        if (!acquire_channel<IN>(pl, tab, d.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u, false)) {
+            // copy timeout: no other copy is in flight; give this one a last bounded wait, then stop
+            if (pl.bulk && tid == 0) mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u);
             break;
         }
 
@@ -274,11 +267,12 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
                 }
             }
         }
-        if (tid == 0) nxt[b] = sched_next(d.sched, draw, ticket, fn, pl.n_sc);
         __syncthreads();
 
         // Phase B: uplink sweeps on x (right-hand side z in shared memory) and downlink sweeps on w
-        // (s read from global memory, cached after the first sweep).
+        // (s read from global memory, cached after the first sweep).  Thread 0 draws the next
+        // subcarrier now and hands it over before the barrier below (the atomic's latency is hidden).
+        const unsigned ticket = (d.sched && tid == 0) ? atomicAdd(d.sched, 1u) : 0u;
         if (gb.active) {
             const bool ul = gb.j < n_sym;
             const int n = ul ? gb.j : gb.j - n_sym;
@@ -297,9 +291,27 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
                 lam[gb.c] = 1.f / msum;
             }
         }
+        if (tid == 0) {
+            int nf = f + (int)gridDim.x;
+            if (d.sched) {
+                const unsigned v = gridDim.x + ticket;
+                nf = v < (unsigned)pl.n_sc ? (int)v : pl.n_sc;
+            }
+            nxt[b] = nf;
+            if (pl.bulk && nf < pl.n_sc) arm_channel_copy<IN>(pl, &bar[b ^ 1]);
+        }
         __syncthreads();
 
-        // Phase C: x_c = H_c w for two symbols per lane, then the normalization | uplink fusion.
+        // Phase C: the next subcarrier's channel copy (into the other buffer, last read in the
+        // previous iteration) and its y and s into L2; x_c = H_c w for two symbols per lane, then the
+        // normalization | uplink fusion.
+        const int fn = nxt[b];
+        if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
+        if (tid == 32 && fn < pl.n_sc) {
+            constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
+            bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * eb, (uint32_t)n_sym * pl.B * eb);
+            bulk_prefetch_l2(io.S + (size_t)fn * n_sym * U, (uint32_t)(n_sym * U * 8));
+        }
         if (gz.active) {
             const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ctz.soff) + gz.a;
             const float2* w0 = Ws + gz.c * n_sym + zn0;
@@ -322,7 +334,6 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
         __syncthreads();  // this channel buffer receives the copy issued at the next iteration's start
         ++done;
         f = fn;
-        fn = nxt[b];
     }
     sched_finish(d.sched, done, pl.n_sc);
 }
