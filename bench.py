@@ -581,9 +581,10 @@ def run_config5(args, dev):
     N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
     X = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64, device=dev)
     res = {}
-    runs = {"learned_K2": lambda: model.detect(H, Y, N0, CS, out=X)}
+    runs = {"learned_K2": lambda: model.detect(H, Y, N0, CS, out=X, form=args.form),
+            "learned_K2_residual_form": lambda: model.detect(H, Y, N0, CS, out=X, form="residual")}
     for Kp in (2, 3, 5):
-        runs[f"plain_K{Kp}"] = (lambda Kp=Kp: cdmimo.detect(H, Y, N0, CS, Kp, out=X))
+        runs[f"plain_K{Kp}"] = (lambda Kp=Kp: cdmimo.detect(H, Y, N0, CS, Kp, out=X, form=args.form))
     for name, fn in runs.items():
         med, _ = time_device(fn, args.steps, args.warmup, dev)
         fn()

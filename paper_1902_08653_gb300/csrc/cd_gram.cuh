@@ -60,7 +60,8 @@ __device__ __forceinline__ GLane gram_lane(int C, int J, int AT)
 // (uplink: alpha = N0/Ex, m_u of Algorithm 1; downlink: alpha = 0, p_u^2 of Algorithm 2).
 template <int AT, int UT>
 __device__ __forceinline__ void gram_columns(const GLane& g, int U, const ClusterTile* tab, const float2* Hb,
-                                             float alpha, float4* Gs, float* Ds, float* Ds0 = nullptr)
+                                             float alpha, float4* Gs, float* Ds, float* Ds0 = nullptr,
+                                             float* Er = nullptr)
 {
     constexpr int LP = AT * kPairs;
     if (!g.active) return;
@@ -82,6 +83,7 @@ __device__ __forceinline__ void gram_columns(const GLane& g, int U, const Cluste
                 const float den = s.x + alpha;
                 Ds[g.c * UT + u] = den > 0.f ? __fdividef(1.f, den) : 0.f;
                 if (Ds0) Ds0[g.c * UT + u] = s.x > 0.f ? __fdividef(1.f, s.x) : 0.f;
+                if (Er) Er[g.c * UT + u] = s.x;  // ||h_u||^2 itself (learned sweeps and fusion)
                 s = make_float2(0.f, 0.f);
             }
             G[u * (2 * UT) + col] = s.x;
@@ -182,6 +184,59 @@ __device__ __forceinline__ float2 slice_entry(const float4 (&x)[UT / 2 / SB], in
     return (u & 1) ? make_float2(xp.y, xp.w) : make_float2(xp.x, xp.z);
 }
 
+// Phase B of the learned unfolded CD (one lane per tile): sweep t applies
+// x_u <- x_u + tau_t (g - gamma_t alpha x_u) / (e_u + gamma_t alpha) with g = h_u^H r =
+// b_u - sum_{v != u} Gt_uv x_v - e_u x_u, i.e. x_u <- a (b_u - sum_{v != u} Gt_uv x_v) + (1 - tau_t) x_u
+// with a = tau_t / (e_u + gamma_t alpha); a non-positive denominator leaves x_u unchanged.
+template <int UT>
+__device__ __forceinline__ void gram_sweeps_learned(int U, int K, const float4* Grow, const float* e, float alpha,
+                                                    const cdmimo_learned* blk, const float2* b, uint32_t bs,
+                                                    float4 (&x)[UT / 2])
+{
+    constexpr int NP = UT / 2;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int t = 0; t < K; ++t) {
+        const float tau = __ldg(&blk->tau[t]), ga = __ldg(&blk->gamma[t]) * alpha;
+#pragma unroll
+        for (int u = 0; u < UT; ++u) {
+            if (u < U) {
+                const float4* gr = Grow + u * NP;
+                float2 R0 = make_float2(0.f, 0.f), I0 = R0, J0 = R0, R1 = R0, I1 = R0, J1 = R0;
+#pragma unroll
+                for (int i = 0; i < NP; i += 2) {
+                    const float4 g0 = gr[i], g1 = gr[i + 1];
+                    R0 = ffma2(lo2(g0), lo2(x[i]), R0);
+                    J0 = ffma2(hi2(g0), hi2(x[i]), J0);
+                    I0 = ffma2(lo2(g0), hi2(x[i]), I0);
+                    I0 = ffma2(hi2(g0), lo2(x[i]), I0);
+                    R1 = ffma2(lo2(g1), lo2(x[i + 1]), R1);
+                    J1 = ffma2(hi2(g1), hi2(x[i + 1]), J1);
+                    I1 = ffma2(lo2(g1), hi2(x[i + 1]), I1);
+                    I1 = ffma2(hi2(g1), lo2(x[i + 1]), I1);
+                }
+                const float2 R = __fadd2_rn(R0, R1), J = __fadd2_rn(J0, J1), I = __fadd2_rn(I0, I1);
+                const float2 bu = b[u * bs];
+                const float den = e[u] + ga;
+                const float a = den > 0.f ? tau * __fdividef(1.f, den) : 0.f;
+                const float keep = den > 0.f ? 1.f - tau : 1.f;
+                float4& xp = x[u >> 1];
+                const float2 xo = (u & 1) ? make_float2(xp.y, xp.w) : make_float2(xp.x, xp.z);
+                const float xr = fmaf(a, bu.x - ((R.x + R.y) - (J.x + J.y)), keep * xo.x);
+                const float xi = fmaf(a, bu.y - (I.x + I.y), keep * xo.y);
+                if (u & 1) {
+                    xp.y = xr;
+                    xp.w = xi;
+                } else {
+                    xp.x = xr;
+                    xp.z = xi;
+                }
+            }
+        }
+    }
+}
+
 // Shared-memory setup common to the Gram kernels: cluster table, barriers, zero padding columns of
 // both channel buffers, and zeroed Gram rows / energies (entries past U are never written again).
 template <int IN, int UT>
@@ -217,7 +272,7 @@ __device__ __forceinline__ void gram_setup(const CdPlan& pl, unsigned char* smem
 // ---------------------------------------------------------------------------------------------
 // Uplink: Algorithm 1 in Gram form + fusion (Sec. III).
 // ---------------------------------------------------------------------------------------------
-template <int IN, int AT, int UT>
+template <int IN, int AT, int UT, bool LEARNED>
 __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, const DetectIO io)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -227,7 +282,10 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, cons
     float4* Gs = reinterpret_cast<float4*>(smem + pl.off_G);  // [C][UT][UT/2]
     float* Ds = reinterpret_cast<float*>(smem + pl.off_E);    // [C][UT] m_u
     float2* Zs = reinterpret_cast<float2*>(smem + pl.off_X);  // [U][x_stride]: z, then each tile's x
-    float* lam = reinterpret_cast<float*>(smem + pl.off_lam); // [C] w_c = 1 / sum_u m_{u,c}
+    float* lam = reinterpret_cast<float*>(smem + pl.off_lam); // [C] w_c = 1 / sum_u m_{u,c}, or lambda_c
+    float* Er = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] ||h_u||^2 (learned plans)
+    float* mlp = reinterpret_cast<float*>(smem + pl.off_mlp); // [C][hidden] (learned fusion)
+    const cdmimo_learned* blk = reinterpret_cast<const cdmimo_learned*>(io.learned);
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);  // [2]
     int* nxt = reinterpret_cast<int*>(smem + pl.off_bar + 16);       // [2] schedule hand-off
@@ -235,6 +293,12 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, cons
     const int tid = threadIdx.x;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
     const uint32_t xs_stride = x_stride(pl);
+    bool learned_ok = true;
+    if (LEARNED) {
+        const int hd = __ldg(&blk->hidden);
+        learned_ok = __ldg(&blk->K) == pl.K && __ldg(&blk->U) == U && hd >= 1 && hd <= CDMIMO_MAX_HIDDEN;
+        if (!learned_ok && tid == 0 && blockIdx.x == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_LEARNED);
+    }
     gram_setup<IN, UT>(pl, smem, tab, bar, true);
     const GLane gz = gram_lane(C, n_sym, AT);  // phase A: (cluster, symbol) tiles, y in registers
     const GLane gb = gram_lane(C, n_sym, 1);   // phase B: one lane per (cluster, symbol)
@@ -272,6 +336,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, cons
             out_scale = __int_as_float(0x7fc00000);
             alpha = 0.f;
         }
+        if (LEARNED && !learned_ok) out_scale = __int_as_float(0x7fc00000);
         if (!acquire_channel<IN>(pl, tab, io.H, f, Hbuf(b), Stg(b), &bar[b], (uint32_t)(k >> 1) & 1u,
                                  io.sched != nullptr || fn + (int)gridDim.x < pl.n_sc)) {
             if (pl.bulk && fn < pl.n_sc && tid == 0) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
@@ -283,7 +348,7 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, cons
             raw_to_pairs(r);
             gram_rhs<AT>(gz, U, n_sym, xs_stride, tab, Hbuf(b), r, Zs);
         }
-        gram_columns<AT, UT>(gg, U, tab, Hbuf(b), alpha, Gs, Ds);
+        gram_columns<AT, UT>(gg, U, tab, Hbuf(b), alpha, Gs, Ds, nullptr, LEARNED ? Er : nullptr);
         if (tid == 0) nxt[b] = sched_next(io.sched, draw, ticket, fn, pl.n_sc);
         if (gz.active && fn < pl.n_sc)  // next subcarrier's y (r is free now)
             load_lane_raw<IN, AT>(io.Y, ((size_t)fn * n_sym + gz.j) * pl.B + ctz.off, ctz.size, gz.a, r);
@@ -296,7 +361,11 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, cons
             const int tile = gb.c * n_sym + gb.j;
             const float* d = Ds + gb.c * UT;
             float4 x[UT / 2];
-            gram_sweeps<UT, 1>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), d, Zs + tile, xs_stride, 0, gb.mask, x);
+            if (LEARNED)
+                gram_sweeps_learned<UT>(U, learned_ok ? pl.K : 0, Gs + (size_t)gb.c * UT * (UT / 2), Er + gb.c * UT,
+                                        alpha, blk, Zs + tile, xs_stride, x);
+            else
+                gram_sweeps<UT, 1>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), d, Zs + tile, xs_stride, 0, gb.mask, x);
 #pragma unroll
             for (int u = 0; u < UT; ++u)  // own tile column: z is no longer read
                 if (u < U) Zs[u * xs_stride + tile] = slice_entry<UT, 1>(x, u);
@@ -310,7 +379,14 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_gram_kernel(const CdPlan pl, cons
 
         // Phase C: fusion.  The next writes of Zs, Gs, Ds and lam come after the next acquire's
         // barriers, and the copy into this iteration's channel buffer after the barrier above.
-        fuse_subcarrier<false>(pl, io, f, lam, Zs, xs_stride, out_scale);
+        if (LEARNED && pl.fuse == CDMIMO_FUSE_LEARNED) {
+            learned_lambda(pl, blk, learned_ok, alpha, tab, mlp, lam, io.lam, f,
+                           [&](int c, int j) { return Er[c * UT + j]; });
+            __syncthreads();
+            fuse_subcarrier<true>(pl, io, f, lam, Zs, xs_stride, out_scale);
+        } else {
+            fuse_subcarrier<false>(pl, io, f, lam, Zs, xs_stride, out_scale);
+        }
         ++done;
         f = fn;
         fn = nxt[b];

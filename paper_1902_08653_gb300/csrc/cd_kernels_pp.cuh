@@ -289,6 +289,59 @@ __device__ __forceinline__ void fuse_subcarrier(const CdPlan& pl, const DetectIO
     }
 }
 
+// Learned fusion weights of one subcarrier: lambda = softmax_c(logit_c), logit_c = b2 + sum_kk
+// w2[kk] relu(z_kk), z_kk = W1[kk] . phi_c + b1[kk] with phi_c = [e(c, u) / B_c (u < U),
+// log10(max(alpha, 1e-6))] and e(c, u) = ||h_{u,c}||^2 (from the caller's accessor).  Warp 0 writes
+// lam (and lam_out[f] if given): the caller puts a barrier before reading it.  Uses mlp[C][hidden]
+// as scratch (one internal barrier).
+template <typename EnergyFn>
+__device__ __forceinline__ void learned_lambda(const CdPlan& pl, const cdmimo_learned* blk, bool learned_ok, float alpha,
+                                               const ClusterTile* tab, float* mlp, float* lam, float* lam_out, int f,
+                                               EnergyFn energy)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, C = pl.C, U = pl.U;
+    const int Hd = learned_ok ? __ldg(&blk->hidden) : 1;
+    const int F = U + 1;
+    const float la = log10f(fmaxf(alpha, 1e-6f));
+    for (int i = tid; i < C * Hd; i += blockDim.x) {
+        const int c = i / Hd, kk = i - c * Hd;
+        const float inv_bc = 1.f / (float)tab[c].size;
+        const unsigned short* w1 = blk->W1 + (size_t)kk * F;
+        float z = __ldg(&blk->b1[kk]);
+        for (int j = 0; j < U; ++j) z = fmaf(bf16_bits_to_float(__ldg(w1 + j)), energy(c, j) * inv_bc, z);
+        z = fmaf(bf16_bits_to_float(__ldg(w1 + U)), la, z);
+        mlp[i] = bf16_bits_to_float(__ldg(&blk->w2[kk])) * fmaxf(z, 0.f);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float lg[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c = lane + 32 * q;
+            if (c < C) {
+                float s = __ldg(&blk->b2);
+                for (int kk = 0; kk < Hd; ++kk) s += mlp[c * Hd + kk];
+                lg[q] = s;
+            }
+        }
+        float mx = fmaxf(lg[0], lg[1]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float ex[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) ex[q] = lane + 32 * q < C ? __expf(lg[q] - mx) : 0.f;
+        const float tot = warp_sum(ex[0] + ex[1]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c = lane + 32 * q;
+            if (c < C) {
+                lam[c] = ex[q] / tot;
+                if (lam_out) lam_out[(size_t)f * C + c] = ex[q] / tot;
+            }
+        }
+    }
+}
+
 // Column energies of one cluster from a staged buffer (K = 0 only: no sweep computed them).
 __device__ __forceinline__ float row_energy(const float2* row, int L)
 {
@@ -493,48 +546,8 @@ __global__ void __maxnreg__(kPPRegs) cd_detect_pp_kernel(const CdPlan pl, const 
 
         if (LEARNED) {  // lambda_c from the learned fusion (or from m, below), then a barrier
             if (pl.fuse == CDMIMO_FUSE_LEARNED) {
-                // Learned fusion: hidden unit kk of cluster c, z = W1[kk] . phi_c + b1[kk], contributes
-                // w2[kk] relu(z) to logit_c; phi_c = [||h_{u,c}||^2 / B_c (u < U), log10(max(alpha, 1e-6))].
-                const int Hd = learned_ok ? __ldg(&blk->hidden) : 1;
-                const int F = U + 1;
-                const float la = log10f(fmaxf(alpha, 1e-6f));
-                for (int i = tid; i < C * Hd; i += blockDim.x) {
-                    const int c = i / Hd, kk = i - c * Hd;
-                    const float inv_bc = 1.f / (float)tab[c].size;
-                    const unsigned short* w1 = blk->W1 + (size_t)kk * F;
-                    float z = __ldg(&blk->b1[kk]);
-                    for (int j = 0; j < U; ++j) z = fmaf(bf16_bits_to_float(__ldg(w1 + j)), Ks[j * xs_stride + c * n_sym].x * inv_bc, z);
-                    z = fmaf(bf16_bits_to_float(__ldg(w1 + U)), la, z);
-                    mlp[i] = bf16_bits_to_float(__ldg(&blk->w2[kk])) * fmaxf(z, 0.f);
-                }
-                __syncthreads();
-                if (warp == 0) {
-                    float lg[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int c = lane + 32 * q;
-                        if (c < C) {
-                            float s = __ldg(&blk->b2);
-                            for (int kk = 0; kk < Hd; ++kk) s += mlp[c * Hd + kk];
-                            lg[q] = s;
-                        }
-                    }
-                    float mx = fmaxf(lg[0], lg[1]);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                    float ex[2];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) ex[q] = lane + 32 * q < C ? __expf(lg[q] - mx) : 0.f;
-                    const float tot = warp_sum(ex[0] + ex[1]);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int c = lane + 32 * q;
-                        if (c < C) {
-                            lam[c] = ex[q] / tot;
-                            if (io.lam) io.lam[(size_t)f * C + c] = ex[q] / tot;
-                        }
-                    }
-                }
+                learned_lambda(pl, blk, learned_ok, alpha, tab, mlp, lam, io.lam, f,
+                               [&](int c, int j) { return Ks[j * xs_stride + c * n_sym].x; });
             } else if (warp == 0) {
                 // Fusion weights: lambda_c proportional to 1 / sum_u m_{u,c} (a zero m marks a skipped
                 // column, whose (||h||^2 + N0/Ex)^{-1} is infinite).

@@ -225,7 +225,7 @@ int plan_auto(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
 int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool auto_rules, CdPlan* pl,
                     bool frame = false)
 {
-    if (p->U > 16 || (detect && p->learned)) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->U > 16 || (frame && p->learned)) return CDMIMO_ERR_UNSUPPORTED;
     if (int rc = build_plan(p, 16, detect, H, pl)) return rc;
     if (!pl->packed) return CDMIMO_ERR_UNSUPPORTED;
     const long U = p->U, n_sym = p->n_sym, K = p->K;
@@ -267,6 +267,12 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
         o = align16(o + (unsigned)U * xs * 8u);
         pl->off_E2 = o;
         o = align16(o + C * UTu * 4u);
+    }
+    if (pl->learned) {  // ||h_u||^2 per cluster, and the learned fusion's hidden activations
+        pl->off_E2 = o;
+        o = align16(o + C * UTu * 4u);
+        pl->off_mlp = o;
+        o = align16(o + C * (unsigned)CDMIMO_MAX_HIDDEN * 4u);
     }
     pl->off_lam = o;
     o = align16(o + C * 4u);

@@ -110,3 +110,26 @@ def test_frame_low_precision_storage(dev, kind):
     assert_vectors_close(X.cpu().numpy(), Xo, TOL, f"frame Xhat {kind}")
     assert_vectors_close(P.cpu().numpy(), Po, TOL, f"frame Xdl {kind}")
     assert cdmimo.device_status(clear=True) == 0
+
+
+def test_frame_edge_cases(dev):
+    cs, U = [32] * 4, 8
+    z = lambda *s: torch.zeros(s, dtype=torch.complex64, device=dev)
+    # empty batch: a no-op that returns the (empty) outputs
+    X, P = cdmimo.detect_precode(z(0, U, 128), z(0, 3, 128), torch.zeros(0, device=dev), z(0, 3, U), cs, 3)
+    assert X.shape == (0, 3, U) and P.shape == (0, 3, 128)
+    d = wl.uplink(12, 5, 1, 128, U, snr_db=15.0)  # one symbol per subcarrier, fewer subcarriers than CTAs
+    H32, H64 = wl.as_c64(d["H"])
+    Y32, Y64 = wl.as_c64(d["Y"])
+    S32, S64 = wl.as_c64(d["X"])
+    N0 = d["N0"].astype(np.float32)
+    for K, form in ((0, "gram"), (2, "gram"), (2, "auto")):
+        X, P = cdmimo.detect_precode(t(H32, dev), t(Y32, dev), t(N0, dev), t(S32, dev), cs, K, form=form)
+        if K == 0:
+            assert not X.abs().any() and not P.abs().any()
+            continue
+        Xo, _, _ = orc.detect(H64, Y64, N0.astype(np.float64), cs, K, threads=4)
+        Po = orc.precode(H64, S64, cs, K, threads=4)
+        assert_vectors_close(X.cpu().numpy(), Xo, TOL, f"frame Xhat {form}")
+        assert_vectors_close(P.cpu().numpy(), Po, TOL, f"frame Xdl {form}")
+    assert cdmimo.device_status(clear=True) == 0

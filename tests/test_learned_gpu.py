@@ -101,6 +101,31 @@ def test_learned_inference_parity(dev, K, n_sym):
     assert cdmimo.device_status(clear=True) == 0
 
 
+@pytest.mark.parametrize("form", ["gram", "residual"])
+@pytest.mark.parametrize("cs,U,K,n_sym,fuse", [([32] * 8, 16, 3, 14, "learned"), ([16] * 6, 8, 2, 9, "learned"),
+                                               ([64] * 4, 16, 2, 14, "colnorm"), ([32] * 3, 5, 4, 7, "equal")])
+def test_learned_forms_match_oracle(dev, form, cs, U, K, n_sym, fuse):
+    """Learned sweeps in both forms: the Gram form sums z_u - sum_v G_uv x_v, the residual form
+    h_u^H r (different rounding), both against the FP64 oracle with the same parameters."""
+    Hd = 32
+    m = random_master(70 + K + U, K, U, Hd)
+    model = learned.LearnedCD(K, U, Hd, master=torch.from_numpy(m), device=dev)
+    n_sc = 19
+    _, (H, Y, N0), (H64, Y64, N064) = _inputs(80 + U, n_sc, n_sym, sum(cs), U, dev)
+    assert cdmimo.selected_form(cdmimo.OP_DETECT, n_sc, n_sym, sum(cs), U, cs, K, H=H, form=form) == form
+    lam = torch.zeros((n_sc, len(cs)), dtype=torch.float32, device=dev)
+    Xc = torch.zeros((n_sc, len(cs), n_sym, U), dtype=torch.complex64, device=dev)
+    X = cdmimo.detect(H, Y, N0, cs, K, fuse=fuse, learned=model.block, lam=lam, Xc=Xc, form=form).cpu().numpy()
+    Xo, Xco, lamo = orc.learned_forward(H64, Y64, N064, cs, K, as_used(m, K, U, Hd), Hd, threads=8)
+    if fuse != "learned":  # learned per-cluster estimates, fused with the plain detector's weights
+        lamo = orc.detect(H64, Y64, N064, cs, 0, fuse=fuse, threads=8)[2]
+        Xo = np.einsum("fc,fcnu->fnu", lamo, Xco)
+    assert_vectors_close(Xc.cpu().numpy(), Xco, 1e-4, f"learned Xc ({form})")
+    np.testing.assert_allclose(lam.cpu().numpy(), lamo, rtol=2e-5, atol=1e-7)
+    assert_vectors_close(X, Xo, 1e-4, f"learned Xhat ({form}, {fuse})")
+    assert cdmimo.device_status(clear=True) == 0
+
+
 def test_untrained_model_is_plain_cd_with_equal_fusion(dev):
     U, cs = 16, [32] * 8
     model = learned.LearnedCD(2, U, 64, seed=3, device=dev)
@@ -110,10 +135,11 @@ def test_untrained_model_is_plain_cd_with_equal_fusion(dev):
     assert_vectors_close(Xl.cpu().numpy(), Xp.cpu().numpy(), 1e-5, "reduction")
 
 
-def test_learned_block_mismatch_is_flagged(dev):
+@pytest.mark.parametrize("form", ["gram", "residual"])
+def test_learned_block_mismatch_is_flagged(dev, form):
     model = learned.LearnedCD(2, 16, 64, device=dev)
     _, (H, Y, N0), _ = _inputs(6, 3, 2, 256, 16, dev)
-    X = cdmimo.detect(H, Y, N0, [32] * 8, 3, fuse="learned", learned=model.block).cpu().numpy()
+    X = cdmimo.detect(H, Y, N0, [32] * 8, 3, fuse="learned", learned=model.block, form=form).cpu().numpy()
     assert cdmimo.device_status(clear=True) & cdmimo.DEV_BAD_LEARNED
     assert np.all(np.isnan(X))
 
