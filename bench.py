@@ -261,17 +261,13 @@ def run_cuda(args, rank, world, local_rank):
     Hdh = Hh if frame else torch.from_numpy(wl.as_c64(dl["H"])[0]).pin_memory()
     Xh = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64).pin_memory()
     Xdh = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64).pin_memory()
-    if frame:
-        Hb, Yb, Nb, Sb = torch.empty_like(H), torch.empty_like(Y), torch.empty_like(N0), torch.empty_like(S)
+    if frame:  # cdmimo_detect_precode_host: chunked; uploads, kernels and downloads overlap
+        ws_fr = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_FRAME, N_SC, N_SYM, B, U, CS, K), dtype=torch.uint8,
+                            device=dev)
 
         def e2e_step():
-            Hb.copy_(Hh, non_blocking=True)
-            Yb.copy_(Yh, non_blocking=True)
-            Nb.copy_(N0h, non_blocking=True)
-            Sb.copy_(Sh, non_blocking=True)
-            cdmimo.detect_precode(Hb, Yb, Nb, Sb, CS, K, out=Xhat, out_dl=Xdl, stream=stream, form=args.form)
-            Xh.copy_(Xhat, non_blocking=True)
-            Xdh.copy_(Xdl, non_blocking=True)
+            cdmimo.detect_precode_host(Hh, Yh, N0h, Sh, CS, K, Xh, Xdh, ws_fr, n_chunks=args.e2e_chunks,
+                                       stream=stream, form=args.form)
     else:
         ws_ul = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K),
                             dtype=torch.uint8, device=dev)
@@ -356,7 +352,9 @@ def run_cuda(args, rank, world, local_rank):
         "mse_vs_mmse": mse,
         "ber": ber,
         "e2e": {"value": whole_job_value(vec_step, world, e2e_ms), "unit": "vectors/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "api": "cdmimo_detect_precode_host (chunks: %s)" % (args.e2e_chunks or "default") if frame
+                else "cdmimo_detect_host + cdmimo_precode_host"},
         "gpu_launches": (1 if frame and kernels[0]["kernel"] == "cd_frame_gram_kernel" else 2) * args.steps,
         "clocks": clocks,
         "wall_s": wall,
@@ -636,6 +634,8 @@ def main():
     ap.add_argument("--profile", choices=["detect", "precode", "frame"], default=None,
                     help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu")
     ap.add_argument("--form", choices=["auto", "residual", "gram"], default="auto", help="CD evaluation form")
+    ap.add_argument("--e2e-chunks", type=int, default=0,
+                    help="chunks of the pipelined host-buffer frame in the e2e leg (0: the library's default)")
     ap.add_argument("--step", choices=["frame", "separate"], default="frame",
                     help="frame (default): UL + DL on one channel, one call; separate: two calls, two channels")
     args = ap.parse_args()

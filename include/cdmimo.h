@@ -199,6 +199,32 @@ int cdmimo_detect_host(const cdmimo_params* p, const void* H_host, const void* Y
 int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* S_host, void* Xdl_host,
                         void* dev_ws, size_t ws_bytes, void* stream);
 
+/*
+ * cdmimo_detect_precode with HOST buffers, pipelined over chunks of subcarriers so that the uploads,
+ * the kernels and the downloads overlap.  The n_sc subcarriers are split into n_chunks contiguous
+ * chunks, the last half the size of the others (chunk i starts at n_sc 2i / (2 n_chunks - 1));
+ * n_chunks = 0: the library's default, 5; more chunks than subcarriers: empty chunks are skipped.  `stream` first copies N0 and S whole into dev_ws, then per
+ * chunk the chunk's H and Y; a kernel stream waits for that copy and runs the frame on the chunk
+ * (static schedule); a
+ * download stream waits for that kernel and copies the chunk's Xhat and Xdl back.  The uploads thus
+ * run back to back on `stream` while earlier chunks compute and download (the two copy directions
+ * run concurrently).  Before returning, the call makes `stream` wait for the last download: as for
+ * every other entry point, the work is ordered after what `stream` holds and the caller synchronizes
+ * `stream` only; the next call's uploads cannot overwrite staging that a download still reads.
+ * n_chunks = 1: everything on `stream`, in order.  Results equal cdmimo_detect_precode's bit for bit.
+ * H_host, Y_host (dtype p->in_dtype), N0_host, S_host, Xhat_host, Xdl_host: HOST arrays in the
+ * layouts of cdmimo_detect_precode; pinned (page-locked) memory is needed for the copies to be
+ * asynchronous.  16-bit storage: p->h_scale and p->y_scale are HOST arrays [n_sc] here.
+ * dev_ws: DEVICE scratch of at least cdmimo_host_workspace_size(p, CDMIMO_OP_FRAME) bytes, 256-byte
+ * aligned (else CDMIMO_ERR_WORKSPACE).
+ * The first pipelined call on a host thread creates, for the current device, the two streams
+ * (non-blocking) and three CUDA events it uses (released when the thread exits); later calls create
+ * nothing.  An error return may leave earlier chunks enqueued.
+ */
+int cdmimo_detect_precode_host(const cdmimo_params* p, const void* H_host, const void* Y_host, const float* N0_host,
+                               const void* S_host, void* Xhat_host, void* Xdl_host, int n_chunks, void* dev_ws,
+                               size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------------------------- */
 /* Batched uneven launch (an extension beyond the paper).                                          */
 /* ---------------------------------------------------------------------------------------------- */
@@ -366,13 +392,15 @@ int cdmimo_synth_uplink(unsigned long long seed, int n_sc, int n_sym, int B, int
 /* ---------------------------------------------------------------------------------------------- */
 #define CDMIMO_OP_DETECT 0
 #define CDMIMO_OP_PRECODE 1
+#define CDMIMO_OP_FRAME 2 /* cdmimo_detect_precode_host staging (cdmimo_host_workspace_size only) */
 
 /* Bytes of the optional device workspace of cdmimo_detect / cdmimo_precode (the schedule counters:
  * 256 for every p). */
 size_t cdmimo_workspace_size(const cdmimo_params* p, int op);
 
-/* Device staging bytes that cdmimo_detect_host / cdmimo_precode_host need for p (the last 256 hold
- * the schedule counters, which every host call zeroes before its launch). */
+/* Device staging bytes that cdmimo_detect_host / cdmimo_precode_host (op DETECT / PRECODE: the last
+ * 256 hold the schedule counters, which every host call zeroes before its launch) or
+ * cdmimo_detect_precode_host (op FRAME) need for p; 0 for an invalid p or op. */
 size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
 
 /* The evaluation form (CDMIMO_FORM_RESIDUAL or CDMIMO_FORM_GRAM) that cdmimo_detect (op =

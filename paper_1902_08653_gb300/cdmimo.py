@@ -34,7 +34,7 @@ LEARNED_BLOCK_BYTES = 4 * 4 + 16 * 4 * 2 + 64 * 4 + 4 * 4 + 64 * 65 * 2 + 64 * 2
 C64, C16F, C16BF = 0, 1, 2
 FUSE = {"equal": 0, "colnorm": 1, "learned": 2}
 FORM = {"auto": 0, "residual": 1, "gram": 2}
-OP_DETECT, OP_PRECODE = 0, 1
+OP_DETECT, OP_PRECODE, OP_FRAME = 0, 1, 2
 
 
 class CdmimoError(RuntimeError):
@@ -86,6 +86,7 @@ def lib():
             "cdmimo_fuse": ([I, I, I, I, P, P, I, P, P], I),
             "cdmimo_detect_host": ([PP, P, P, P, P, P, S, P], I),
             "cdmimo_precode_host": ([PP, P, P, P, P, S, P], I),
+            "cdmimo_detect_precode_host": ([PP, P, P, P, P, P, P, I, P, S, P], I),
             "cdmimo_workspace_size": ([PP, I], S),
             "cdmimo_selected_form": ([PP, I, P], I),
             "cdmimo_detect_precode": ([PP, P, P, P, P, P, P, P, S, P], I),
@@ -347,6 +348,26 @@ def detect_host(H, Y, N0, cluster_size, K, Xhat, dev_ws, *, Ex=1.0, fuse="colnor
                                   dev_ws.numel() * dev_ws.element_size(), _stream(stream))
     _check("cdmimo_detect_host", rc)
     return Xhat
+
+
+def detect_precode_host(H, Y, N0, S, cluster_size, K, Xhat, Xdl, dev_ws, *, Ex=1.0, fuse="colnorm", rho=1.0,
+                        h_scale=None, y_scale=None, n_chunks=0, stream=None, form="auto"):
+    """cdmimo_detect_precode_host: one TDD frame on host (pinned) buffers, pipelined over n_chunks
+    chunks of subcarriers (0: the library's default; 1: no pipelining).  dev_ws: device bytes of
+    host_workspace_size(OP_FRAME, ...).  The caller synchronizes `stream` before reading Xhat, Xdl."""
+    for t, nm in ((H, "H"), (Y, "Y"), (N0, "N0"), (S, "S"), (Xhat, "Xhat"), (Xdl, "Xdl")):
+        _need(t, nm, dev=False)
+    _need(dev_ws, "dev_ws")
+    dt = _dtype_of(H)
+    n_sc, U, B = H.shape[:3]
+    n_sym = Y.shape[1]
+    p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, Ex=Ex, fuse=fuse, rho=rho, in_dtype=dt,
+                          h_scale=h_scale, y_scale=y_scale, form=form)
+    rc = lib().cdmimo_detect_precode_host(ctypes.byref(p), _ptr(H), _ptr(Y), _ptr(N0), _ptr(S), _ptr(Xhat), _ptr(Xdl),
+                                          int(n_chunks), _ptr(dev_ws), dev_ws.numel() * dev_ws.element_size(),
+                                          _stream(stream))
+    _check("cdmimo_detect_precode_host", rc)
+    return Xhat, Xdl
 
 
 def precode_host(H, S, cluster_size, K, Xdl, dev_ws, *, rho=1.0, stream=None):

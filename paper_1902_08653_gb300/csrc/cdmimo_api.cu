@@ -432,6 +432,7 @@ size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Bytes of the optional device workspace of cdmimo_detect / cdmimo_precode: the three schedule
 // counters, padded to one 256-byte line.
 constexpr size_t kSchedBytes = 256;
+constexpr int kHostFrameChunks = 5;  // default chunks of the pipelined host-buffer frame
 
 // The schedule counters in a caller's workspace: NULL -> static schedule; else it must be 16-byte
 // aligned and hold kSchedBytes.
@@ -805,16 +806,15 @@ int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* X
     return precode_impl(p, H, S, Xdl, sched, static_cast<cudaStream_t>(stream));
 }
 
-int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
-                          const void* S, void* Xdl, void* workspace, size_t ws_bytes, void* stream)
+namespace {
+
+int frame_impl(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, const void* S,
+               void* Xdl, unsigned* sched, cudaStream_t s)
 {
-    unsigned* sched;
-    if (int rc = sched_from_workspace(workspace, ws_bytes, &sched)) return rc;
     if (int rc = validate(p)) return rc;
     if (int rc = check_detect_ptrs(p, H, Y, N0, Xhat)) return rc;
     if (p->n_sc == 0) return CDMIMO_OK;
     if (!S || !Xdl || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     CdPlan pl;
     if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
         build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK) {
@@ -825,6 +825,124 @@ int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, 
     // otherwise the two calls, each in the form it selects
     if (int rc = detect_impl(p, H, Y, N0, Xhat, nullptr, nullptr, sched, s)) return rc;
     return precode_impl(p, H, S, Xdl, sched, s);
+}
+
+// Per host thread and device, for the pipelined host-buffer frame: a kernel stream and a download
+// stream (non-blocking, created on first use) and one event per hand-off (upload -> kernel,
+// kernel -> download, download -> caller's stream).  Each record is followed by its wait before the
+// event is recorded again, so the events are reused by every chunk and call.
+struct HostPipe {
+    cudaStream_t sk = nullptr, sd = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    ~HostPipe()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (sk) cudaStreamDestroy(sk);
+        if (sd) cudaStreamDestroy(sd);
+    }
+};
+constexpr int kMaxPipeDevices = 64;
+thread_local HostPipe t_host_pipe[kMaxPipeDevices];
+
+int host_pipe(HostPipe** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxPipeDevices) return CDMIMO_ERR_UNSUPPORTED;
+    HostPipe& h = t_host_pipe[dev];
+    for (cudaEvent_t& e : h.ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    for (cudaStream_t* q : {&h.sk, &h.sd})
+        if (!*q && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess) return CDMIMO_ERR_CUDA;
+    *out = &h;
+    return CDMIMO_OK;
+}
+
+}  // namespace
+
+int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
+                          const void* S, void* Xdl, void* workspace, size_t ws_bytes, void* stream)
+{
+    unsigned* sched;
+    if (int rc = sched_from_workspace(workspace, ws_bytes, &sched)) return rc;
+    return frame_impl(p, H, Y, N0, Xhat, S, Xdl, sched, static_cast<cudaStream_t>(stream));
+}
+
+int cdmimo_detect_precode_host(const cdmimo_params* p, const void* H_host, const void* Y_host, const float* N0_host,
+                               const void* S_host, void* Xhat_host, void* Xdl_host, int n_chunks, void* dev_ws,
+                               size_t ws_bytes, void* stream)
+{
+    if (int rc = validate(p)) return rc;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H_host || !Y_host || !N0_host || !S_host || !Xhat_host || !Xdl_host || n_chunks < 0)
+        return CDMIMO_ERR_INVALID_ARG;
+    if (p->in_dtype != CDMIMO_C64 && (!p->h_scale || !p->y_scale)) return CDMIMO_ERR_INVALID_ARG;
+    const size_t need = cdmimo_host_workspace_size(p, CDMIMO_OP_FRAME);
+    if (!dev_ws || !aligned(dev_ws, 256) || ws_bytes < need) return CDMIMO_ERR_WORKSPACE;
+    const int n = p->n_sc, nch = std::min(n_chunks > 0 ? n_chunks : kHostFrameChunks, n);
+    cudaStream_t su = static_cast<cudaStream_t>(stream), sk = su, sd = su;
+    HostPipe* hp = nullptr;
+    if (nch > 1) {
+        if (int rc = host_pipe(&hp)) return rc;
+        sk = hp->sk;
+        sd = hp->sd;
+    }
+    // per-subcarrier bytes of each staged array, and the staging layout (as in the size query)
+    const size_t eb = elem_bytes(p->in_dtype);
+    const size_t hs = (size_t)p->U * p->B * eb, ys = (size_t)p->n_sym * p->B * eb;
+    const size_t ss = (size_t)p->n_sym * p->U * 8, xs = ss, xds = (size_t)p->n_sym * p->B * 8;
+    char* dH = static_cast<char*>(dev_ws);
+    char* dY = dH + round256(n * hs);
+    char* dN = dY + round256(n * ys);
+    char* dS = dN + round256((size_t)n * 4);
+    char* dX = dS + round256(n * ss);
+    char* dXd = dX + round256(n * xs);
+    float* dhs = reinterpret_cast<float*>(dXd + round256(n * xds));
+    float* dys = reinterpret_cast<float*>(reinterpret_cast<char*>(dhs) + round256((size_t)n * 4));
+    const char* hH = static_cast<const char*>(H_host);
+    const char* hY = static_cast<const char*>(Y_host);
+    const char* hS = static_cast<const char*>(S_host);
+    char* hX = static_cast<char*>(Xhat_host);
+    char* hXd = static_cast<char*>(Xdl_host);
+    auto hand_off = [&](cudaEvent_t e, cudaStream_t from, cudaStream_t to) {
+        return from == to || (cudaEventRecord(e, from) == cudaSuccess && cudaStreamWaitEvent(to, e, 0) == cudaSuccess);
+    };
+    // the small arrays whole first (a copy has a fixed cost), then H and Y chunk by chunk
+    if (cudaMemcpyAsync(dN, N0_host, (size_t)n * 4, cudaMemcpyHostToDevice, su) != cudaSuccess ||
+        cudaMemcpyAsync(dS, hS, n * ss, cudaMemcpyHostToDevice, su) != cudaSuccess)
+        return CDMIMO_ERR_CUDA;
+    if (p->in_dtype != CDMIMO_C64) {
+        if (cudaMemcpyAsync(dhs, p->h_scale, (size_t)n * 4, cudaMemcpyHostToDevice, su) != cudaSuccess ||
+            cudaMemcpyAsync(dys, p->y_scale, (size_t)n * 4, cudaMemcpyHostToDevice, su) != cudaSuccess)
+            return CDMIMO_ERR_CUDA;
+    }
+    // chunk i starts at subcarrier n 2i / (2 nch - 1): the last chunk is half the size of the others,
+    // which shortens the kernel and download that follow the last upload
+    const size_t den = 2 * (size_t)nch - 1;
+    for (int i = 0; i < nch; ++i) {
+        const size_t f0 = (size_t)n * 2 * i / den, f1 = i + 1 < nch ? (size_t)n * 2 * (i + 1) / den : (size_t)n;
+        const size_t m = f1 - f0;
+        if (m == 0) continue;
+        if (cudaMemcpyAsync(dH + f0 * hs, hH + f0 * hs, m * hs, cudaMemcpyHostToDevice, su) != cudaSuccess ||
+            cudaMemcpyAsync(dY + f0 * ys, hY + f0 * ys, m * ys, cudaMemcpyHostToDevice, su) != cudaSuccess)
+            return CDMIMO_ERR_CUDA;
+        if (!hand_off(hp ? hp->ev[0] : nullptr, su, sk)) return CDMIMO_ERR_CUDA;
+        cdmimo_params q = *p;
+        q.n_sc = (int)m;
+        if (p->in_dtype != CDMIMO_C64) {
+            q.h_scale = dhs + f0;
+            q.y_scale = dys + f0;
+        }
+        if (int rc = frame_impl(&q, dH + f0 * hs, dY + f0 * ys, reinterpret_cast<const float*>(dN) + f0, dX + f0 * xs,
+                                dS + f0 * ss, dXd + f0 * xds, nullptr, sk))
+            return rc;
+        if (!hand_off(hp ? hp->ev[1] : nullptr, sk, sd)) return CDMIMO_ERR_CUDA;
+        if (cudaMemcpyAsync(hX + f0 * xs, dX + f0 * xs, m * xs, cudaMemcpyDeviceToHost, sd) != cudaSuccess ||
+            cudaMemcpyAsync(hXd + f0 * xds, dXd + f0 * xds, m * xds, cudaMemcpyDeviceToHost, sd) != cudaSuccess)
+            return CDMIMO_ERR_CUDA;
+    }
+    return hand_off(hp ? hp->ev[2] : nullptr, sd, su) ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
 int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* w, int weights_are_lambda, void* Xhat,
@@ -873,6 +991,11 @@ size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op)
     if (op == CDMIMO_OP_PRECODE)
         return hb + round256((size_t)p->n_sc * p->n_sym * p->U * 8) + round256((size_t)p->n_sc * p->n_sym * p->B * 8) +
                kSchedBytes;
+    if (op == CDMIMO_OP_FRAME) {  // H, Y, N0, S, Xhat, Xdl (and the two scale arrays); static schedule
+        const size_t su = round256((size_t)p->n_sc * p->n_sym * p->U * 8), nb = round256((size_t)p->n_sc * 4);
+        return hb + round256((size_t)p->n_sc * p->n_sym * p->B * eb) + nb + 2 * su +
+               round256((size_t)p->n_sc * p->n_sym * p->B * 8) + (p->in_dtype != CDMIMO_C64 ? 2 * nb : 0);
+    }
     return 0;
 }
 

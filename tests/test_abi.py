@@ -104,6 +104,33 @@ def test_host_workspace_sizes():
                                 ctypes.c_void_p(1), ctypes.c_void_p(256), 16, None) == cdmimo.ERR_WORKSPACE
 
 
+def test_frame_host_workspace_and_validation():
+    L = cdmimo.lib()
+    n, ns, B, U = 1200, 14, 256, 16
+    p, keep = cdmimo.make_params(n, ns, B, U, [32] * 8, 3)
+    r = lambda v: (v + 255) // 256 * 256
+    need = L.cdmimo_host_workspace_size(ctypes.byref(p), cdmimo.OP_FRAME)
+    # staging of H, Y, N0, S, Xhat and Xdl, each 256-byte aligned (no schedule counters: static schedule)
+    assert need == r(n * U * B * 8) + r(n * ns * B * 8) + r(n * 4) + 2 * r(n * ns * U * 8) + r(n * ns * B * 8)
+    q, keep2 = cdmimo.make_params(n, ns, B, U, [32] * 8, 3, in_dtype=cdmimo.C16BF, h_scale=None, y_scale=None)
+    assert L.cdmimo_host_workspace_size(ctypes.byref(q), cdmimo.OP_FRAME) == \
+        r(n * U * B * 4) + r(n * ns * B * 4) + 3 * r(n * 4) + 2 * r(n * ns * U * 8) + r(n * ns * B * 8)
+    assert L.cdmimo_host_workspace_size(ctypes.byref(p), 3) == 0
+    one = ctypes.c_void_p(256)
+    args = [one] * 6
+    call = lambda a, chunks=0, ws=one, wsb=need: L.cdmimo_detect_precode_host(ctypes.byref(p), *a, chunks, ws, wsb,
+                                                                             None)
+    assert call(args[:2] + [None] + args[3:]) == cdmimo.ERR_INVALID_ARG  # no N0
+    assert call(args[:5] + [None]) == cdmimo.ERR_INVALID_ARG  # no Xdl
+    assert call(args, chunks=-1) == cdmimo.ERR_INVALID_ARG
+    assert call(args, ws=None) == cdmimo.ERR_WORKSPACE
+    assert call(args, wsb=need - 1) == cdmimo.ERR_WORKSPACE
+    assert call(args, ws=ctypes.c_void_p(256 + 16)) == cdmimo.ERR_WORKSPACE  # not 256-byte aligned
+    assert call(args, ws=None, chunks=-1) == cdmimo.ERR_INVALID_ARG
+    e, keep3 = cdmimo.make_params(0, ns, B, U, [32] * 8, 3)
+    assert L.cdmimo_detect_precode_host(ctypes.byref(e), *([None] * 6), 0, None, 0, None) == cdmimo.OK
+
+
 def test_form_validation_and_query():
     L = cdmimo.lib()
     p, keep = cdmimo.make_params(8, 14, 256, 16, [32] * 8, 3, form=7)

@@ -133,3 +133,44 @@ def test_frame_edge_cases(dev):
         assert_vectors_close(X.cpu().numpy(), Xo, TOL, f"frame Xhat {form}")
         assert_vectors_close(P.cpu().numpy(), Po, TOL, f"frame Xdl {form}")
     assert cdmimo.device_status(clear=True) == 0
+
+
+@pytest.mark.parametrize("case,n_chunks,side", [("c64", 0, False), ("c64", 1, False), ("c64", 3, True),
+                                                ("c64", 7, False), ("c64", 5000, False), ("bf16", 4, False),
+                                                ("residual", 5, True)])
+def test_frame_host_pipeline_matches_device_call(dev, case, n_chunks, side):
+    """cdmimo_detect_precode_host (host buffers, chunked; uploads, kernels and downloads on three
+    streams) returns exactly what cdmimo_detect_precode returns on the same data in device memory,
+    on the current stream or on a caller's side stream."""
+    cs, U, K, n_sc, n_sym = ([16] * 8, 16, 2, 61, 9) if case == "residual" else ([32] * 8, 16, 3, 203, 14)
+    B = sum(cs)
+    d = wl.uplink(33, n_sc, n_sym, B, U, snr_db=wl.sweep_snr(n_sc))
+    S32, _ = wl.as_c64(d["X"])
+    N0 = d["N0"].astype(np.float32)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    if case == "bf16":
+        qH, sH, _ = wl.quantize_c16(d["H"], "bf16")
+        qY, sY, _ = wl.quantize_c16(d["Y"], "bf16")
+        Hh = pin(qH.view(np.int16)).view(torch.bfloat16)
+        Yh = pin(qY.view(np.int16)).view(torch.bfloat16)
+        sc_dev = dict(h_scale=t(sH, dev), y_scale=t(sY, dev))
+        sc_host = dict(h_scale=pin(sH), y_scale=pin(sY))
+    else:
+        Hh, Yh = pin(wl.as_c64(d["H"])[0]), pin(wl.as_c64(d["Y"])[0])
+        sc_dev, sc_host = {}, {}
+    Xd, Pd = cdmimo.detect_precode(Hh.to(dev), Yh.to(dev), t(N0, dev), t(S32, dev), cs, K, **sc_dev)
+    if case == "residual":
+        assert cdmimo.selected_form(cdmimo.OP_DETECT, n_sc, n_sym, B, U, cs, K, H=Hh.to(dev)) == "residual"
+    Xh = torch.full((n_sc, n_sym, U), float("nan"), dtype=torch.complex64).pin_memory()
+    Ph = torch.full((n_sc, n_sym, B), float("nan"), dtype=torch.complex64).pin_memory()
+    dt = cdmimo.C16BF if case == "bf16" else cdmimo.C64
+    nb = cdmimo.host_workspace_size(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, K, in_dtype=dt)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream() if side else torch.cuda.current_stream()
+    st.wait_stream(torch.cuda.current_stream())
+    for _ in range(2):  # the second call reuses the staging, the thread's streams and events
+        cdmimo.detect_precode_host(Hh, Yh, pin(N0), pin(S32), cs, K, Xh, Ph, ws, n_chunks=n_chunks, stream=st,
+                                   **sc_host)
+    st.synchronize()
+    assert torch.equal(Xh, Xd.cpu()) and torch.equal(Ph, Pd.cpu())
+    assert cdmimo.device_status(clear=True) == 0
