@@ -203,10 +203,10 @@ int cdmimo_precode_host(const cdmimo_params* p, const void* H_host, const void* 
  * cdmimo_detect_precode with HOST buffers, pipelined over chunks of subcarriers so that the uploads,
  * the kernels and the downloads overlap.  The n_sc subcarriers are split into n_chunks contiguous
  * chunks, the last half the size of the others (chunk i starts at n_sc 2i / (2 n_chunks - 1));
- * n_chunks = 0: the library's default, 5; more chunks than subcarriers: empty chunks are skipped.  `stream` first copies N0 and S whole into dev_ws, then per
- * chunk the chunk's H and Y; a kernel stream waits for that copy and runs the frame on the chunk
- * (static schedule); a
- * download stream waits for that kernel and copies the chunk's Xhat and Xdl back.  The uploads thus
+ * n_chunks = 0: the library's default, 5; more chunks than subcarriers: empty chunks are skipped.
+ * `stream` first copies N0 and S whole into dev_ws, then per chunk the chunk's H and Y; a kernel
+ * stream waits for that copy and runs the frame on the chunk (static schedule); a download stream
+ * waits for that kernel and copies the chunk's Xhat and Xdl back.  The uploads thus
  * run back to back on `stream` while earlier chunks compute and download (the two copy directions
  * run concurrently).  Before returning, the call makes `stream` wait for the last download: as for
  * every other entry point, the work is ordered after what `stream` holds and the caller synchronizes
