@@ -145,6 +145,7 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
     float* Dp = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] p_u^2
     float2* Zs = reinterpret_cast<float2*>(smem + pl.off_X);  // [U][x_stride]: z, then each tile's x
     float2* Ws = reinterpret_cast<float2*>(smem + pl.off_W);  // [U][x_stride]: w per tile
+    float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);  // [U][n_sym]: s of the subcarrier, transposed
     float* lam = reinterpret_cast<float*>(smem + pl.off_lam);
     ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
@@ -177,6 +178,11 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
     if (pl.bulk && tid == 0 && f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
     __syncthreads();
     if (pl.bulk && f < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, f, Dst(0), &bar[0]);
+    const int n_s = n_sym * U;
+    // s is stored [u][n] so that a warp's lanes (consecutive symbols) read consecutive words
+    auto put_s = [&](int i, float2 v) { Ss[(i % U) * n_sym + i / U] = v; };
+    if (f < pl.n_sc)
+        for (int i = tid; i < n_s; i += blockDim.x) put_s(i, io.S[(size_t)f * n_s + i]);
     float4 y0[kPairs], y1[kPairs];
     auto load_y = [&](int fy) {
         const size_t base = (size_t)fy * n_sym * pl.B + ctz.off;
@@ -216,7 +222,7 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
             raw_to_pairs(y1);
             const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ctz.soff) + gz.a;
             float2* z = Zs + gz.c * n_sym;
-#pragma unroll 1
+#pragma unroll 2
             for (int u = 0; u < U; ++u) {
                 float2 s0, s1;
                 corr2<AT>(hb + u * LP, y0, y1, s0, s1);
@@ -242,7 +248,7 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
             }
             float* G = reinterpret_cast<float*>(Gs + (size_t)gg.c * UT * (UT / 2));
             const int col = (v0 >> 1) * 4;  // v0 even: columns v0, v1 are the pair's two halves
-#pragma unroll 1
+#pragma unroll 2
             for (int u = 0; u < U; ++u) {
                 float2 s0, s1;
                 corr2<AT>(hb + u * LP, h0, h1, s0, s1);
@@ -269,8 +275,8 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
         }
         __syncthreads();
 
-        // Phase B: uplink sweeps on x (right-hand side z in shared memory) and downlink sweeps on w
-        // (s read from global memory, cached after the first sweep).  Thread 0 draws the next
+        // Phase B: uplink sweeps on x (right-hand side z) and downlink sweeps on w (right-hand side s),
+        // both read from shared memory.  Thread 0 draws the next
         // subcarrier now and hands it over before the barrier below (the atomic's latency is hidden).
         const unsigned ticket = (d.sched && tid == 0) ? atomicAdd(d.sched, 1u) : 0u;
         if (gb.active) {
@@ -278,9 +284,9 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
             const int n = ul ? gb.j : gb.j - n_sym;
             const int tile = gb.c * n_sym + n;
             const float* dd = (ul ? Dm : Dp) + gb.c * UT;
-            const float2* rhs = ul ? Zs + tile : io.S + ((size_t)f * n_sym + n) * U;
+            const float2* rhs = ul ? Zs + tile : Ss + n;
             float4 x[UT / 2];
-            gram_sweeps<UT, 1>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, rhs, ul ? xs : 1u, 0, gb.mask, x);
+            gram_sweeps<UT>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, rhs, ul ? xs : (uint32_t)n_sym, x);
             float2* dst = (ul ? Zs : Ws) + tile;
 #pragma unroll
             for (int u = 0; u < UT; ++u)
@@ -303,14 +309,14 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
         __syncthreads();
 
         // Phase C: the next subcarrier's channel copy (into the other buffer, last read in the
-        // previous iteration) and its y and s into L2; x_c = H_c w for two symbols per lane, then the
-        // normalization | uplink fusion.
+        // previous iteration) and its y into L2; x_c = H_c w for two symbols per lane, then the
+        // normalization | uplink fusion and the next subcarrier's s into shared memory (this one's
+        // was last read in phase B; the loads are issued before the fusion and stored after it).
         const int fn = nxt[b];
         if (pl.bulk && fn < pl.n_sc) issue_channel_copy<IN>(pl, tab, d.H, fn, Dst(b ^ 1), &bar[b ^ 1]);
         if (tid == 32 && fn < pl.n_sc) {
             constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
             bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * eb, (uint32_t)n_sym * pl.B * eb);
-            bulk_prefetch_l2(io.S + (size_t)fn * n_sym * U, (uint32_t)(n_sym * U * 8));
         }
         if (gz.active) {
             const float4* hb = reinterpret_cast<const float4*>(Hbuf(b) + ctz.soff) + gz.a;
@@ -329,7 +335,21 @@ __global__ void __maxnreg__(kPPRegs) cd_frame_gram_kernel(const CdPlan pl, const
             store_normalized<AT>(a0, pl.rho_c, gz.mask, gz.a, ctz.size, out, true);
             store_normalized<AT>(a1, pl.rho_c, gz.mask, gz.a, ctz.size, out + pl.B, has1);
         } else {
-            fuse_range(pl, d, f, lam, Zs, xs, out_scale, t_g, (int)blockDim.x - t_g);
+            constexpr int kSv = 2;  // entries of the next s per thread kept in flight across the fusion
+            const int r = tid - t_g, nr = (int)blockDim.x - t_g;
+            const bool ld = r >= 0 && fn < pl.n_sc;
+            const float2* src = io.S + (size_t)min(fn, pl.n_sc - 1) * n_s;
+            float2 sv[kSv];
+#pragma unroll
+            for (int q = 0; q < kSv; ++q)
+                sv[q] = (ld && r + q * nr < n_s) ? src[r + q * nr] : make_float2(0.f, 0.f);
+            fuse_range(pl, d, f, lam, Zs, xs, out_scale, t_g, nr);
+            if (ld) {
+#pragma unroll
+                for (int q = 0; q < kSv; ++q)
+                    if (r + q * nr < n_s) put_s(r + q * nr, sv[q]);
+                for (int i = r + kSv * nr; i < n_s; i += nr) put_s(i, src[i]);
+            }
         }
         __syncthreads();  // this channel buffer receives the copy issued at the next iteration's start
         ++done;

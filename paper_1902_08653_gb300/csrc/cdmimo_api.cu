@@ -262,11 +262,13 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
         pl->off_S = o;
         o = align16(o + ((unsigned)n_sym * ((unsigned)U | 1u) + UTu) * 8u);
     }
-    if (frame) {  // the downlink's w per tile and p_u^2 (s is read from global memory)
+    if (frame) {  // the downlink's w per tile, p_u^2, and the subcarrier's s [n_sym][U]
         pl->off_W = o;
         o = align16(o + (unsigned)U * xs * 8u);
         pl->off_E2 = o;
         o = align16(o + C * UTu * 4u);
+        pl->off_S = o;
+        o = align16(o + (unsigned)n_sym * (unsigned)U * 8u);
     }
     if (pl->learned) {  // ||h_u||^2 per cluster, and the learned fusion's hidden activations
         pl->off_E2 = o;
