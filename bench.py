@@ -53,13 +53,13 @@ KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
 UL_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8
 DL_BYTES_PER_VEC = U * B * 8 / N_SYM + U * 8 + B * 8
 FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
-# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one --set full
-# capture of `python bench.py --profile detect|precode|frame`, see profiles/) for the kernel named in
+# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one capture
+# of `python bench.py --profile detect|precode|frame`, see profiles/) for the kernel named in
 # the key; a kernel without an entry (or changed since its capture) reports null.  Outputs still in
 # L2 when a kernel ends are written back after it, outside the launch.
-NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.801216e6 + 1.029376e6,
-               "cd_precode_gram_kernel": 41.527296e6 + 0.883968e6,
-               "cd_frame_gram_kernel": 75.962880e6 + 3.199744e6}
+NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.806592e6 + 0.621568e6,
+               "cd_precode_gram_kernel": 41.539072e6 + 0.377088e6,
+               "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6}
 
 WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
             "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
