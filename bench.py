@@ -49,6 +49,9 @@ FLOP_PER_VEC = {"residual": 2 * K * U * B * 8, "gram": 8 * (K * C * U * U + U * 
 FRAME_FLOP_PER_VEC = {"residual": 2 * FLOP_PER_VEC["residual"], "gram": 8 * (2 * K * C * U * U + 2 * U * B + GRAM_G)}
 KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
            "gram": ("cd_detect_gram_kernel", "cd_precode_gram_kernel")}
+# One-kernel TDD frames by form: FP32 Gram form, and Gram form with z, G_c and x_c = H_c w on the
+# tensor cores (split-TF32 MMAs; the sweeps, K C U^2 of the flops above, stay on the FP32 pipes).
+FRAME_KERNELS = {"gram": "cd_frame_gram_kernel", "gram_tc": "cd_frame_tc_kernel"}
 # Algorithmic HBM bytes per vector: uplink H/14 + y + xhat; downlink H/14 + s + x; frame H/14 once.
 UL_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8
 DL_BYTES_PER_VEC = U * B * 8 / N_SYM + U * 8 + B * 8
@@ -311,10 +314,11 @@ def run_cuda(args, rank, world, local_rank):
                 "hbm_frac": nbytes * vec_step / (ms * 1e-3) / 1e9 / hbm_peak}
 
     if frame:
-        fused = form_ul == "gram" and form_dl == "gram"
-        name = "cd_frame_gram_kernel" if fused else "+".join(KERNELS[form_ul][:1] + KERNELS[form_dl][1:])
+        form_fr = cdmimo.selected_form(cdmimo.OP_FRAME, N_SC, N_SYM, B, U, CS, K, form=args.form, H=H)
+        fused = form_fr in FRAME_KERNELS
+        name = FRAME_KERNELS[form_fr] if fused else "+".join(KERNELS[form_ul][:1] + KERNELS[form_dl][1:])
         fl = FRAME_FLOP_PER_VEC["gram"] if fused else FLOP_PER_VEC[form_ul] + FLOP_PER_VEC[form_dl]
-        kernels = [kernel_line(name, "gram" if fused else form_ul, float(np.mean(t_a)), fl, FRAME_BYTES_PER_VEC)]
+        kernels = [kernel_line(name, form_fr if fused else form_ul, float(np.mean(t_a)), fl, FRAME_BYTES_PER_VEC)]
         dom = kernels[0]
         dom_bytes = FRAME_BYTES_PER_VEC * vec_step
     else:
@@ -355,7 +359,7 @@ def run_cuda(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "api": "cdmimo_detect_precode_host (chunks: %s)" % (args.e2e_chunks or "default") if frame
                 else "cdmimo_detect_host + cdmimo_precode_host"},
-        "gpu_launches": (1 if frame and kernels[0]["kernel"] == "cd_frame_gram_kernel" else 2) * args.steps,
+        "gpu_launches": (1 if frame and kernels[0]["kernel"] in FRAME_KERNELS.values() else 2) * args.steps,
         "clocks": clocks,
         "wall_s": wall,
     }
@@ -633,7 +637,7 @@ def main():
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
     ap.add_argument("--profile", choices=["detect", "precode", "frame"], default=None,
                     help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu")
-    ap.add_argument("--form", choices=["auto", "residual", "gram"], default="auto", help="CD evaluation form")
+    ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc"], default="auto", help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="chunks of the pipelined host-buffer frame in the e2e leg (0: the library's default)")
     ap.add_argument("--step", choices=["frame", "separate"], default="frame",

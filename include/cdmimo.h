@@ -77,10 +77,22 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             sweep and vector plus U B_c (z or H_c w) and U^2 B_c / n_sym (G_c).  Requires U <= 16,
  *             equal lanes per cluster tile (8 < B_c <= 64 for all clusters, or all B_c <= 16, ...:
  *             the packed-kernel shapes) and no learned block; otherwise CDMIMO_ERR_UNSUPPORTED.
+ *   GRAM_TC   GRAM, with the TDD frame's (cdmimo_detect_precode) contractions z = H_c^H y_c,
+ *             G_c = H_c^H H_c and x_c = H_c w on the tensor cores (TF32 MMAs with each FP32 operand
+ *             split into two TF32 parts, FP32 accumulation; the sweeps stay FP32).  That kernel
+ *             takes c64 storage, every B_c = 16 or every B_c = 32, 8 < U <= 16, n_sym <= 16,
+ *             2 C n_sym <= 256 and no learned block; elsewhere (and for cdmimo_detect and
+ *             cdmimo_precode) GRAM_TC is GRAM.
  *   AUTO      GRAM where it applies, every B_c >= 2 U (so G_c + (N0/Ex) I stays well conditioned
- *             in FP32) and it needs fewer complex MACs; else RESIDUAL.
+ *             in FP32) and it needs fewer complex MACs, with the frame on the tensor cores where
+ *             GRAM_TC's kernel takes the shape; else RESIDUAL.
  */
-typedef enum { CDMIMO_FORM_AUTO = 0, CDMIMO_FORM_RESIDUAL = 1, CDMIMO_FORM_GRAM = 2 } cdmimo_form;
+typedef enum {
+    CDMIMO_FORM_AUTO = 0,
+    CDMIMO_FORM_RESIDUAL = 1,
+    CDMIMO_FORM_GRAM = 2,
+    CDMIMO_FORM_GRAM_TC = 3
+} cdmimo_form;
 
 /*
  * Problem description shared by detection and precoding.
@@ -165,9 +177,10 @@ int cdmimo_precode(const cdmimo_params* p, const void* H, const void* S, void* X
  * One TDD frame on one channel: cdmimo_detect on (H, Y) followed by cdmimo_precode of S on the same
  * H (the downlink channel is the transpose of the uplink one, Sec. IV; precoding uses p->rho),
  * with the same arguments, outputs and results as those two calls (no Xc_opt / lambda_opt).
- * Where the Gram form applies (see cdmimo_form; p->form AUTO or GRAM) one kernel does both and
- * shares the channel copy and G_c between the directions; otherwise (or with p->form RESIDUAL) it
- * enqueues the two calls.  workspace as for cdmimo_detect.
+ * Where the Gram form applies (see cdmimo_form; p->form AUTO, GRAM or GRAM_TC) one kernel does both
+ * and shares the channel copy and G_c between the directions (with AUTO and GRAM_TC, on the tensor
+ * cores where that kernel takes the shape); otherwise (or with p->form RESIDUAL) it enqueues the two
+ * calls.  workspace as for cdmimo_detect.
  */
 int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat,
                           const void* S, void* Xdl, void* workspace, size_t ws_bytes, void* stream);
@@ -392,7 +405,7 @@ int cdmimo_synth_uplink(unsigned long long seed, int n_sc, int n_sym, int B, int
 /* ---------------------------------------------------------------------------------------------- */
 #define CDMIMO_OP_DETECT 0
 #define CDMIMO_OP_PRECODE 1
-#define CDMIMO_OP_FRAME 2 /* cdmimo_detect_precode_host staging (cdmimo_host_workspace_size only) */
+#define CDMIMO_OP_FRAME 2 /* the TDD frame: cdmimo_host_workspace_size, cdmimo_selected_form */
 
 /* Bytes of the optional device workspace of cdmimo_detect / cdmimo_precode (the schedule counters:
  * 256 for every p). */
@@ -406,7 +419,9 @@ size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
 /* The evaluation form (CDMIMO_FORM_RESIDUAL or CDMIMO_FORM_GRAM) that cdmimo_detect (op =
  * CDMIMO_OP_DETECT) or cdmimo_precode (CDMIMO_OP_PRECODE) would run for p and a channel at H (its
  * alignment decides the staging path), or a negative status (for example UNSUPPORTED for a forced
- * GRAM that does not apply).  Host only: nothing is launched. */
+ * GRAM that does not apply).  op = CDMIMO_OP_FRAME: the form of cdmimo_detect_precode's one-kernel
+ * frame (CDMIMO_FORM_GRAM_TC on the tensor cores, CDMIMO_FORM_GRAM), or, where it enqueues two
+ * calls, the uplink's form.  Host only: nothing is launched. */
 int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H);
 
 /* Static name of a status code. */

@@ -33,7 +33,7 @@ LEARNED_BLOCK_BYTES = 4 * 4 + 16 * 4 * 2 + 64 * 4 + 4 * 4 + 64 * 65 * 2 + 64 * 2
 
 C64, C16F, C16BF = 0, 1, 2
 FUSE = {"equal": 0, "colnorm": 1, "learned": 2}
-FORM = {"auto": 0, "residual": 1, "gram": 2}
+FORM = {"auto": 0, "residual": 1, "gram": 2, "gram_tc": 3}
 OP_DETECT, OP_PRECODE, OP_FRAME = 0, 1, 2
 
 
@@ -229,7 +229,7 @@ def detect(H, Y, N0, cluster_size, K, *, Ex=1.0, fuse="colnorm", h_scale=None, y
            out=None, Xc=None, lam=None, workspace=None, stream=None, form="auto"):
     """cdmimo_detect: Algorithm 1 + fusion.  Returns Xhat [n_sc, n_sym, U] complex64.
     workspace: None or False = static subcarrier schedule; True = dynamic schedule on this binding's
-    per-stream counters; or a zero-filled device tensor of cdmimo_workspace_size bytes (dynamic).  form: "auto", "residual" or "gram"
+    per-stream counters; or a zero-filled device tensor of cdmimo_workspace_size bytes (dynamic).  form: "auto", "residual", "gram" or "gram_tc"
     (cdmimo_form)."""
     _need(H, "H")
     _need(Y, "Y")
@@ -319,7 +319,8 @@ def fuse(Xc, w, *, weights_are_lambda=False, out=None, stream=None):
 
 
 def selected_form(op, n_sc, n_sym, B, U, cluster_size, K, *, in_dtype=C64, form="auto", H=None):
-    """cdmimo_selected_form: "residual" or "gram", the form a call with these arguments runs."""
+    """cdmimo_selected_form: "residual", "gram" or (op OP_FRAME) "gram_tc", the form a call with these
+    arguments runs."""
     p, keep = make_params(n_sc, n_sym, B, U, cluster_size, K, in_dtype=in_dtype, form=form)
     rc = lib().cdmimo_selected_form(ctypes.byref(p), op, _ptr(H) if H is not None else ctypes.c_void_p(256))
     if rc < 0:

@@ -1,0 +1,390 @@
+// TDD frame kernel with the contractions on the tensor cores: uplink detection (Algorithm 1 +
+// fusion, Sec. III) and downlink precoding (Algorithm 2 + normalization, Sec. IV-B) on one channel
+// per subcarrier, in Gram form (see cd_gram.cuh), like cd_frame_gram_kernel, but with
+//   z = H_c^H y_c,  G_c = H_c^H H_c  (phase A)   and   x_c = H_c w  (phase C)
+// computed by warp-level tensor-core MMAs (mma.sync m16n8k8, TF32 operands, FP32 accumulation),
+// one warp per cluster.  The sweeps (phase B) are the FP32 Gauss-Seidel steps of the SIMT kernel.
+//
+// FP32 accuracy from TF32 operands.  Every FP32 operand x is split as x = hi + lo, hi = x with its
+// 13 low mantissa bits cleared (a TF32 value) and lo = x - hi (exact in FP32, |lo| < 2^-10 |x|); the
+// MMA reads a TF32 operand from its upper 19 bits, so lo enters with an error below 2^-10 of itself,
+// 2^-20 of x.  Every product is accumulated as lo_a hi_b + hi_a lo_b + hi_a hi_b (the lo_a lo_b
+// term, below 2^-20 |a b|, is dropped): three MMAs per tile, with no conversion instructions.
+//
+// Complex products as real MMAs.  Each k-step of 8 real values covers four complex entries e:
+// k = t is Re of entry e0 + t and k = t + 4 is Im of it (t = 0..3), so a lane's two values of a
+// fragment (k = tig and tig + 4) come from one 64-bit load of a complex entry.  Then
+//   Re(h_u^H v) = sum_k h_u[k] v[k]            Im(h_u^H v) = sum_k h_u[k] rot(v)[k]
+// with rot(v) = (Im v, -Re v) per entry: one contraction gives both parts, the second with the B
+// operand rotated (from the same loaded value).  For x_c = H_c w the entries are the users:
+// Re x_b = sum_k h^T[b][k] (Re w, -Im w)[k], Im x_b = sum_k h^T[b][k] (Im w, Re w)[k].
+//
+// Shared memory.  The channel rows of a cluster are UT = 16 rows (rows U..15 zero) of 2 B_c + 8
+// floats: with that stride the 64-bit fragment loads of both phases (rows gid x entries tig, and
+// users tig x antennas gid) fall on distinct banks.  The rows land in that layout by one bulk copy
+// per row, double-buffered one subcarrier ahead as in the SIMT kernel; no permutation pass follows.
+// The downlink's w per tile takes the place of the Gram rows once the sweeps are over (a barrier
+// separates the two), which keeps two CTAs per SM.  Per-tile rows (z, x, w) have a stride of
+// 4 mod 16 entries, so that phase C's loads of w (users tig x symbols gid) are conflict-free too.
+#pragma once
+#include "cd_frame.cuh"
+
+namespace cdmimo {
+
+constexpr int kTcUT = 16;        // users per cluster in the MMA tiles (rows U..15 are zero)
+constexpr int kTcThreads = 256;  // eight warps: one per cluster in phases A and C
+
+// x = hi + lo (see above); the negated split of -x is the two values with the sign bit flipped.
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo)
+{
+    const uint32_t h = __float_as_uint(x) & 0xffffe000u;
+    hi = h;
+    lo = __float_as_uint(x - __uint_as_float(h));
+}
+
+__device__ __forceinline__ uint32_t neg_bits(uint32_t v) { return v ^ 0x80000000u; }
+
+// One B fragment (k = tig, tig + 4) in TF32 halves.
+struct BFrag {
+    uint32_t h[2], l[2];
+};
+
+// d += A B for one m16n8k8 tile (A row-major 16 x 8, B 8 x 8 "col"), TF32 in, FP32 accumulate.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += A B with FP32-accurate operands (three passes, smallest terms first).
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                           const BFrag& b)
+{
+    mma_tf32(d, al, b.h[0], b.h[1]);
+    mma_tf32(d, ah, b.l[0], b.l[1]);
+    mma_tf32(d, ah, b.h[0], b.h[1]);
+}
+
+// A fragment (rows r0 and r0 + 8 of a k-step) from two complex entries: k = tig is Re, tig + 4 Im.
+__device__ __forceinline__ void a_frag(float2 e0, float2 e1, uint32_t (&ah)[4], uint32_t (&al)[4])
+{
+    tf32_split(e0.x, ah[0], al[0]);
+    tf32_split(e1.x, ah[1], al[1]);
+    tf32_split(e0.y, ah[2], al[2]);
+    tf32_split(e1.y, ah[3], al[3]);
+}
+
+// B fragments of a complex entry v for the plain and the rotated operand: (Re v, Im v) and
+// (Im v, -Re v) as (k = tig, k = tig + 4) values, split into TF32 halves.
+__device__ __forceinline__ void b_frags(float2 v, BFrag& plain, BFrag& rot)
+{
+    tf32_split(v.x, plain.h[0], plain.l[0]);
+    tf32_split(v.y, plain.h[1], plain.l[1]);
+    rot.h[0] = plain.h[1];
+    rot.l[0] = plain.l[1];
+    rot.h[1] = neg_bits(plain.h[0]);
+    rot.l[1] = neg_bits(plain.l[0]);
+}
+
+// Bulk copies of subcarrier f's channel rows into the padded per-cluster layout (row (c, u) at
+// floats (c UT + u) srow); thread i issues row i.
+__device__ __forceinline__ void issue_channel_copy_tc(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
+                                                      float* dst, int srow, uint64_t* bar)
+{
+    const char* Hf = reinterpret_cast<const char*>(H) + (size_t)f * pl.U * pl.B * 8u;
+    for (int row = threadIdx.x; row < pl.U * pl.C; row += blockDim.x) {
+        const int c = row / pl.U, u = row - c * pl.U;
+        const ClusterTile ct = tab[c];
+        fence_proxy_async_smem();
+        bulk_g2s(dst + (size_t)(c * kTcUT + u) * srow, Hf + ((size_t)u * pl.B + ct.off) * 8u, (uint32_t)ct.size * 8u,
+                 bar);
+    }
+}
+
+template <int BC>
+__global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan pl, const FusedIO io)
+{
+    constexpr int UT = kTcUT;
+    constexpr int SROW = (int)tc_row_floats(BC);  // floats per channel row
+    constexpr int SR2 = SROW / 2;     // the same in complex entries
+    constexpr int KA = BC / 4;        // phase A k-steps (4 antennas each)
+    constexpr int MT = BC / 16;       // phase C m-tiles (16 antennas each)
+    constexpr int KC = UT / 4;        // phase C k-steps (4 users each)
+    static_assert(BC == 16 || BC == 32, "cluster size 16 or 32");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* Gs = reinterpret_cast<float4*>(smem + pl.off_G);  // [C][UT][UT/2] pair-planar rows, zero diagonal
+    float2* Ws = reinterpret_cast<float2*>(smem + pl.off_G);  // [U][x_stride] w per tile, after the sweeps
+    float* Dm = reinterpret_cast<float*>(smem + pl.off_E);    // [C][UT] m_u
+    float* Dp = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] p_u^2
+    float2* Zs = reinterpret_cast<float2*>(smem + pl.off_X);  // [UT][x_stride]: z, then each tile's x
+    float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);  // [U][n_sym]: s of the subcarrier, transposed
+    float* lam = reinterpret_cast<float*>(smem + pl.off_lam);
+    ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + pl.off_tab);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + pl.off_bar);
+    int* nxt = reinterpret_cast<int*>(smem + pl.off_bar + 16);
+    auto Hbuf = [&](int j) { return reinterpret_cast<float*>(smem + (j ? pl.off_H2 : 0u)); };
+    const DetectIO& d = io.d;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+    const int U = pl.U, C = pl.C, n_sym = pl.n_sym, n_s = n_sym * U;
+    const uint32_t xs = tc_x_stride(pl.n_tiles);
+
+    // Setup: cluster table, barriers, zero channel rows U..UT-1 of both buffers (never copied).
+    if (tid < C) tab[tid] = pl.cl[tid];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_proxy_async_smem();
+    }
+    for (int j = 0; j < 2; ++j) {
+        float* hb = Hbuf(j);
+        const int per_c = (UT - U) * SROW;
+        for (int i = tid; i < C * per_c; i += blockDim.x) {
+            const int c = i / per_c, r = i - c * per_c;
+            hb[(c * UT + U) * SROW + r] = 0.f;
+        }
+    }
+    __syncthreads();
+
+    // Phase B lanes: one per uplink or downlink (cluster, symbol) tile, as in the SIMT frame kernel.
+    const GLane gb = frame_lane(0, C, 2 * n_sym, 1);
+
+    int f = blockIdx.x;
+    if (tid == 0 && f < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[0]);
+    __syncthreads();
+    if (f < pl.n_sc) issue_channel_copy_tc(pl, tab, d.H, f, Hbuf(0), SROW, &bar[0]);
+    auto put_s = [&](int i, float2 v) { Ss[(i % U) * n_sym + i / U] = v; };
+    if (f < pl.n_sc)
+        for (int i = tid; i < n_s; i += blockDim.x) put_s(i, io.S[(size_t)f * n_s + i]);
+
+    int done = 0;
+    for (int k = 0; f < pl.n_sc; ++k) {
+        const int b = k & 1;
+        float alpha = __ldg(d.N0 + f) * pl.inv_Ex;
+        float out_scale = 1.f;
+        if (!(alpha >= 0.f)) {
+            if (tid == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_N0);
+            out_scale = __int_as_float(0x7fc00000);
+            alpha = 0.f;
+        }
+        const uint32_t parity = (uint32_t)(k >> 1) & 1u;
+        const bool ok = mbar_wait_bounded(&bar[b], parity);
+        if (__syncthreads_or(!ok)) {
+            // copy timeout: no other copy is in flight; give this one a last bounded wait, then stop
+            if (tid == 0) mbar_wait_bounded(&bar[b], parity);
+            break;
+        }
+        const float* Hb = Hbuf(b);
+
+        // Phase A: per cluster (one warp), G_c (4 n-tiles: Re and Im of columns 0-7, 8-15) and z
+        // (4 n-tiles: Re and Im of symbols 0-7, 8-15), over KA k-steps.
+        for (int c = warp; c < C; c += kTcThreads / 32) {
+            const float2* Hc2 = reinterpret_cast<const float2*>(Hb + c * UT * SROW);
+            const ClusterTile ct = tab[c];
+            const float2* Yc = reinterpret_cast<const float2*>(d.Y) + (size_t)f * n_sym * pl.B + ct.off;
+            float accG[4][4], accZ[4][4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) accG[t][q] = accZ[t][q] = 0.f;
+            // receive samples of the B fragments (entry 4 ks + tig of symbols 8 j + gid), two k-steps
+            // ahead: [stage][n-tile]
+            float2 yv[2][2];
+            auto load_y = [&](int ks, float2 (&dst)[2]) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int n = 8 * j + gid;
+                    dst[j] = n < n_sym ? __ldg(Yc + (size_t)n * pl.B + 4 * ks + tig) : make_float2(0.f, 0.f);
+                }
+            };
+            load_y(0, yv[0]);
+            if (KA > 1) load_y(1, yv[1]);
+#pragma unroll
+            for (int ks = 0; ks < KA; ++ks) {
+                const int e = 4 * ks + tig;  // the lane's complex entry of this k-step
+                uint32_t ah[4], al[4];
+                a_frag(Hc2[gid * SR2 + e], Hc2[(gid + 8) * SR2 + e], ah, al);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    BFrag bp, br;
+                    b_frags(Hc2[(8 * j + gid) * SR2 + e], bp, br);
+                    mma_3xtf32(accG[j], ah, al, bp);
+                    mma_3xtf32(accG[2 + j], ah, al, br);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    BFrag bp, br;
+                    b_frags(yv[ks & 1][j], bp, br);
+                    mma_3xtf32(accZ[j], ah, al, bp);
+                    mma_3xtf32(accZ[2 + j], ah, al, br);
+                }
+                if (ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
+            }
+            // G rows (pair-planar, zero diagonal) with m_u and p_u^2 from the diagonal; rows u = gid,
+            // gid + 8, columns v = 8 j + 2 tig, +1 (accumulator element 2 r + e)
+            float4* Gc = Gs + (size_t)c * UT * (UT / 2);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int u = gid + 8 * r, v = 8 * j + 2 * tig;
+                    float g0 = accG[j][2 * r], g1 = accG[j][2 * r + 1];
+                    float i0 = accG[2 + j][2 * r], i1 = accG[2 + j][2 * r + 1];
+                    if (v == u || v + 1 == u) {
+                        const float e = v == u ? g0 : g1, den = e + alpha;
+                        Dm[c * UT + u] = (u < U && den > 0.f) ? __fdividef(1.f, den) : 0.f;
+                        Dp[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
+                        if (v == u) g0 = i0 = 0.f;
+                        else g1 = i1 = 0.f;
+                    }
+                    Gc[u * (UT / 2) + (v >> 1)] = make_float4(g0, g1, i0, i1);
+                }
+            // z for tile (c, n): rows u = gid, gid + 8, symbols n = 8 j + 2 tig, +1
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int u = gid + 8 * r, n = 8 * j + 2 * tig;
+                    if (u < U) {
+                        float2* z = Zs + u * xs + c * n_sym;
+                        if (n < n_sym) z[n] = make_float2(accZ[j][2 * r], accZ[2 + j][2 * r]);
+                        if (n + 1 < n_sym) z[n + 1] = make_float2(accZ[j][2 * r + 1], accZ[2 + j][2 * r + 1]);
+                    }
+                }
+        }
+        __syncthreads();
+
+        // Phase B: uplink sweeps on x (right-hand side z), downlink sweeps on w (right-hand side s);
+        // the downlink lanes keep w in registers until every lane has finished reading G.
+        const unsigned ticket = (d.sched && tid == 0) ? atomicAdd(d.sched, 1u) : 0u;
+        float4 x[UT / 2];
+        const bool ul = gb.j < n_sym;
+        const int n_b = ul ? gb.j : gb.j - n_sym;
+        const int tile = gb.c * n_sym + n_b;
+        if (gb.active) {
+            const float* dd = (ul ? Dm : Dp) + gb.c * UT;
+            const float2* rhs = ul ? Zs + tile : Ss + n_b;
+            gram_sweeps<UT>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, rhs, ul ? xs : (uint32_t)n_sym, x);
+            if (ul) {
+#pragma unroll
+                for (int u = 0; u < UT; ++u)
+                    if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
+                if (n_b == 0) {
+                    float msum = 0.f;
+                    for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
+                    lam[gb.c] = 1.f / msum;
+                }
+            }
+        }
+        if (tid == 0) {
+            int nf = f + (int)gridDim.x;
+            if (d.sched) {
+                const unsigned v = gridDim.x + ticket;
+                nf = v < (unsigned)pl.n_sc ? (int)v : pl.n_sc;
+            }
+            nxt[b] = nf;
+            if (nf < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[b ^ 1]);
+        }
+        __syncthreads();
+        if (gb.active && !ul) {
+#pragma unroll
+            for (int u = 0; u < UT; ++u)
+                if (u < U) Ws[tile + u * xs] = slice_entry<UT, 1>(x, u);
+        }
+        __syncthreads();
+
+        // Phase C: the next subcarrier's channel copy (into the other buffer, last read in the
+        // previous iteration) and its y into L2; the next s is loaded now and stored at the end.
+        // Per cluster (one warp): x_c = H_c w for all symbols (MT x 4 tiles), normalized per symbol.
+        // Then the uplink fusion.
+        const int fn = nxt[b];
+        if (fn < pl.n_sc) issue_channel_copy_tc(pl, tab, d.H, fn, Hbuf(b ^ 1), SROW, &bar[b ^ 1]);
+        if (tid == 32 && fn < pl.n_sc)
+            bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * 8u, (uint32_t)n_sym * pl.B * 8u);
+        constexpr int kSv = 2;
+        const bool ld_s = fn < pl.n_sc;
+        const float2* s_src = io.S + (size_t)min(fn, pl.n_sc - 1) * n_s;
+        float2 sv[kSv];
+#pragma unroll
+        for (int q = 0; q < kSv; ++q)
+            sv[q] = (ld_s && tid + q * kTcThreads < n_s) ? s_src[tid + q * kTcThreads] : make_float2(0.f, 0.f);
+
+        for (int c = warp; c < C; c += kTcThreads / 32) {
+            const float2* Hc2 = reinterpret_cast<const float2*>(Hb + c * UT * SROW);
+            const ClusterTile ct = tab[c];
+            float acc[MT][4][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[m][t][q] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < KC; ++ks) {
+                const int u = 4 * ks + tig;  // the lane's user of this k-step
+                BFrag br[2], bi[2];         // per n-tile: (Re w, -Im w) and (Im w, Re w)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int n = 8 * j + gid;
+                    const float2 w = (u < U && n < n_sym) ? Ws[u * xs + c * n_sym + n] : make_float2(0.f, 0.f);
+                    b_frags(make_float2(w.y, w.x), bi[j], br[j]);  // rot(Im w, Re w) = (Re w, -Im w)
+                }
+#pragma unroll
+                for (int m = 0; m < MT; ++m) {
+                    uint32_t ah[4], al[4];
+                    a_frag(Hc2[u * SR2 + 16 * m + gid], Hc2[u * SR2 + 16 * m + gid + 8], ah, al);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        mma_3xtf32(acc[m][j], ah, al, br[j]);
+                        mma_3xtf32(acc[m][2 + j], ah, al, bi[j]);
+                    }
+                }
+            }
+            // rows b = 16 m + gid (+8), symbols n = 8 j + 2 tig + e; norm over the cluster's antennas
+            // (the thread's rows, then the eight lanes of the same tig)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float nr = 0.f;
+#pragma unroll
+                    for (int m = 0; m < MT; ++m)
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const float xr = acc[m][j][2 * r + e], xi = acc[m][2 + j][2 * r + e];
+                            nr = fmaf(xr, xr, fmaf(xi, xi, nr));
+                        }
+                    nr += __shfl_xor_sync(0xffffffffu, nr, 4);
+                    nr += __shfl_xor_sync(0xffffffffu, nr, 8);
+                    nr += __shfl_xor_sync(0xffffffffu, nr, 16);
+                    const float sc = nr > 0.f ? pl.rho_c * rsqrtf(nr) : 0.f;
+                    const int n = 8 * j + 2 * tig + e;
+                    if (n < n_sym) {
+                        float2* out = io.Xdl + ((size_t)f * n_sym + n) * pl.B + ct.off;
+#pragma unroll
+                        for (int m = 0; m < MT; ++m)
+#pragma unroll
+                            for (int r = 0; r < 2; ++r)
+                                out[16 * m + 8 * r + gid] =
+                                    make_float2(acc[m][j][2 * r + e] * sc, acc[m][2 + j][2 * r + e] * sc);
+                    }
+                }
+        }
+        fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
+        if (ld_s) {
+#pragma unroll
+            for (int q = 0; q < kSv; ++q)
+                if (tid + q * kTcThreads < n_s) put_s(tid + q * kTcThreads, sv[q]);
+            for (int i = tid + kSv * kTcThreads; i < n_s; i += kTcThreads) put_s(i, s_src[i]);
+        }
+        __syncthreads();  // this channel buffer receives the copy issued at the next iteration's start
+        ++done;
+        f = fn;
+    }
+    sched_finish(d.sched, done, pl.n_sc);
+}
+
+}  // namespace cdmimo

@@ -64,7 +64,8 @@ int validate(const cdmimo_params* p)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->fuse != CDMIMO_FUSE_EQUAL && p->fuse != CDMIMO_FUSE_COLNORM && p->fuse != CDMIMO_FUSE_LEARNED)
         return CDMIMO_ERR_INVALID_ARG;
-    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_RESIDUAL && p->form != CDMIMO_FORM_GRAM)
+    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_RESIDUAL && p->form != CDMIMO_FORM_GRAM &&
+        p->form != CDMIMO_FORM_GRAM_TC)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
     if (!p->cluster_size || p->C > CDMIMO_MAX_CLUSTERS) return CDMIMO_ERR_BAD_PARTITION;
@@ -290,13 +291,59 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
     return CDMIMO_OK;
 }
 
+// GRAM and GRAM_TC ask for the Gram form (UNSUPPORTED where it does not apply).
+bool is_forced_gram(const cdmimo_params* p) { return p->form == CDMIMO_FORM_GRAM || p->form == CDMIMO_FORM_GRAM_TC; }
+
+// Tensor-core frame plan: the Gram frame plan's cluster table and tiling, with the layout of
+// cd_frame_tc_kernel: two channel buffers of C x 16 rows of 2 B_c + 8 floats, the Gram rows (later
+// w per tile), m_u and p_u^2, z / x per tile, s.  UNSUPPORTED unless the shape is the kernel's
+// (c64 storage by bulk copy, every B_c = 16 or every B_c = 32, 8 < U <= 16, n_sym <= 16,
+// 2 C n_sym <= 256, no learned block) and, for AUTO, the Gram form's own rules hold.
+int build_frame_tc_plan(const cdmimo_params* p, const void* H, CdPlan* pl)
+{
+    if (p->in_dtype != CDMIMO_C64 || p->learned || p->fuse == CDMIMO_FUSE_LEARNED) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->U <= 8 || p->U > 16 || p->n_sym > 16 || 2 * p->C * p->n_sym > 256) return CDMIMO_ERR_UNSUPPORTED;
+    if (int rc = build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, pl, true)) return rc;
+    const int Bc = p->cluster_size[0];
+    if (!pl->bulk || (Bc != 16 && Bc != 32) || pl->A_uniform != Bc / 16) return CDMIMO_ERR_UNSUPPORTED;
+    for (int c = 0; c < p->C; ++c)
+        if (p->cluster_size[c] != Bc) return CDMIMO_ERR_UNSUPPORTED;
+    const unsigned C = p->C, U = p->U, UT = 16, xs = tc_x_stride(pl->n_tiles), n_sym = p->n_sym;
+    const unsigned hbytes = align16(C * UT * tc_row_floats(Bc) * 4u);
+    unsigned o = 2u * hbytes;
+    pl->off_H2 = hbytes;
+    pl->off_H3 = 0u;
+    pl->off_G = o;  // Gram rows, then (after the sweeps) w per tile
+    o = align16(o + std::max(C * UT * UT * 8u, U * xs * 8u));
+    pl->off_E = o;
+    o = align16(o + C * UT * 4u);
+    pl->off_E2 = o;
+    o = align16(o + C * UT * 4u);
+    pl->off_X = o;
+    o = align16(o + UT * xs * 8u);
+    pl->off_W = pl->off_G;
+    pl->off_S = o;
+    o = align16(o + n_sym * U * 8u);
+    pl->off_lam = o;
+    o = align16(o + C * 4u);
+    pl->off_tab = o;
+    o = align16(o + C * (unsigned)sizeof(ClusterTile));
+    pl->off_bar = o;
+    o = align16(o + 32u);
+    pl->smem_bytes = o;
+    if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    pl->threads = 256;
+    pl->UT = 16;
+    return CDMIMO_OK;
+}
+
 // The plan for p->form: GRAM where requested, or (AUTO) where the Gram form applies and pays,
 // else the residual form.
 int plan_for(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
 {
     if (p->form != CDMIMO_FORM_RESIDUAL) {
         const int rc = build_gram_plan(p, detect, H, p->form == CDMIMO_FORM_AUTO, pl);
-        if (rc == CDMIMO_OK || p->form == CDMIMO_FORM_GRAM) return rc;
+        if (rc == CDMIMO_OK || is_forced_gram(p)) return rc;
     }
     return plan_auto(p, detect, H, pl);
 }
@@ -394,7 +441,7 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
     if (p->n_sc == 0) return CDMIMO_OK;
     CdPlan pl;
     if (int rc = plan_for(p, true, H, &pl)) {
-        if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam || p->form == CDMIMO_FORM_GRAM) return rc;
+        if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam || is_forced_gram(p)) return rc;
         return streaming_launch(p, CDMIMO_OP_DETECT, H, Y, N0, Xhat, s);
     }
     if (pl.learned && !pl.packed) return CDMIMO_ERR_UNSUPPORTED;  // learned sweeps: uniform B_c <= 64
@@ -417,7 +464,7 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
     if (!aligned(H, ea) || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
     if (int rc = plan_for(p, false, H, &pl)) {
-        if (rc != CDMIMO_ERR_UNSUPPORTED || p->form == CDMIMO_FORM_GRAM) return rc;
+        if (rc != CDMIMO_ERR_UNSUPPORTED || is_forced_gram(p)) return rc;
         return streaming_launch(p, CDMIMO_OP_PRECODE, H, S, nullptr, Xdl, s);
     }
     PrecodeIO io{H, reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl), sched};
@@ -818,12 +865,14 @@ int frame_impl(const cdmimo_params* p, const void* H, const void* Y, const float
     if (p->n_sc == 0) return CDMIMO_OK;
     if (!S || !Xdl || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
+    const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr, nullptr,
+                      sched},
+                     reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
+    if ((p->form == CDMIMO_FORM_AUTO || p->form == CDMIMO_FORM_GRAM_TC) && build_frame_tc_plan(p, H, &pl) == CDMIMO_OK)
+        return dispatch_frame_tc(pl, io, s);
     if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
-        build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK) {
-        FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr, nullptr, sched},
-                   reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
+        build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)
         return dispatch_frame_gram(p->in_dtype, pl, io, s);
-    }
     // otherwise the two calls, each in the form it selects
     if (int rc = detect_impl(p, H, Y, N0, Xhat, nullptr, nullptr, sched, s)) return rc;
     return precode_impl(p, H, S, Xdl, sched, s);
@@ -964,10 +1013,18 @@ int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* 
 int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
 {
     if (int rc = validate(p)) return rc;
-    if (op != CDMIMO_OP_DETECT && op != CDMIMO_OP_PRECODE) return CDMIMO_ERR_INVALID_ARG;
+    if (op != CDMIMO_OP_DETECT && op != CDMIMO_OP_PRECODE && op != CDMIMO_OP_FRAME) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
+    if (op == CDMIMO_OP_FRAME) {
+        if ((p->form == CDMIMO_FORM_AUTO || p->form == CDMIMO_FORM_GRAM_TC) && build_frame_tc_plan(p, H, &pl) == CDMIMO_OK)
+            return CDMIMO_FORM_GRAM_TC;
+        if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
+            build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)
+            return CDMIMO_FORM_GRAM;
+        op = CDMIMO_OP_DETECT;
+    }
     const int rc = plan_for(p, op == CDMIMO_OP_DETECT, H, &pl);
-    if (rc == CDMIMO_ERR_UNSUPPORTED && p->form != CDMIMO_FORM_GRAM) return CDMIMO_FORM_RESIDUAL;  // streaming
+    if (rc == CDMIMO_ERR_UNSUPPORTED && !is_forced_gram(p)) return CDMIMO_FORM_RESIDUAL;  // streaming
     if (rc) return rc;
     return pl.gram ? CDMIMO_FORM_GRAM : CDMIMO_FORM_RESIDUAL;
 }
@@ -1253,7 +1310,8 @@ int cdmimo_device_status(int clear)
     if (cudaDeviceSynchronize() != cudaSuccess) return CDMIMO_ERR_CUDA;
     unsigned v = 0;
     if (module_status(&v, clear) != CDMIMO_OK || gram_detect_module_status(&v, clear) != CDMIMO_OK ||
-        gram_precode_module_status(&v, clear) != CDMIMO_OK || gram_frame_module_status(&v, clear) != CDMIMO_OK)
+        gram_precode_module_status(&v, clear) != CDMIMO_OK || gram_frame_module_status(&v, clear) != CDMIMO_OK ||
+        frame_tc_module_status(&v, clear) != CDMIMO_OK)
         return CDMIMO_ERR_CUDA;
     return (int)v;
 }

@@ -72,5 +72,8 @@ int gram_detect_module_status(unsigned* v, int clear);
 int gram_precode_module_status(unsigned* v, int clear);
 int dispatch_frame_gram(int in_dtype, const CdPlan& pl, const FusedIO& io, cudaStream_t s);
 int gram_frame_module_status(unsigned* v, int clear);
+// Entry points of the tensor-core frame translation unit (gram_frame_tc.cu).
+int dispatch_frame_tc(const CdPlan& pl, const FusedIO& io, cudaStream_t s);
+int frame_tc_module_status(unsigned* v, int clear);
 
 }  // namespace cdmimo

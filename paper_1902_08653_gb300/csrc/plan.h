@@ -90,4 +90,10 @@ __host__ __device__ inline int gram_phase_threads(int C, int J, int AT)
     return ((L + 31) / 32 + 3) / 4 * 4 * 32;
 }
 
+// Tile-row stride (entries) of z, x and w in the tensor-core frame kernel: at least n_tiles, 4 mod 16.
+__host__ __device__ constexpr unsigned tc_x_stride(int n_tiles) { return ((unsigned)n_tiles + 11u) / 16u * 16u + 4u; }
+
+// Floats per shared-memory channel row of the tensor-core frame kernel for clusters of Bc antennas.
+__host__ __device__ constexpr unsigned tc_row_floats(int Bc) { return 2u * (unsigned)Bc + 8u; }
+
 }  // namespace cdmimo

@@ -1,0 +1,130 @@
+"""GPU parity of the tensor-core TDD frame kernel (cdmimo_detect_precode with form GRAM_TC, and AUTO
+where it applies): z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w on TF32 MMAs with split FP32
+operands, FP32 sweeps.
+
+Each case is compared with the FP64 oracle (Algorithms 1 and 2 as written) at the 1e-4 relative L2
+bound per vector, and the well-conditioned ones with the FP32 Gram-form frame kernel at 2e-5 (the
+same iterates, different rounding).
+"""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1902_08653_gb300 import cdmimo
+from paper_1902_08653_gb300 import workload as wl
+
+from _util import assert_vectors_close
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    orc.build()
+    cdmimo.lib()
+    cdmimo.device_status(clear=True)
+    return torch.device("cuda:0")
+
+
+def t(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+CASES = {
+    # name: (n_sc, n_sym, cluster sizes, U, K, fuse, snr, compare with the FP32 Gram frame)
+    "cfg2_B256_C8x32_U16": (50, 14, [32] * 8, 16, 3, "colnorm", "sweep", True),
+    "more_subcarriers_than_ctas": (333, 14, [32] * 8, 16, 3, "colnorm", 20.0, True),
+    "one_subcarrier": (1, 14, [32] * 8, 16, 3, "colnorm", 10.0, True),
+    "n_sym16_max_lanes": (23, 16, [32] * 8, 16, 2, "colnorm", 25.0, True),
+    "Bc16_C16_U10_n_sym8": (19, 8, [16] * 16, 10, 3, "colnorm", 20.0, False),
+    "Bc16_U9_odd_symbols": (13, 5, [16] * 6, 9, 4, "equal", 10.0, False),
+    "U12_K1_one_symbol": (29, 1, [32] * 4, 12, 1, "colnorm", 15.0, True),
+    "K5_equal": (17, 14, [32] * 8, 16, 5, "equal", 30.0, True),
+}
+
+
+def run_case(dev, n_sc, n_sym, cs, U, K, fuse, snr, seed, tweak=None):
+    snr = wl.sweep_snr(n_sc) if snr == "sweep" else snr
+    d = wl.uplink(seed, n_sc, n_sym, sum(cs), U, snr_db=snr)
+    if tweak:
+        tweak(d)
+    H32, H64 = wl.as_c64(d["H"])
+    Y32, Y64 = wl.as_c64(d["Y"])
+    S32, S64 = wl.as_c64(d["X"])  # downlink symbols: any U-vectors per (subcarrier, symbol)
+    N0 = d["N0"].astype(np.float32)
+    Ht, Yt, St, Nt = t(H32, dev), t(Y32, dev), t(S32, dev), t(N0, dev)
+    assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, sum(cs), U, cs, K, form="gram_tc", H=Ht) == "gram_tc"
+    X, P = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, K, fuse=fuse, form="gram_tc")
+    Xg, Pg = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, K, fuse=fuse, form="gram")
+    torch.cuda.synchronize()
+    Xo, _, _ = orc.detect(H64, Y64, N0.astype(np.float64), cs, K, fuse=fuse, threads=8)
+    Po = orc.precode(H64, S64, cs, K, threads=8)
+    return X.cpu().numpy(), P.cpu().numpy(), Xg.cpu().numpy(), Pg.cpu().numpy(), Xo, Po
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_frame_tc_matches_oracle(dev, name):
+    n_sc, n_sym, cs, U, K, fuse, snr, vs_gram = CASES[name]
+    X, P, Xg, Pg, Xo, Po = run_case(dev, n_sc, n_sym, cs, U, K, fuse, snr, zlib.crc32(name.encode()) % 1000)
+    assert_vectors_close(X, Xo, TOL, "tc frame Xhat")
+    assert_vectors_close(P, Po, TOL, "tc frame Xdl")
+    if vs_gram:
+        assert_vectors_close(X, Xg, 2e-5, "tc vs fp32 gram frame Xhat")
+        assert_vectors_close(P, Pg, 2e-5, "tc vs fp32 gram frame Xdl")
+    assert cdmimo.device_status(clear=True) == 0
+
+
+def test_frame_tc_zero_column_and_noise_free(dev):
+    """A user with a zero channel in one cluster (the downlink skips it there, p = 0; the uplink's
+    m = 1/alpha keeps its estimate 0) and N0 = 0 on some subcarriers (plain Gauss-Seidel LS)."""
+    cs, U = [32] * 8, 16
+
+    def tweak(d):
+        d["H"][:, 3, 64:96] = 0.0
+        d["N0"][::2] = 0.0
+        d["Y"][:] = np.einsum("fub,fnu->fnb", d["H"], d["X"])
+        d["Y"][1::2] += 0.05 * (np.random.default_rng(5).standard_normal(d["Y"][1::2].shape) + 0j)
+
+    X, P, Xg, Pg, Xo, Po = run_case(dev, 21, 14, cs, U, 3, "colnorm", 20.0, 77, tweak)
+    assert_vectors_close(X, Xo, TOL, "tc frame Xhat")
+    assert_vectors_close(P, Po, TOL, "tc frame Xdl")
+    assert np.isfinite(X).all() and np.isfinite(P).all()
+    assert cdmimo.device_status(clear=True) == 0
+
+
+def test_frame_tc_k0_and_schedules(dev):
+    """K = 0 gives zero outputs; the dynamic schedule (workspace) gives the static schedule's result
+    bit for bit; AUTO runs the tensor-core kernel at the config-2 shape."""
+    cs, U, n_sc, n_sym = [32] * 8, 16, 700, 14
+    d = wl.uplink(4242, n_sc, n_sym, 256, U, snr_db=wl.sweep_snr(n_sc))
+    H32, _ = wl.as_c64(d["H"])
+    Y32, _ = wl.as_c64(d["Y"])
+    S32, _ = wl.as_c64(d["X"])
+    Ht, Yt, St, Nt = t(H32, dev), t(Y32, dev), t(S32, dev), t(d["N0"].astype(np.float32), dev)
+    assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, 256, U, cs, 3, H=Ht) == "gram_tc"
+    assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, 256, U, cs, 3, form="gram", H=Ht) == "gram"
+    X0, P0 = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, 0, form="gram_tc")
+    assert not X0.abs().any() and not P0.abs().any()
+    a = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, 3)
+    b = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, 3, workspace=True)
+    c = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, 3, form="gram_tc")
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+    assert cdmimo.device_status(clear=True) == 0
+
+
+def test_frame_tc_declines_other_shapes(dev):
+    """Shapes outside the kernel's (U <= 8, uneven or other cluster sizes, n_sym > 16, 16-bit
+    storage) run the FP32 Gram frame or the two calls."""
+    for args in ((8, 14, 128, 8, [32] * 4), (8, 14, 192, 16, [64, 64, 64]), (8, 17, 256, 16, [32] * 8),
+                 (8, 14, 256, 16, [48, 16] * 4)):
+        n_sc, n_sym, B, U, cs = args
+        assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, 3) != "gram_tc"
+    assert cdmimo.selected_form(cdmimo.OP_FRAME, 8, 14, 256, 16, [32] * 8, 3, in_dtype=cdmimo.C16F) != "gram_tc"
