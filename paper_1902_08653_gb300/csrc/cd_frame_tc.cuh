@@ -3,7 +3,8 @@
 // per subcarrier, in Gram form (see cd_gram.cuh), like cd_frame_gram_kernel, but with
 //   z = H_c^H y_c,  G_c = H_c^H H_c  (phase A)   and   x_c = H_c w  (phase C)
 // computed by warp-level tensor-core MMAs (mma.sync m16n8k8, TF32 operands, FP32 accumulation),
-// one warp per cluster.  The sweeps (phase B) are the FP32 Gauss-Seidel steps of the SIMT kernel.
+// one warp per cluster.  The sweeps (phase B) are FP32 Gauss-Seidel steps, one lane per (cluster,
+// symbol) running the uplink and the downlink vector side by side.
 //
 // FP32 accuracy from TF32 operands.  Every FP32 operand x is split as x = hi + lo, hi = x with its
 // 13 low mantissa bits cleared (a TF32 value) and lo = x - hi (exact in FP32, |lo| < 2^-10 |x|); the
@@ -103,6 +104,75 @@ __device__ __forceinline__ void issue_channel_copy_tc(const CdPlan& pl, const Cl
     }
 }
 
+// Phase B with two vectors per lane: the uplink x and the downlink w of one (cluster, symbol) tile
+// read the same rows of G_c, so each 16-byte pair of a row loaded from shared memory feeds eight
+// packed FMAs (four per vector).  The sweeps are bound by the shared-memory pipe (each row pair
+// costs four of its cycles whichever lanes read it), and two vectors per lane halve its load.
+
+// Sum_v Gt_uv x_v and Sum_v Gt_uv w_v over the first npu pairs of row gr (as gram_row_dot).  In the
+// full sweeps the pairs are visited from the one after the pair holding x_{u-1}, so that only the
+// last pair's terms wait for the previous step.
+template <int UT>
+__device__ __forceinline__ void gram_row_dot2(const float4* gr, int u, int npu, const float4 (&x)[UT / 2],
+                                              const float4 (&w)[UT / 2], float2& dx, float2& dw)
+{
+    constexpr int NP = UT / 2;
+    const int s = npu < NP ? 0 : ((((u + UT - 1) % UT) >> 1) + 1) % NP;
+    const float2 z = make_float2(0.f, 0.f);
+    float2 Rx = z, Jx = z, Ix = z, Kx = z, Rw = z, Jw = z, Iw = z, Kw = z;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        if (k < npu) {
+            const int i = (s + k) % NP;
+            const float4 g = gr[i];
+            Rx = ffma2(lo2(g), lo2(x[i]), Rx);
+            Rw = ffma2(lo2(g), lo2(w[i]), Rw);
+            Jx = ffma2(hi2(g), hi2(x[i]), Jx);
+            Jw = ffma2(hi2(g), hi2(w[i]), Jw);
+            Ix = ffma2(lo2(g), hi2(x[i]), Ix);
+            Iw = ffma2(lo2(g), hi2(w[i]), Iw);
+            Kx = ffma2(hi2(g), lo2(x[i]), Kx);
+            Kw = ffma2(hi2(g), lo2(w[i]), Kw);
+        }
+    }
+    dx = make_float2((Rx.x + Rx.y) - (Jx.x + Jx.y), (Ix.x + Ix.y) + (Kx.x + Kx.y));
+    dw = make_float2((Rw.x + Rw.y) - (Jw.x + Jw.y), (Iw.x + Iw.y) + (Kw.x + Kw.y));
+}
+
+// K Gauss-Seidel sweeps for x (coefficients dx_, right-hand side bx with stride bxs) and for w
+// (dw_, bw, bws) on the same Gram rows, from zero, as gram_sweeps does for one vector (the first
+// sweep sums only the pairs holding some x_v, v < u).
+template <int UT>
+__device__ __forceinline__ void gram_sweeps2(int U, int K, const float4* Grow, const float* dx_, const float* dw_,
+                                             const float2* bx, uint32_t bxs, const float2* bw, uint32_t bws,
+                                             float4 (&x)[UT / 2], float4 (&w)[UT / 2])
+{
+    constexpr int NP = UT / 2;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        w[i] = x[i];
+    }
+    if (K < 1) return;
+    auto step = [&](int u, int npu) {
+        float2 ddx, ddw;
+        gram_row_dot2<UT>(Grow + u * NP, u, npu, x, w, ddx, ddw);
+        const float2 bxu = bx[u * bxs], bwu = bw[u * bws];
+        const float du = dx_[u], eu = dw_[u];
+        set_entry(x[u >> 1], u, du * (bxu.x - ddx.x), du * (bxu.y - ddx.y));
+        set_entry(w[u >> 1], u, eu * (bwu.x - ddw.x), eu * (bwu.y - ddw.y));
+    };
+#pragma unroll
+    for (int u = 0; u < UT; ++u)
+        if (u < U) step(u, (u + 1) / 2);
+#pragma unroll 1
+    for (int t = 1; t < K; ++t) {
+#pragma unroll
+        for (int u = 0; u < UT; ++u)
+            if (u < U) step(u, NP);
+    }
+}
+
 template <int BC>
 __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan pl, const FusedIO io)
 {
@@ -149,8 +219,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     }
     __syncthreads();
 
-    // Phase B lanes: one per uplink or downlink (cluster, symbol) tile, as in the SIMT frame kernel.
-    const GLane gb = frame_lane(0, C, 2 * n_sym, 1);
+    // Phase B lanes: one per (cluster, symbol), holding that tile's uplink x and downlink w.
+    const GLane gb = frame_lane(0, C, n_sym, 1);
 
     int f = blockIdx.x;
     if (tid == 0 && f < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[0]);
@@ -257,26 +327,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         }
         __syncthreads();
 
-        // Phase B: uplink sweeps on x (right-hand side z), downlink sweeps on w (right-hand side s);
-        // the downlink lanes keep w in registers until every lane has finished reading G.
+        // Phase B: uplink sweeps on x (right-hand side z) and downlink sweeps on w (right-hand side s)
+        // in the same lane; w stays in registers until every lane has finished reading G.
         const unsigned ticket = (d.sched && tid == 0) ? atomicAdd(d.sched, 1u) : 0u;
-        float4 x[UT / 2];
-        const bool ul = gb.j < n_sym;
-        const int n_b = ul ? gb.j : gb.j - n_sym;
-        const int tile = gb.c * n_sym + n_b;
+        float4 x[UT / 2], xw[UT / 2];
+        const int n_b = gb.j, tile = gb.c * n_sym + n_b;
         if (gb.active) {
-            const float* dd = (ul ? Dm : Dp) + gb.c * UT;
-            const float2* rhs = ul ? Zs + tile : Ss + n_b;
-            gram_sweeps<UT>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, rhs, ul ? xs : (uint32_t)n_sym, x);
-            if (ul) {
+            const float* dd = Dm + gb.c * UT;
+            gram_sweeps2<UT>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, Dp + gb.c * UT, Zs + tile, xs, Ss + n_b,
+                             (uint32_t)n_sym, x, xw);
 #pragma unroll
-                for (int u = 0; u < UT; ++u)
-                    if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
-                if (n_b == 0) {
-                    float msum = 0.f;
-                    for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
-                    lam[gb.c] = 1.f / msum;
-                }
+            for (int u = 0; u < UT; ++u)
+                if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
+            if (n_b == 0) {
+                float msum = 0.f;
+                for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
+                lam[gb.c] = 1.f / msum;
             }
         }
         if (tid == 0) {
@@ -289,11 +355,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
             if (nf < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[b ^ 1]);
         }
         __syncthreads();
-        if (gb.active && !ul) {
+        if (gb.active) {
 #pragma unroll
             for (int u = 0; u < UT; ++u)
-                if (u < U) Ws[tile + u * xs] = slice_entry<UT, 1>(x, u);
+                if (u < U) Ws[tile + u * xs] = slice_entry<UT, 1>(xw, u);
         }
+
         __syncthreads();
 
         // Phase C: the next subcarrier's channel copy (into the other buffer, last read in the
