@@ -77,15 +77,15 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             sweep and vector plus U B_c (z or H_c w) and U^2 B_c / n_sym (G_c).  Requires U <= 16,
  *             equal lanes per cluster tile (8 < B_c <= 64 for all clusters, or all B_c <= 16, ...:
  *             the packed-kernel shapes) and no learned block; otherwise CDMIMO_ERR_UNSUPPORTED.
- *   GRAM_TC   GRAM, with the TDD frame's (cdmimo_detect_precode) contractions z = H_c^H y_c,
- *             G_c = H_c^H H_c and x_c = H_c w on the tensor cores (TF32 MMAs with each FP32 operand
- *             split into two TF32 parts, FP32 accumulation; the sweeps stay FP32).  That kernel
- *             takes c64 storage, every B_c = 16 or every B_c = 32, 8 < U <= 16, n_sym <= 16,
- *             2 C n_sym <= 256 and no learned block; elsewhere (and for cdmimo_detect and
- *             cdmimo_precode) GRAM_TC is GRAM.
+ *   GRAM_TC   GRAM, with the contractions z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w on the
+ *             tensor cores (TF32 MMAs with each FP32 operand split into a TF32 part and its
+ *             remainder, FP32 accumulation; the sweeps stay FP32), for cdmimo_detect (without
+ *             Xc_opt / lambda_opt), cdmimo_precode and cdmimo_detect_precode.  That kernel takes
+ *             c64 storage, every B_c = 16 or every B_c = 32, 8 < U <= 16, n_sym <= 16,
+ *             2 C n_sym <= 256 and no learned block; elsewhere GRAM_TC is GRAM.
  *   AUTO      GRAM where it applies, every B_c >= 2 U (so G_c + (N0/Ex) I stays well conditioned
- *             in FP32) and it needs fewer complex MACs, with the frame on the tensor cores where
- *             GRAM_TC's kernel takes the shape; else RESIDUAL.
+ *             in FP32) and it needs fewer complex MACs, on the tensor cores where GRAM_TC's kernel
+ *             takes the call; else RESIDUAL.
  */
 typedef enum {
     CDMIMO_FORM_AUTO = 0,
@@ -416,12 +416,12 @@ size_t cdmimo_workspace_size(const cdmimo_params* p, int op);
  * cdmimo_detect_precode_host (op FRAME) need for p; 0 for an invalid p or op. */
 size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
 
-/* The evaluation form (CDMIMO_FORM_RESIDUAL or CDMIMO_FORM_GRAM) that cdmimo_detect (op =
- * CDMIMO_OP_DETECT) or cdmimo_precode (CDMIMO_OP_PRECODE) would run for p and a channel at H (its
- * alignment decides the staging path), or a negative status (for example UNSUPPORTED for a forced
- * GRAM that does not apply).  op = CDMIMO_OP_FRAME: the form of cdmimo_detect_precode's one-kernel
- * frame (CDMIMO_FORM_GRAM_TC on the tensor cores, CDMIMO_FORM_GRAM), or, where it enqueues two
- * calls, the uplink's form.  Host only: nothing is launched. */
+/* The evaluation form (CDMIMO_FORM_RESIDUAL, CDMIMO_FORM_GRAM or CDMIMO_FORM_GRAM_TC) that
+ * cdmimo_detect (op = CDMIMO_OP_DETECT, without Xc_opt / lambda_opt) or cdmimo_precode
+ * (CDMIMO_OP_PRECODE) would run for p and a channel at H (its alignment decides the staging path), or
+ * a negative status (for example UNSUPPORTED for a forced GRAM that does not apply).
+ * op = CDMIMO_OP_FRAME: the form of cdmimo_detect_precode's one-kernel frame, or, where it enqueues
+ * two calls, the uplink's form.  Host only: nothing is launched. */
 int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H);
 
 /* Static name of a status code. */

@@ -34,6 +34,9 @@ namespace cdmimo {
 
 constexpr int kTcUT = 16;        // users per cluster in the MMA tiles (rows U..15 are zero)
 constexpr int kTcThreads = 256;  // eight warps: one per cluster in phases A and C
+// What one launch computes: the TDD frame, the uplink alone (cdmimo_detect) or the downlink alone
+// (cdmimo_precode).  Each mode compiles only its own steps.
+constexpr int kTcFrame = 0, kTcDetect = 1, kTcPrecode = 2;
 
 // x = hi + lo (see above); the negated split of -x is the two values with the sign bit flipped.
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo)
@@ -173,9 +176,10 @@ __device__ __forceinline__ void gram_sweeps2(int U, int K, const float4* Grow, c
     }
 }
 
-template <int BC>
+template <int BC, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan pl, const FusedIO io)
 {
+    constexpr bool UL = MODE != kTcPrecode, DL = MODE != kTcDetect;
     constexpr int UT = kTcUT;
     constexpr int SROW = (int)tc_row_floats(BC);  // floats per channel row
     constexpr int SR2 = SROW / 2;     // the same in complex entries
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     }
     __syncthreads();
 
-    // Phase B lanes: one per (cluster, symbol), holding that tile's uplink x and downlink w.
+    // Phase B lanes: one per (cluster, symbol), holding that tile's uplink x and (or) downlink w.
     const GLane gb = frame_lane(0, C, n_sym, 1);
 
     int f = blockIdx.x;
@@ -227,18 +231,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     __syncthreads();
     if (f < pl.n_sc) issue_channel_copy_tc(pl, tab, d.H, f, Hbuf(0), SROW, &bar[0]);
     auto put_s = [&](int i, float2 v) { Ss[(i % U) * n_sym + i / U] = v; };
-    if (f < pl.n_sc)
+    if (DL && f < pl.n_sc)
         for (int i = tid; i < n_s; i += blockDim.x) put_s(i, io.S[(size_t)f * n_s + i]);
 
     int done = 0;
     for (int k = 0; f < pl.n_sc; ++k) {
         const int b = k & 1;
-        float alpha = __ldg(d.N0 + f) * pl.inv_Ex;
-        float out_scale = 1.f;
-        if (!(alpha >= 0.f)) {
-            if (tid == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_N0);
-            out_scale = __int_as_float(0x7fc00000);
-            alpha = 0.f;
+        float alpha = 0.f, out_scale = 1.f;
+        if constexpr (UL) {
+            alpha = __ldg(d.N0 + f) * pl.inv_Ex;
+            if (!(alpha >= 0.f)) {
+                if (tid == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_N0);
+                out_scale = __int_as_float(0x7fc00000);
+                alpha = 0.f;
+            }
         }
         const uint32_t parity = (uint32_t)(k >> 1) & 1u;
         const bool ok = mbar_wait_bounded(&bar[b], parity);
@@ -249,12 +255,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         }
         const float* Hb = Hbuf(b);
 
-        // Phase A: per cluster (one warp), G_c (4 n-tiles: Re and Im of columns 0-7, 8-15) and z
-        // (4 n-tiles: Re and Im of symbols 0-7, 8-15), over KA k-steps.
+        // Phase A: per cluster (one warp), G_c (4 n-tiles: Re and Im of columns 0-7, 8-15) and, for
+        // the uplink, z (4 n-tiles: Re and Im of symbols 0-7, 8-15), over KA k-steps.
         for (int c = warp; c < C; c += kTcThreads / 32) {
             const float2* Hc2 = reinterpret_cast<const float2*>(Hb + c * UT * SROW);
             const ClusterTile ct = tab[c];
-            const float2* Yc = reinterpret_cast<const float2*>(d.Y) + (size_t)f * n_sym * pl.B + ct.off;
+            const float2* Yc = UL ? reinterpret_cast<const float2*>(d.Y) + (size_t)f * n_sym * pl.B + ct.off : nullptr;
             float accG[4][4], accZ[4][4];
 #pragma unroll
             for (int t = 0; t < 4; ++t)
@@ -270,8 +276,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     dst[j] = n < n_sym ? __ldg(Yc + (size_t)n * pl.B + 4 * ks + tig) : make_float2(0.f, 0.f);
                 }
             };
-            load_y(0, yv[0]);
-            if (KA > 1) load_y(1, yv[1]);
+            if constexpr (UL) {
+                load_y(0, yv[0]);
+                if (KA > 1) load_y(1, yv[1]);
+            }
 #pragma unroll
             for (int ks = 0; ks < KA; ++ks) {
                 const int e = 4 * ks + tig;  // the lane's complex entry of this k-step
@@ -284,14 +292,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     mma_3xtf32(accG[j], ah, al, bp);
                     mma_3xtf32(accG[2 + j], ah, al, br);
                 }
+                if constexpr (UL) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    BFrag bp, br;
-                    b_frags(yv[ks & 1][j], bp, br);
-                    mma_3xtf32(accZ[j], ah, al, bp);
-                    mma_3xtf32(accZ[2 + j], ah, al, br);
+                    for (int j = 0; j < 2; ++j) {
+                        BFrag bp, br;
+                        b_frags(yv[ks & 1][j], bp, br);
+                        mma_3xtf32(accZ[j], ah, al, bp);
+                        mma_3xtf32(accZ[2 + j], ah, al, br);
+                    }
+                    if (ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
                 }
-                if (ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
             }
             // G rows (pair-planar, zero diagonal) with m_u and p_u^2 from the diagonal; rows u = gid,
             // gid + 8, columns v = 8 j + 2 tig, +1 (accumulator element 2 r + e)
@@ -313,36 +323,45 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     Gc[u * (UT / 2) + (v >> 1)] = make_float4(g0, g1, i0, i1);
                 }
             // z for tile (c, n): rows u = gid, gid + 8, symbols n = 8 j + 2 tig, +1
+            if constexpr (UL) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+                for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int u = gid + 8 * r, n = 8 * j + 2 * tig;
-                    if (u < U) {
-                        float2* z = Zs + u * xs + c * n_sym;
-                        if (n < n_sym) z[n] = make_float2(accZ[j][2 * r], accZ[2 + j][2 * r]);
-                        if (n + 1 < n_sym) z[n + 1] = make_float2(accZ[j][2 * r + 1], accZ[2 + j][2 * r + 1]);
+                    for (int r = 0; r < 2; ++r) {
+                        const int u = gid + 8 * r, n = 8 * j + 2 * tig;
+                        if (u < U) {
+                            float2* z = Zs + u * xs + c * n_sym;
+                            if (n < n_sym) z[n] = make_float2(accZ[j][2 * r], accZ[2 + j][2 * r]);
+                            if (n + 1 < n_sym) z[n + 1] = make_float2(accZ[j][2 * r + 1], accZ[2 + j][2 * r + 1]);
+                        }
                     }
-                }
+            }
         }
         __syncthreads();
 
-        // Phase B: uplink sweeps on x (right-hand side z) and downlink sweeps on w (right-hand side s)
-        // in the same lane; w stays in registers until every lane has finished reading G.
+        // Phase B: uplink sweeps on x (right-hand side z) and downlink sweeps on w (right-hand side s),
+        // in the same lane for the frame; w stays in registers until every lane has finished reading G.
         const unsigned ticket = (d.sched && tid == 0) ? atomicAdd(d.sched, 1u) : 0u;
         float4 x[UT / 2], xw[UT / 2];
         const int n_b = gb.j, tile = gb.c * n_sym + n_b;
         if (gb.active) {
+            const float4* Gc = Gs + (size_t)gb.c * UT * (UT / 2);
             const float* dd = Dm + gb.c * UT;
-            gram_sweeps2<UT>(U, pl.K, Gs + (size_t)gb.c * UT * (UT / 2), dd, Dp + gb.c * UT, Zs + tile, xs, Ss + n_b,
-                             (uint32_t)n_sym, x, xw);
+            if constexpr (MODE == kTcFrame)
+                gram_sweeps2<UT>(U, pl.K, Gc, dd, Dp + gb.c * UT, Zs + tile, xs, Ss + n_b, (uint32_t)n_sym, x, xw);
+            else if constexpr (MODE == kTcDetect)
+                gram_sweeps<UT>(U, pl.K, Gc, dd, Zs + tile, xs, x);
+            else
+                gram_sweeps<UT>(U, pl.K, Gc, Dp + gb.c * UT, Ss + n_b, (uint32_t)n_sym, xw);
+            if constexpr (UL) {
 #pragma unroll
-            for (int u = 0; u < UT; ++u)
-                if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
-            if (n_b == 0) {
-                float msum = 0.f;
-                for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
-                lam[gb.c] = 1.f / msum;
+                for (int u = 0; u < UT; ++u)
+                    if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
+                if (n_b == 0) {
+                    float msum = 0.f;
+                    for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
+                    lam[gb.c] = 1.f / msum;
+                }
             }
         }
         if (tid == 0) {
@@ -355,31 +374,32 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
             if (nf < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[b ^ 1]);
         }
         __syncthreads();
-        if (gb.active) {
+        if constexpr (DL) {
+            if (gb.active) {
 #pragma unroll
-            for (int u = 0; u < UT; ++u)
-                if (u < U) Ws[tile + u * xs] = slice_entry<UT, 1>(xw, u);
+                for (int u = 0; u < UT; ++u)
+                    if (u < U) Ws[tile + u * xs] = slice_entry<UT, 1>(xw, u);
+            }
+            __syncthreads();
         }
-
-        __syncthreads();
 
         // Phase C: the next subcarrier's channel copy (into the other buffer, last read in the
         // previous iteration) and its y into L2; the next s is loaded now and stored at the end.
-        // Per cluster (one warp): x_c = H_c w for all symbols (MT x 4 tiles), normalized per symbol.
-        // Then the uplink fusion.
+        // Downlink, per cluster (one warp): x_c = H_c w for all symbols (MT x 4 tiles), normalized
+        // per symbol.  Then the uplink fusion.
         const int fn = nxt[b];
         if (fn < pl.n_sc) issue_channel_copy_tc(pl, tab, d.H, fn, Hbuf(b ^ 1), SROW, &bar[b ^ 1]);
-        if (tid == 32 && fn < pl.n_sc)
+        if (UL && tid == 32 && fn < pl.n_sc)
             bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * 8u, (uint32_t)n_sym * pl.B * 8u);
         constexpr int kSv = 2;
-        const bool ld_s = fn < pl.n_sc;
-        const float2* s_src = io.S + (size_t)min(fn, pl.n_sc - 1) * n_s;
+        const bool ld_s = DL && fn < pl.n_sc;
+        const float2* s_src = DL ? io.S + (size_t)min(fn, pl.n_sc - 1) * n_s : nullptr;
         float2 sv[kSv];
 #pragma unroll
         for (int q = 0; q < kSv; ++q)
             sv[q] = (ld_s && tid + q * kTcThreads < n_s) ? s_src[tid + q * kTcThreads] : make_float2(0.f, 0.f);
 
-        for (int c = warp; c < C; c += kTcThreads / 32) {
+        for (int c = warp; DL && c < C; c += kTcThreads / 32) {
             const float2* Hc2 = reinterpret_cast<const float2*>(Hb + c * UT * SROW);
             const ClusterTile ct = tab[c];
             float acc[MT][4][4];
@@ -440,7 +460,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     }
                 }
         }
-        fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
+        if constexpr (UL) fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
         if (ld_s) {
 #pragma unroll
             for (int q = 0; q < kSv; ++q)

@@ -1,6 +1,7 @@
-"""GPU parity of the tensor-core TDD frame kernel (cdmimo_detect_precode with form GRAM_TC, and AUTO
-where it applies): z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w on TF32 MMAs with split FP32
-operands, FP32 sweeps.
+"""GPU parity of the tensor-core Gram-form kernel (form GRAM_TC, and AUTO where it applies) in its
+three modes: the TDD frame (cdmimo_detect_precode), the uplink alone (cdmimo_detect) and the
+downlink alone (cdmimo_precode).  z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w run on TF32 MMAs
+with split FP32 operands; the sweeps are FP32.
 
 Each case is compared with the FP64 oracle (Algorithms 1 and 2 as written) at the 1e-4 relative L2
 bound per vector, and the well-conditioned ones with the FP32 Gram-form frame kernel at 2e-5 (the
@@ -128,3 +129,53 @@ def test_frame_tc_declines_other_shapes(dev):
         n_sc, n_sym, B, U, cs = args
         assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, 3) != "gram_tc"
     assert cdmimo.selected_form(cdmimo.OP_FRAME, 8, 14, 256, 16, [32] * 8, 3, in_dtype=cdmimo.C16F) != "gram_tc"
+
+
+@pytest.mark.parametrize("name", ["cfg2_B256_C8x32_U16", "more_subcarriers_than_ctas", "Bc16_C16_U10_n_sym8",
+                                  "Bc16_U9_odd_symbols", "U12_K1_one_symbol", "K5_equal"])
+def test_detect_and_precode_tc_match_oracle(dev, name):
+    """cdmimo_detect and cdmimo_precode alone on the tensor-core kernel (uplink and downlink modes)."""
+    n_sc, n_sym, cs, U, K, fuse, snr, vs_gram = CASES[name]
+    snr = wl.sweep_snr(n_sc) if snr == "sweep" else snr
+    d = wl.uplink(zlib.crc32(name.encode()) % 1000 + 1, n_sc, n_sym, sum(cs), U, snr_db=snr)
+    H32, H64 = wl.as_c64(d["H"])
+    Y32, Y64 = wl.as_c64(d["Y"])
+    S32, S64 = wl.as_c64(d["X"])
+    N0 = d["N0"].astype(np.float32)
+    Ht, Yt, St, Nt = t(H32, dev), t(Y32, dev), t(S32, dev), t(N0, dev)
+    for op in (cdmimo.OP_DETECT, cdmimo.OP_PRECODE):
+        assert cdmimo.selected_form(op, n_sc, n_sym, sum(cs), U, cs, K, form="gram_tc", H=Ht) == "gram_tc"
+    X = cdmimo.detect(Ht, Yt, Nt, cs, K, fuse=fuse, form="gram_tc").cpu().numpy()
+    P = cdmimo.precode(Ht, St, cs, K, form="gram_tc").cpu().numpy()
+    Xo, _, _ = orc.detect(H64, Y64, N0.astype(np.float64), cs, K, fuse=fuse, threads=8)
+    Po = orc.precode(H64, S64, cs, K, threads=8)
+    assert_vectors_close(X, Xo, TOL, "tc detect")
+    assert_vectors_close(P, Po, TOL, "tc precode")
+    if vs_gram:
+        Xg = cdmimo.detect(Ht, Yt, Nt, cs, K, fuse=fuse, form="gram").cpu().numpy()
+        Pg = cdmimo.precode(Ht, St, cs, K, form="gram").cpu().numpy()
+        assert_vectors_close(X, Xg, 2e-5, "tc vs fp32 gram detect")
+        assert_vectors_close(P, Pg, 2e-5, "tc vs fp32 gram precode")
+    # the frame on the same data gives the same uplink and downlink bits as the two calls
+    Xf, Pf = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, K, fuse=fuse, form="gram_tc")
+    assert_vectors_close(Xf.cpu().numpy(), X, 2e-5, "tc frame vs tc detect")
+    assert_vectors_close(Pf.cpu().numpy(), P, 2e-5, "tc frame vs tc precode")
+    assert cdmimo.device_status(clear=True) == 0
+
+
+def test_detect_tc_with_per_cluster_outputs_uses_fp32_gram(dev):
+    """Xc_opt / lambda_opt are written by the FP32 Gram kernel: a call that asks for them returns
+    exactly what form GRAM returns."""
+    cs, U, n_sc = [32] * 8, 16, 9
+    d = wl.uplink(606, n_sc, 14, 256, U, snr_db=20.0)
+    Ht, Yt = t(wl.as_c64(d["H"])[0], dev), t(wl.as_c64(d["Y"])[0], dev)
+    Nt = t(d["N0"].astype(np.float32), dev)
+    mk = lambda: (torch.empty((n_sc, 8, 14, U), dtype=torch.complex64, device=dev),
+                  torch.empty((n_sc, 8), dtype=torch.float32, device=dev))
+    Xc_a, lam_a = mk()
+    Xc_b, lam_b = mk()
+    a = cdmimo.detect(Ht, Yt, Nt, cs, 3, Xc=Xc_a, lam=lam_a, form="gram_tc")
+    b = cdmimo.detect(Ht, Yt, Nt, cs, 3, Xc=Xc_b, lam=lam_b, form="gram")
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(Xc_a, Xc_b) and torch.equal(lam_a, lam_b)
+    assert cdmimo.device_status(clear=True) == 0

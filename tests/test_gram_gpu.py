@@ -134,8 +134,9 @@ def test_gram_low_precision_storage(dev, kind):
 
 def test_gram_full_size_schedules_and_auto(dev):
     """The 1200-subcarrier workload in the persistent launch: dynamic and static schedules agree bit
-    for bit, AUTO selects the Gram form here (same bits as form="gram"), and sampled subcarriers
-    (first, counter-handed, last) match the oracle."""
+    for bit, AUTO selects the Gram form on the tensor cores here (within 2e-5 of form="gram", the
+    same iterates with other rounding), and sampled subcarriers (first, counter-handed, last) match
+    the oracle."""
     cs, U, K, n_sc = [32] * 8, 16, 3, 1200
     d = wl.uplink(20190222, n_sc, 14, 256, U, snr_db=wl.sweep_snr(n_sc))
     H32, H64 = wl.as_c64(d["H"])
@@ -151,8 +152,9 @@ def test_gram_full_size_schedules_and_auto(dev):
     pb = cdmimo.precode(Ht, St, cs, K, form="gram", workspace=False)
     pc = cdmimo.precode(Ht, St, cs, K)
     torch.cuda.synchronize()
-    assert torch.equal(a, b) and torch.equal(a, c)
-    assert torch.equal(pa, pb) and torch.equal(pa, pc)
+    assert torch.equal(a, b) and torch.equal(pa, pb)
+    assert_vectors_close(c.cpu().numpy(), a.cpu().numpy(), 2e-5, "auto (tensor cores) vs gram detect")
+    assert_vectors_close(pc.cpu().numpy(), pa.cpu().numpy(), 2e-5, "auto (tensor cores) vs gram precode")
     idx = np.r_[0:3, 700:704, n_sc - 3:n_sc]
     Xo, _, _ = orc.detect(H64[idx], Y64[idx], N0.astype(np.float64)[idx], cs, K, threads=8)
     assert_vectors_close(a.cpu().numpy()[idx], Xo, TOL, "full-size detect")
@@ -184,7 +186,8 @@ def test_selector_rules(dev):
 def test_selected_form_query(dev):
     H = torch.zeros((4, 16, 256), dtype=torch.complex64, device=dev)
     q = lambda op, **kw: cdmimo.selected_form(op, 4, 14, 256, 16, [32] * 8, 3, H=H, **kw)
-    assert q(cdmimo.OP_DETECT) == "gram" and q(cdmimo.OP_PRECODE) == "gram"
+    assert q(cdmimo.OP_DETECT) == "gram_tc" and q(cdmimo.OP_PRECODE) == "gram_tc"
+    assert q(cdmimo.OP_DETECT, form="gram") == "gram" and q(cdmimo.OP_PRECODE, form="gram") == "gram"
     assert q(cdmimo.OP_DETECT, form="residual") == "residual"
     # one OFDM symbol per subcarrier: the Gram matrix does not pay for itself
     assert cdmimo.selected_form(cdmimo.OP_DETECT, 4, 1, 256, 16, [32] * 8, 3, H=H) == "residual"
