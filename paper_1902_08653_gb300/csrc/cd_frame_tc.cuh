@@ -34,9 +34,10 @@ namespace cdmimo {
 
 constexpr int kTcUT = 16;        // users per cluster in the MMA tiles (rows U..15 are zero)
 constexpr int kTcThreads = 256;  // eight warps: one per cluster in phases A and C
-// What one launch computes: the TDD frame, the uplink alone (cdmimo_detect) or the downlink alone
-// (cdmimo_precode).  Each mode compiles only its own steps.
-constexpr int kTcFrame = 0, kTcDetect = 1, kTcPrecode = 2;
+// What one launch computes: the TDD frame, the uplink alone (cdmimo_detect), the downlink alone
+// (cdmimo_precode), or the uplink with the learned sweeps and fusion of a cdmimo_learned block.
+// Each mode compiles only its own steps.
+constexpr int kTcFrame = 0, kTcDetect = 1, kTcPrecode = 2, kTcDetectLearned = 3;
 
 // x = hi + lo (see above); the negated split of -x is the two values with the sign bit flipped.
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo)
@@ -179,7 +180,8 @@ __device__ __forceinline__ void gram_sweeps2(int U, int K, const float4* Grow, c
 template <int BC, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan pl, const FusedIO io)
 {
-    constexpr bool UL = MODE != kTcPrecode, DL = MODE != kTcDetect;
+    constexpr bool UL = MODE != kTcPrecode, DL = MODE == kTcFrame || MODE == kTcPrecode;
+    constexpr bool LEARNED = MODE == kTcDetectLearned;
     constexpr int UT = kTcUT;
     constexpr int SROW = (int)tc_row_floats(BC);  // floats per channel row
     constexpr int SR2 = SROW / 2;     // the same in complex entries
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     float4* Gs = reinterpret_cast<float4*>(smem + pl.off_G);  // [C][UT][UT/2] pair-planar rows, zero diagonal
     float2* Ws = reinterpret_cast<float2*>(smem + pl.off_G);  // [U][x_stride] w per tile, after the sweeps
     float* Dm = reinterpret_cast<float*>(smem + pl.off_E);    // [C][UT] m_u
-    float* Dp = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] p_u^2
+    float* Dp = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] p_u^2 (learned: ||h_u||^2)
     float2* Zs = reinterpret_cast<float2*>(smem + pl.off_X);  // [UT][x_stride]: z, then each tile's x
     float2* Ss = reinterpret_cast<float2*>(smem + pl.off_S);  // [U][n_sym]: s of the subcarrier, transposed
     float* lam = reinterpret_cast<float*>(smem + pl.off_lam);
@@ -201,10 +203,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     int* nxt = reinterpret_cast<int*>(smem + pl.off_bar + 16);
     auto Hbuf = [&](int j) { return reinterpret_cast<float*>(smem + (j ? pl.off_H2 : 0u)); };
     const DetectIO& d = io.d;
+    const cdmimo_learned* blk = reinterpret_cast<const cdmimo_learned*>(d.learned);
+    float* mlp = reinterpret_cast<float*>(smem + pl.off_mlp);  // [C][hidden] (learned fusion)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym, n_s = n_sym * U;
     const uint32_t xs = tc_x_stride(pl.n_tiles);
+    bool learned_ok = true;
+    if constexpr (LEARNED) {
+        const int hd = __ldg(&blk->hidden);
+        learned_ok = __ldg(&blk->K) == pl.K && __ldg(&blk->U) == U && hd >= 1 && hd <= CDMIMO_MAX_HIDDEN;
+        if (!learned_ok && tid == 0 && blockIdx.x == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_LEARNED);
+    }
 
     // Setup: cluster table, barriers, zero channel rows U..UT-1 of both buffers (never copied).
     if (tid < C) tab[tid] = pl.cl[tid];
@@ -245,6 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                 out_scale = __int_as_float(0x7fc00000);
                 alpha = 0.f;
             }
+            if (LEARNED && !learned_ok) out_scale = __int_as_float(0x7fc00000);
         }
         const uint32_t parity = (uint32_t)(k >> 1) & 1u;
         const bool ok = mbar_wait_bounded(&bar[b], parity);
@@ -316,7 +327,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     if (v == u || v + 1 == u) {
                         const float e = v == u ? g0 : g1, den = e + alpha;
                         Dm[c * UT + u] = (u < U && den > 0.f) ? __fdividef(1.f, den) : 0.f;
-                        Dp[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
+                        if constexpr (LEARNED) Dp[c * UT + u] = e;
+                        else Dp[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
                         if (v == u) g0 = i0 = 0.f;
                         else g1 = i1 = 0.f;
                     }
@@ -351,6 +363,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                 gram_sweeps2<UT>(U, pl.K, Gc, dd, Dp + gb.c * UT, Zs + tile, xs, Ss + n_b, (uint32_t)n_sym, x, xw);
             else if constexpr (MODE == kTcDetect)
                 gram_sweeps<UT>(U, pl.K, Gc, dd, Zs + tile, xs, x);
+            else if constexpr (LEARNED)
+                gram_sweeps_learned<UT>(U, learned_ok ? pl.K : 0, Gc, Dp + gb.c * UT, alpha, blk, Zs + tile, xs, x);
             else
                 gram_sweeps<UT>(U, pl.K, Gc, Dp + gb.c * UT, Ss + n_b, (uint32_t)n_sym, xw);
             if constexpr (UL) {
@@ -460,7 +474,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     }
                 }
         }
-        if constexpr (UL) fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
+        if constexpr (LEARNED) {
+            if (pl.fuse == CDMIMO_FUSE_LEARNED) {  // lambda = softmax of the MLP on ||h_u||^2 / B_c and log10 alpha
+                learned_lambda(pl, blk, learned_ok, alpha, tab, mlp, lam, nullptr, f,
+                               [&](int cc, int j) { return Dp[cc * UT + j]; });
+                __syncthreads();
+                fuse_subcarrier<true>(pl, d, f, lam, Zs, xs, out_scale);
+            } else {
+                fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
+            }
+        } else if constexpr (UL) {
+            fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
+        }
         if (ld_s) {
 #pragma unroll
             for (int q = 0; q < kSv; ++q)

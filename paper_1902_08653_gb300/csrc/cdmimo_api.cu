@@ -298,14 +298,15 @@ bool is_forced_gram(const cdmimo_params* p) { return p->form == CDMIMO_FORM_GRAM
 // tiling, with the kernel's layout: two channel buffers of C x 16 rows of 2 B_c + 8 floats, the
 // Gram rows (later w per tile), m_u and p_u^2, z / x per tile, s.  UNSUPPORTED unless the shape is
 // the kernel's (c64 storage by bulk copy, every B_c = 16 or every B_c = 32, 8 < U <= 16,
-// n_sym <= 16, 2 C n_sym <= 256, no learned block) and, for AUTO, the Gram form's own rules hold.
-// p->form must be AUTO or GRAM_TC.
-int build_tc_plan(const cdmimo_params* p, const void* H, CdPlan* pl)
+// n_sym <= 16, 2 C n_sym <= 256; a learned block only for op DETECT) and, for AUTO, the Gram form's
+// own rules hold.  p->form must be AUTO or GRAM_TC.
+int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
 {
     if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC) return CDMIMO_ERR_UNSUPPORTED;
-    if (p->in_dtype != CDMIMO_C64 || p->learned || p->fuse == CDMIMO_FUSE_LEARNED) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->in_dtype != CDMIMO_C64) return CDMIMO_ERR_UNSUPPORTED;
+    if (op != CDMIMO_OP_DETECT && (p->learned || p->fuse == CDMIMO_FUSE_LEARNED)) return CDMIMO_ERR_UNSUPPORTED;
     if (p->U <= 8 || p->U > 16 || p->n_sym > 16 || 2 * p->C * p->n_sym > 256) return CDMIMO_ERR_UNSUPPORTED;
-    if (int rc = build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, pl, true)) return rc;
+    if (int rc = build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, pl, op == CDMIMO_OP_FRAME)) return rc;
     const int Bc = p->cluster_size[0];
     if (!pl->bulk || (Bc != 16 && Bc != 32) || pl->A_uniform != Bc / 16) return CDMIMO_ERR_UNSUPPORTED;
     for (int c = 0; c < p->C; ++c)
@@ -326,6 +327,10 @@ int build_tc_plan(const cdmimo_params* p, const void* H, CdPlan* pl)
     pl->off_W = pl->off_G;
     pl->off_S = o;
     o = align16(o + n_sym * U * 8u);
+    if (pl->learned) {  // the learned fusion's hidden activations
+        pl->off_mlp = o;
+        o = align16(o + C * (unsigned)CDMIMO_MAX_HIDDEN * 4u);
+    }
     pl->off_lam = o;
     o = align16(o + C * 4u);
     pl->off_tab = o;
@@ -442,9 +447,9 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
         return p->in_dtype != CDMIMO_C64 ? CDMIMO_ERR_UNSUPPORTED : CDMIMO_ERR_INVALID_ARG;
     if (p->n_sc == 0) return CDMIMO_OK;
     CdPlan pl;
-    if (!Xc && !lam && build_tc_plan(p, H, &pl) == CDMIMO_OK) {
-        const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr, nullptr,
-                          sched},
+    if (!Xc && !lam && build_tc_plan(p, H, CDMIMO_OP_DETECT, &pl) == CDMIMO_OK) {
+        const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr,
+                          p->learned, sched},
                          nullptr, nullptr};
         return dispatch_frame_tc(pl, io, CDMIMO_OP_DETECT, s);
     }
@@ -471,7 +476,7 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
     const size_t ea = p->in_dtype == CDMIMO_C64 ? 8 : 4;
     if (!aligned(H, ea) || !aligned(S, 8) || !aligned(Xdl, 8)) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
-    if (build_tc_plan(p, H, &pl) == CDMIMO_OK) {
+    if (build_tc_plan(p, H, CDMIMO_OP_PRECODE, &pl) == CDMIMO_OK) {
         const FusedIO io{{H, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, sched},
                          reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
         return dispatch_frame_tc(pl, io, CDMIMO_OP_PRECODE, s);
@@ -881,7 +886,7 @@ int frame_impl(const cdmimo_params* p, const void* H, const void* Y, const float
     const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr, nullptr,
                       sched},
                      reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
-    if (build_tc_plan(p, H, &pl) == CDMIMO_OK) return dispatch_frame_tc(pl, io, CDMIMO_OP_FRAME, s);
+    if (build_tc_plan(p, H, CDMIMO_OP_FRAME, &pl) == CDMIMO_OK) return dispatch_frame_tc(pl, io, CDMIMO_OP_FRAME, s);
     if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
         build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)
         return dispatch_frame_gram(p->in_dtype, pl, io, s);
@@ -1027,7 +1032,7 @@ int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
     if (int rc = validate(p)) return rc;
     if (op != CDMIMO_OP_DETECT && op != CDMIMO_OP_PRECODE && op != CDMIMO_OP_FRAME) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
-    if (build_tc_plan(p, H, &pl) == CDMIMO_OK) return CDMIMO_FORM_GRAM_TC;
+    if (build_tc_plan(p, H, op, &pl) == CDMIMO_OK) return CDMIMO_FORM_GRAM_TC;
     if (op == CDMIMO_OP_FRAME) {
         if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
             build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)

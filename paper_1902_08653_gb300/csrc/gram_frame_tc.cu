@@ -1,5 +1,6 @@
 // Translation unit of the tensor-core Gram-form kernel (cd_frame_tc.cuh): instantiation for
-// clusters of 16 or 32 antennas and each mode (TDD frame, uplink alone, downlink alone), and dispatch.
+// clusters of 16 or 32 antennas and each mode (TDD frame, uplink alone, downlink alone, learned
+// uplink), and dispatch.
 #include "cd_frame_tc.cuh"
 #include "launch.h"
 
@@ -23,7 +24,7 @@ int dispatch_frame_tc(const CdPlan& pl, const FusedIO& io, int op, cudaStream_t 
 {
     switch (op) {
     case CDMIMO_OP_FRAME: return dispatch_mode<kTcFrame>(pl, io, s);
-    case CDMIMO_OP_DETECT: return dispatch_mode<kTcDetect>(pl, io, s);
+    case CDMIMO_OP_DETECT: return pl.learned ? dispatch_mode<kTcDetectLearned>(pl, io, s) : dispatch_mode<kTcDetect>(pl, io, s);
     case CDMIMO_OP_PRECODE: return dispatch_mode<kTcPrecode>(pl, io, s);
     }
     return CDMIMO_ERR_INVALID_ARG;

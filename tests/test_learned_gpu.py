@@ -135,7 +135,32 @@ def test_untrained_model_is_plain_cd_with_equal_fusion(dev):
     assert_vectors_close(Xl.cpu().numpy(), Xp.cpu().numpy(), 1e-5, "reduction")
 
 
-@pytest.mark.parametrize("form", ["gram", "residual"])
+@pytest.mark.parametrize("cs,U,K,n_sym,fuse,vs_gram", [([32] * 8, 16, 2, 14, "learned", True),
+                                                       ([32] * 8, 16, 3, 14, "colnorm", True),
+                                                       ([16] * 6, 10, 2, 9, "learned", False),
+                                                       ([32] * 4, 9, 4, 7, "equal", True)])
+def test_learned_tensor_core_form_matches_oracle(dev, cs, U, K, n_sym, fuse, vs_gram):
+    """Learned sweeps and fusion on the tensor-core kernel (z and G_c from split-TF32 MMAs): against
+    the FP64 oracle, and against the FP32 Gram-form learned kernel (same iterates, other rounding)."""
+    Hd = 32
+    m = random_master(90 + K + U, K, U, Hd)
+    model = learned.LearnedCD(K, U, Hd, master=torch.from_numpy(m), device=dev)
+    n_sc = 37
+    _, (H, Y, N0), (H64, Y64, N064) = _inputs(100 + U, n_sc, n_sym, sum(cs), U, dev)
+    assert cdmimo.selected_form(cdmimo.OP_DETECT, n_sc, n_sym, sum(cs), U, cs, K, H=H, form="gram_tc") == "gram_tc"
+    X = cdmimo.detect(H, Y, N0, cs, K, fuse=fuse, learned=model.block, form="gram_tc").cpu().numpy()
+    Xo, Xco, lamo = orc.learned_forward(H64, Y64, N064, cs, K, as_used(m, K, U, Hd), Hd, threads=8)
+    if fuse != "learned":  # learned per-cluster estimates, fused with the plain detector's weights
+        lamo = orc.detect(H64, Y64, N064, cs, 0, fuse=fuse, threads=8)[2]
+        Xo = np.einsum("fc,fcnu->fnu", lamo, Xco)
+    assert_vectors_close(X, Xo, 1e-4, f"learned Xhat (gram_tc, {fuse})")
+    if vs_gram:
+        Xg = cdmimo.detect(H, Y, N0, cs, K, fuse=fuse, learned=model.block, form="gram").cpu().numpy()
+        assert_vectors_close(X, Xg, 2e-5, f"learned gram_tc vs gram ({fuse})")
+    assert cdmimo.device_status(clear=True) == 0
+
+
+@pytest.mark.parametrize("form", ["gram", "residual", "gram_tc"])
 def test_learned_block_mismatch_is_flagged(dev, form):
     model = learned.LearnedCD(2, 16, 64, device=dev)
     _, (H, Y, N0), _ = _inputs(6, 3, 2, 256, 16, dev)
