@@ -24,8 +24,9 @@
 // floats: with that stride the 64-bit fragment loads of both phases (rows gid x entries tig, and
 // users tig x antennas gid) fall on distinct banks.  The rows land in that layout by one bulk copy
 // per row, double-buffered one subcarrier ahead as in the SIMT kernel; no permutation pass follows.
-// The downlink's w per tile takes the place of the Gram rows once the sweeps are over (a barrier
-// separates the two), which keeps two CTAs per SM.  Per-tile rows (z, x, w) have a stride of
+// In the frame, the downlink's w per tile takes the place of the Gram rows once the sweeps are over
+// (a barrier separates the two), which keeps two CTAs per SM; the downlink alone keeps w where the
+// uplink's z and x would be.  Per-tile rows (z, x, w) have a stride of
 // 4 mod 16 entries, so that phase C's loads of w (users tig x symbols gid) are conflict-free too.
 #pragma once
 #include "cd_frame.cuh"
@@ -192,7 +193,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
 
     extern __shared__ __align__(128) unsigned char smem[];
     float4* Gs = reinterpret_cast<float4*>(smem + pl.off_G);  // [C][UT][UT/2] pair-planar rows, zero diagonal
-    float2* Ws = reinterpret_cast<float2*>(smem + pl.off_G);  // [U][x_stride] w per tile, after the sweeps
+    // [U][x_stride] w per tile: over the Gram rows after the sweeps (frame), or where z / x would be
+    // (downlink alone: stored as soon as a lane's sweeps end)
+    float2* Ws = reinterpret_cast<float2*>(smem + (MODE == kTcPrecode ? pl.off_X : pl.off_G));
     float* Dm = reinterpret_cast<float*>(smem + pl.off_E);    // [C][UT] m_u
     float* Dp = reinterpret_cast<float*>(smem + pl.off_E2);   // [C][UT] p_u^2 (learned: ||h_u||^2)
     float2* Zs = reinterpret_cast<float2*>(smem + pl.off_X);  // [UT][x_stride]: z, then each tile's x
@@ -367,6 +370,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                 gram_sweeps_learned<UT>(U, learned_ok ? pl.K : 0, Gc, Dp + gb.c * UT, alpha, blk, Zs + tile, xs, x);
             else
                 gram_sweeps<UT>(U, pl.K, Gc, Dp + gb.c * UT, Ss + n_b, (uint32_t)n_sym, xw);
+            if constexpr (MODE == kTcPrecode) {
+#pragma unroll
+                for (int u = 0; u < UT; ++u)
+                    if (u < U) Ws[tile + u * xs] = slice_entry<UT, 1>(xw, u);
+            }
             if constexpr (UL) {
 #pragma unroll
                 for (int u = 0; u < UT; ++u)
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
             if (nf < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[b ^ 1]);
         }
         __syncthreads();
-        if constexpr (DL) {
+        if constexpr (MODE == kTcFrame) {
             if (gb.active) {
 #pragma unroll
                 for (int u = 0; u < UT; ++u)
