@@ -17,7 +17,7 @@ import oracle as orc
 from paper_1902_08653_gb300 import cdmimo
 from paper_1902_08653_gb300 import workload as wl
 
-from _util import assert_vectors_close
+from _util import assert_decisions_match, assert_vectors_close
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -75,6 +75,7 @@ def test_frame_tc_matches_oracle(dev, name):
     X, P, Xg, Pg, Xo, Po = run_case(dev, n_sc, n_sym, cs, U, K, fuse, snr, zlib.crc32(name.encode()) % 1000)
     assert_vectors_close(X, Xo, TOL, "tc frame Xhat")
     assert_vectors_close(P, Po, TOL, "tc frame Xdl")
+    assert_decisions_match(X, Xo, 16)
     if vs_gram:
         assert_vectors_close(X, Xg, 2e-5, "tc vs fp32 gram frame Xhat")
         assert_vectors_close(P, Pg, 2e-5, "tc vs fp32 gram frame Xdl")
@@ -178,4 +179,28 @@ def test_detect_tc_with_per_cluster_outputs_uses_fp32_gram(dev):
     b = cdmimo.detect(Ht, Yt, Nt, cs, 3, Xc=Xc_b, lam=lam_b, form="gram")
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(Xc_a, Xc_b) and torch.equal(lam_a, lam_b)
+    assert cdmimo.device_status(clear=True) == 0
+
+
+def test_tc_bad_noise_variance_and_K0(dev):
+    """A negative N0 sets CDMIMO_DEV_BAD_N0 and gives NaN for that subcarrier's uplink estimate only
+    (the downlink does not use N0); K = 0 gives zero outputs in every mode."""
+    cs, U, n_sc = [32] * 8, 16, 5
+    d = wl.uplink(515, n_sc, 14, 256, U, snr_db=15.0)
+    Ht, Yt, St = t(wl.as_c64(d["H"])[0], dev), t(wl.as_c64(d["Y"])[0], dev), t(wl.as_c64(d["X"])[0], dev)
+    N0 = d["N0"].astype(np.float32)
+    N0[2] = -1.0
+    Nt = t(N0, dev)
+    cdmimo.device_status(clear=True)
+    X = cdmimo.detect(Ht, Yt, Nt, cs, 3, form="gram_tc").cpu().numpy()
+    assert cdmimo.device_status(clear=True) & cdmimo.DEV_BAD_N0
+    assert np.all(np.isnan(X[2])) and np.all(np.isfinite(X[[0, 1, 3, 4]]))
+    Xf, Pf = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, 3, form="gram_tc")
+    assert cdmimo.device_status(clear=True) & cdmimo.DEV_BAD_N0
+    Xf, Pf = Xf.cpu().numpy(), Pf.cpu().numpy()
+    assert np.all(np.isnan(Xf[2])) and np.all(np.isfinite(Xf[[0, 1, 3, 4]])) and np.all(np.isfinite(Pf))
+    N0[2] = 0.1
+    Nt = t(N0, dev)
+    assert not cdmimo.detect(Ht, Yt, Nt, cs, 0, form="gram_tc").abs().any()
+    assert not cdmimo.precode(Ht, St, cs, 0, form="gram_tc").abs().any()
     assert cdmimo.device_status(clear=True) == 0
