@@ -94,6 +94,94 @@ __device__ __forceinline__ void b_frags(float2 v, BFrag& plain, BFrag& rot)
     rot.l[1] = neg_bits(plain.l[0]);
 }
 
+// The learned sweeps of gram_sweeps_learned, x_u <- a_{t,u} (b_u - sum_{v != u} Gt_uv x_v) +
+// keep_{t,u} x_u, with (a, keep)_{t,u} = (tau_t / (e_u + gamma_t alpha), 1 - tau_t) (or (0, 1) for a
+// non-positive denominator) read from the cluster's table co[t][UT] instead of formed at every step.
+template <int UT>
+__device__ __forceinline__ void gram_sweeps_learned_tab(int U, int K, const float4* Grow, const float2* co,
+                                                        const float2* b, uint32_t bs, float4 (&x)[UT / 2])
+{
+#pragma unroll
+    for (int i = 0; i < UT / 2; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto step = [&](int u, int npu, const float2* ct) {
+        const float2 dot = gram_row_dot<UT>(Grow, u, npu, x);
+        const float2 bu = b[u * bs];
+        const float2 ak = ct[u];
+        float4& xp = x[u >> 1];
+        const float2 xo = (u & 1) ? make_float2(xp.y, xp.w) : make_float2(xp.x, xp.z);
+        set_entry(xp, u, fmaf(ak.x, bu.x - dot.x, ak.y * xo.x), fmaf(ak.x, bu.y - dot.y, ak.y * xo.y));
+    };
+    if (K < 1) return;
+#pragma unroll
+    for (int u = 0; u < UT; ++u)  // first sweep from x = 0: pairs holding some x_v, v < u
+        if (u < U) step(u, (u + 1) / 2, co);
+#pragma unroll 1
+    for (int t = 1; t < K; ++t) {
+#pragma unroll
+        for (int u = 0; u < UT; ++u)
+            if (u < U) step(u, UT / 2, co + t * UT);
+    }
+}
+
+// Learned fusion weights of one subcarrier (the same function as learned_lambda): lambda =
+// softmax_c(logit_c), logit_c = b2 + sum_k w2[k] relu(W1[k] . phi_c + b1[k]) with phi_c =
+// [||h_{u,c}||^2 / B_c (u < U), log10(max(alpha, 1e-6))], computed by the nw warps starting at warp
+// w0 (all of the CTA's, or four that have no sweep lanes).  Warp w0 + i takes clusters i, i + nw, ...;
+// each lane computes hidden units lane and lane + 32 with the features in registers, and the logit
+// is a warp reduction.  lam[c] is written by warp w0 after one barrier among the nw warps (the CTA
+// barrier, or named barrier 1); the caller puts a barrier before reading it.  logit: [C] floats of
+// shared scratch.
+template <int UT>
+__device__ __forceinline__ void tc_learned_lambda(const CdPlan& pl, const cdmimo_learned* blk, bool learned_ok,
+                                                  float alpha, const ClusterTile* tab, const float* energy,
+                                                  float* logit, float* lam, int w0, int nw)
+{
+    const int lane = threadIdx.x & 31, warp = (int)(threadIdx.x >> 5) - w0, C = pl.C, U = pl.U;
+    const int Hd = learned_ok ? __ldg(&blk->hidden) : 1;
+    const int F = U + 1;
+    const float la = log10f(fmaxf(alpha, 1e-6f));
+    for (int c = warp; c < C; c += nw) {
+        const float inv_bc = 1.f / (float)tab[c].size;
+        float phi[UT];
+#pragma unroll
+        for (int j = 0; j < UT; ++j) phi[j] = j < U ? energy[c * UT + j] * inv_bc : 0.f;
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k = lane + 32 * q;
+            if (k < Hd) {
+                const unsigned short* w1 = blk->W1 + (size_t)k * F;
+                float z = __ldg(&blk->b1[k]);
+#pragma unroll
+                for (int j = 0; j < UT; ++j)
+                    if (j < U) z = fmaf(bf16_bits_to_float(__ldg(w1 + j)), phi[j], z);
+                z = fmaf(bf16_bits_to_float(__ldg(w1 + U)), la, z);
+                part = fmaf(bf16_bits_to_float(__ldg(&blk->w2[k])), fmaxf(z, 0.f), part);
+            }
+        }
+        part = warp_sum(part);
+        if (lane == 0) logit[c] = __ldg(&blk->b2) + part;
+    }
+    if (nw * 32 == (int)blockDim.x) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+    if (warp == 0) {
+        float lg[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (lane + 32 * q < C) lg[q] = logit[lane + 32 * q];
+        float mx = fmaxf(lg[0], lg[1]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float ex[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) ex[q] = lane + 32 * q < C ? __expf(lg[q] - mx) : 0.f;
+        const float tot = warp_sum(ex[0] + ex[1]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (lane + 32 * q < C) lam[lane + 32 * q] = ex[q] / tot;
+    }
+}
+
 // Bulk copies of subcarrier f's channel rows into the padded per-cluster layout (row (c, u) at
 // floats (c UT + u) srow); thread i issues row i.
 __device__ __forceinline__ void issue_channel_copy_tc(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
@@ -207,7 +295,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     auto Hbuf = [&](int j) { return reinterpret_cast<float*>(smem + (j ? pl.off_H2 : 0u)); };
     const DetectIO& d = io.d;
     const cdmimo_learned* blk = reinterpret_cast<const cdmimo_learned*>(d.learned);
-    float* mlp = reinterpret_cast<float*>(smem + pl.off_mlp);  // [C][hidden] (learned fusion)
+    float* mlp = reinterpret_cast<float*>(smem + pl.off_mlp);  // [C] logits (learned fusion)
+    float2* LA = reinterpret_cast<float2*>(smem + pl.off_K);   // [C][K][UT] learned (a, keep) per sweep
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
     const int U = pl.U, C = pl.C, n_sym = pl.n_sym, n_s = n_sym * U;
@@ -330,8 +419,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     if (v == u || v + 1 == u) {
                         const float e = v == u ? g0 : g1, den = e + alpha;
                         Dm[c * UT + u] = (u < U && den > 0.f) ? __fdividef(1.f, den) : 0.f;
-                        if constexpr (LEARNED) Dp[c * UT + u] = e;
-                        else Dp[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
+                        if constexpr (LEARNED) {
+                            Dp[c * UT + u] = e;
+                            for (int t = 0; t < pl.K; ++t) {  // learned coefficients of every sweep
+                                const float tau = __ldg(&blk->tau[t]), dl = e + __ldg(&blk->gamma[t]) * alpha;
+                                LA[(c * pl.K + t) * UT + u] = dl > 0.f ? make_float2(tau * __fdividef(1.f, dl), 1.f - tau)
+                                                                      : make_float2(0.f, 1.f);
+                            }
+                        } else {
+                            Dp[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
+                        }
                         if (v == u) g0 = i0 = 0.f;
                         else g1 = i1 = 0.f;
                     }
@@ -359,6 +456,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         const unsigned ticket = (d.sched && tid == 0) ? atomicAdd(d.sched, 1u) : 0u;
         float4 x[UT / 2], xw[UT / 2];
         const int n_b = gb.j, tile = gb.c * n_sym + n_b;
+        // Learned fusion: its weights need only ||h_u||^2 and N0, so where the sweep lanes leave warps
+        // 4-7 free those warps compute them now, during the sweeps.
+        const bool mlp_now = LEARNED && pl.fuse == CDMIMO_FUSE_LEARNED && frame_warps(C * n_sym) <= 4;
+        if (mlp_now && warp >= 4) tc_learned_lambda<UT>(pl, blk, learned_ok, alpha, tab, Dp, mlp, lam, 4, 4);
         if (gb.active) {
             const float4* Gc = Gs + (size_t)gb.c * UT * (UT / 2);
             const float* dd = Dm + gb.c * UT;
@@ -367,7 +468,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
             else if constexpr (MODE == kTcDetect)
                 gram_sweeps<UT>(U, pl.K, Gc, dd, Zs + tile, xs, x);
             else if constexpr (LEARNED)
-                gram_sweeps_learned<UT>(U, learned_ok ? pl.K : 0, Gc, Dp + gb.c * UT, alpha, blk, Zs + tile, xs, x);
+                gram_sweeps_learned_tab<UT>(U, learned_ok ? pl.K : 0, Gc, LA + gb.c * pl.K * UT, Zs + tile, xs, x);
             else
                 gram_sweeps<UT>(U, pl.K, Gc, Dp + gb.c * UT, Ss + n_b, (uint32_t)n_sym, xw);
             if constexpr (MODE == kTcPrecode) {
@@ -379,7 +480,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
 #pragma unroll
                 for (int u = 0; u < UT; ++u)
                     if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
-                if (n_b == 0) {
+                if (n_b == 0 && !(LEARNED && pl.fuse == CDMIMO_FUSE_LEARNED)) {
                     float msum = 0.f;
                     for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
                     lam[gb.c] = 1.f / msum;
@@ -484,9 +585,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         }
         if constexpr (LEARNED) {
             if (pl.fuse == CDMIMO_FUSE_LEARNED) {  // lambda = softmax of the MLP on ||h_u||^2 / B_c and log10 alpha
-                learned_lambda(pl, blk, learned_ok, alpha, tab, mlp, lam, nullptr, f,
-                               [&](int cc, int j) { return Dp[cc * UT + j]; });
-                __syncthreads();
+                if (!mlp_now) {
+                    tc_learned_lambda<UT>(pl, blk, learned_ok, alpha, tab, Dp, mlp, lam, 0, kTcThreads / 32);
+                    __syncthreads();
+                }
                 fuse_subcarrier<true>(pl, d, f, lam, Zs, xs, out_scale);
             } else {
                 fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);

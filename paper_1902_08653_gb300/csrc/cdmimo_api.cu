@@ -291,6 +291,10 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
     return CDMIMO_OK;
 }
 
+// Shared memory per CTA that still lets two CTAs of the tensor-core kernel share an SM (228 KB per
+// SM, 1 KB reserved per CTA).
+constexpr unsigned kTcTwoCtaSmem = (228u * 1024u - 2u * 1024u) / 2u;
+
 // GRAM and GRAM_TC ask for the Gram form (UNSUPPORTED where it does not apply).
 bool is_forced_gram(const cdmimo_params* p) { return p->form == CDMIMO_FORM_GRAM || p->form == CDMIMO_FORM_GRAM_TC; }
 
@@ -327,9 +331,11 @@ int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
     pl->off_W = pl->off_G;
     pl->off_S = o;
     o = align16(o + n_sym * U * 8u);
-    if (pl->learned) {  // the learned fusion's hidden activations
+    if (pl->learned) {  // the learned fusion's logits, and the learned sweep coefficients [C][K][16]
         pl->off_mlp = o;
-        o = align16(o + C * (unsigned)CDMIMO_MAX_HIDDEN * 4u);
+        o = align16(o + C * 4u);
+        pl->off_K = o;
+        o = align16(o + C * (unsigned)p->K * UT * 8u);
     }
     pl->off_lam = o;
     o = align16(o + C * 4u);
@@ -339,6 +345,7 @@ int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
     o = align16(o + 32u);
     pl->smem_bytes = o;
     if ((int)pl->smem_bytes > device_smem_optin()) return CDMIMO_ERR_UNSUPPORTED;
+    if (pl->learned && pl->smem_bytes > kTcTwoCtaSmem) return CDMIMO_ERR_UNSUPPORTED;  // long learned schedules
     pl->threads = 256;
     pl->UT = 16;
     return CDMIMO_OK;
