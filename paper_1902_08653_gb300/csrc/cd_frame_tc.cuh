@@ -1,10 +1,11 @@
-// TDD frame kernel with the contractions on the tensor cores: uplink detection (Algorithm 1 +
-// fusion, Sec. III) and downlink precoding (Algorithm 2 + normalization, Sec. IV-B) on one channel
-// per subcarrier, in Gram form (see cd_gram.cuh), like cd_frame_gram_kernel, but with
+// Gram-form CD kernel with the contractions on the tensor cores, for the TDD frame (uplink detection,
+// Algorithm 1 + fusion of Sec. III, and downlink precoding, Algorithm 2 + normalization of
+// Sec. IV-B, on one channel per subcarrier, like cd_frame_gram_kernel), for either direction alone,
+// and for the learned uplink.  In Gram form (see cd_gram.cuh),
 //   z = H_c^H y_c,  G_c = H_c^H H_c  (phase A)   and   x_c = H_c w  (phase C)
-// computed by warp-level tensor-core MMAs (mma.sync m16n8k8, TF32 operands, FP32 accumulation),
+// are computed by warp-level tensor-core MMAs (mma.sync m16n8k8, TF32 operands, FP32 accumulation),
 // one warp per cluster.  The sweeps (phase B) are FP32 Gauss-Seidel steps, one lane per (cluster,
-// symbol) running the uplink and the downlink vector side by side.
+// symbol); in the frame that lane runs the uplink and the downlink vector side by side.
 //
 // FP32 accuracy from TF32 operands.  Every FP32 operand x is split as x = hi + lo, hi = x with its
 // 13 low mantissa bits cleared (a TF32 value) and lo = x - hi (exact in FP32, |lo| < 2^-10 |x|); the
@@ -26,8 +27,8 @@
 // per row, double-buffered one subcarrier ahead as in the SIMT kernel; no permutation pass follows.
 // In the frame, the downlink's w per tile takes the place of the Gram rows once the sweeps are over
 // (a barrier separates the two), which keeps two CTAs per SM; the downlink alone keeps w where the
-// uplink's z and x would be.  Per-tile rows (z, x, w) have a stride of
-// 4 mod 16 entries, so that phase C's loads of w (users tig x symbols gid) are conflict-free too.
+// uplink's z and x would be.  Per-tile rows (z, x, w) have a stride of 4 mod 16 entries, so that
+// phase C's loads of w (users tig x symbols gid) are conflict-free too.
 #pragma once
 #include "cd_frame.cuh"
 
