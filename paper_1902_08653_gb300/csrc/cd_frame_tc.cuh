@@ -183,17 +183,43 @@ __device__ __forceinline__ void tc_learned_lambda(const CdPlan& pl, const cdmimo
     }
 }
 
+// 16-bit storage: an fp16 or bf16 value converted to FP32 has at most 11 significant bits, so its
+// FP32 bits are an exact TF32 operand (no split).  A fragment from two such complex entries, and the
+// plain and rotated B fragments of one.
+__device__ __forceinline__ void a_frag_exact(float2 e0, float2 e1, uint32_t (&a)[4])
+{
+    a[0] = __float_as_uint(e0.x);
+    a[1] = __float_as_uint(e1.x);
+    a[2] = __float_as_uint(e0.y);
+    a[3] = __float_as_uint(e1.y);
+}
+
+__device__ __forceinline__ void mma_exact(float (&d)[4], const uint32_t (&a)[4], float2 v, bool rot)
+{
+    if (rot) mma_tf32(d, a, __float_as_uint(v.y), __float_as_uint(-v.x));
+    else mma_tf32(d, a, __float_as_uint(v.x), __float_as_uint(v.y));
+}
+
+// d += A B with A exact and B split: two passes.
+__device__ __forceinline__ void mma_2xtf32(float (&d)[4], const uint32_t (&a)[4], const BFrag& b)
+{
+    mma_tf32(d, a, b.l[0], b.l[1]);
+    mma_tf32(d, a, b.h[0], b.h[1]);
+}
+
 // Bulk copies of subcarrier f's channel rows into the padded per-cluster layout (row (c, u) at
-// floats (c UT + u) srow); thread i issues row i.
+// 32-bit words (c UT + u) srow); thread i issues row i.  Complex entries of 8 (c64) or 4 bytes.
+template <int IN>
 __device__ __forceinline__ void issue_channel_copy_tc(const CdPlan& pl, const ClusterTile* tab, const void* H, int f,
                                                       float* dst, int srow, uint64_t* bar)
 {
-    const char* Hf = reinterpret_cast<const char*>(H) + (size_t)f * pl.U * pl.B * 8u;
+    constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
+    const char* Hf = reinterpret_cast<const char*>(H) + (size_t)f * pl.U * pl.B * eb;
     for (int row = threadIdx.x; row < pl.U * pl.C; row += blockDim.x) {
         const int c = row / pl.U, u = row - c * pl.U;
         const ClusterTile ct = tab[c];
         fence_proxy_async_smem();
-        bulk_g2s(dst + (size_t)(c * kTcUT + u) * srow, Hf + ((size_t)u * pl.B + ct.off) * 8u, (uint32_t)ct.size * 8u,
+        bulk_g2s(dst + (size_t)(c * kTcUT + u) * srow, Hf + ((size_t)u * pl.B + ct.off) * eb, (uint32_t)ct.size * eb,
                  bar);
     }
 }
@@ -267,13 +293,13 @@ __device__ __forceinline__ void gram_sweeps2(int U, int K, const float4* Grow, c
     }
 }
 
-template <int BC, int MODE>
+template <int BC, int MODE, int IN>
 __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan pl, const FusedIO io)
 {
     constexpr bool UL = MODE != kTcPrecode, DL = MODE == kTcFrame || MODE == kTcPrecode;
     constexpr bool LEARNED = MODE == kTcDetectLearned;
     constexpr int UT = kTcUT;
-    constexpr int SROW = (int)tc_row_floats(BC);  // floats per channel row
+    constexpr int SROW = (int)tc_row_words(BC, IN);  // 32-bit words per channel row
     constexpr int SR2 = SROW / 2;     // the same in complex entries
     constexpr int KA = BC / 4;        // phase A k-steps (4 antennas each)
     constexpr int MT = BC / 16;       // phase C m-tiles (16 antennas each)
@@ -330,9 +356,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     const GLane gb = frame_lane(0, C, n_sym, 1);
 
     int f = blockIdx.x;
-    if (tid == 0 && f < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[0]);
+    if (tid == 0 && f < pl.n_sc) arm_channel_copy<IN>(pl, &bar[0]);
     __syncthreads();
-    if (f < pl.n_sc) issue_channel_copy_tc(pl, tab, d.H, f, Hbuf(0), SROW, &bar[0]);
+    if (f < pl.n_sc) issue_channel_copy_tc<IN>(pl, tab, d.H, f, Hbuf(0), SROW, &bar[0]);
     auto put_s = [&](int i, float2 v) { Ss[(i % U) * n_sym + i / U] = v; };
     if (DL && f < pl.n_sc)
         for (int i = tid; i < n_s; i += blockDim.x) put_s(i, io.S[(size_t)f * n_s + i]);
@@ -349,6 +375,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                 alpha = 0.f;
             }
             if (LEARNED && !learned_ok) out_scale = __int_as_float(0x7fc00000);
+            if constexpr (IN != CDMIMO_C64) {  // stored H / a_f, y / b_f: solve with alpha / a_f^2, scale x by b_f / a_f
+                const float hs = __ldg(d.h_scale + f), ys = __ldg(d.y_scale + f);
+                alpha = alpha / (hs * hs);
+                out_scale = out_scale * (ys / hs);
+            }
         }
         const uint32_t parity = (uint32_t)(k >> 1) & 1u;
         const bool ok = mbar_wait_bounded(&bar[b], parity);
@@ -380,31 +411,59 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     dst[j] = n < n_sym ? __ldg(Yc + (size_t)n * pl.B + 4 * ks + tig) : make_float2(0.f, 0.f);
                 }
             };
-            if constexpr (UL) {
-                load_y(0, yv[0]);
-                if (KA > 1) load_y(1, yv[1]);
-            }
-#pragma unroll
-            for (int ks = 0; ks < KA; ++ks) {
-                const int e = 4 * ks + tig;  // the lane's complex entry of this k-step
-                uint32_t ah[4], al[4];
-                a_frag(Hc2[gid * SR2 + e], Hc2[(gid + 8) * SR2 + e], ah, al);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    BFrag bp, br;
-                    b_frags(Hc2[(8 * j + gid) * SR2 + e], bp, br);
-                    mma_3xtf32(accG[j], ah, al, bp);
-                    mma_3xtf32(accG[2 + j], ah, al, br);
-                }
+            if constexpr (IN == CDMIMO_C64) {
                 if constexpr (UL) {
-#pragma unroll
+                    load_y(0, yv[0]);
+                    if (KA > 1) load_y(1, yv[1]);
+                }
+    #pragma unroll
+                for (int ks = 0; ks < KA; ++ks) {
+                    const int e = 4 * ks + tig;  // the lane's complex entry of this k-step
+                    uint32_t ah[4], al[4];
+                    a_frag(Hc2[gid * SR2 + e], Hc2[(gid + 8) * SR2 + e], ah, al);
+    #pragma unroll
                     for (int j = 0; j < 2; ++j) {
                         BFrag bp, br;
-                        b_frags(yv[ks & 1][j], bp, br);
-                        mma_3xtf32(accZ[j], ah, al, bp);
-                        mma_3xtf32(accZ[2 + j], ah, al, br);
+                        b_frags(Hc2[(8 * j + gid) * SR2 + e], bp, br);
+                        mma_3xtf32(accG[j], ah, al, bp);
+                        mma_3xtf32(accG[2 + j], ah, al, br);
                     }
-                    if (ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
+                    if constexpr (UL) {
+    #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            BFrag bp, br;
+                            b_frags(yv[ks & 1][j], bp, br);
+                            mma_3xtf32(accZ[j], ah, al, bp);
+                            mma_3xtf32(accZ[2 + j], ah, al, br);
+                        }
+                        if (ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
+                    }
+                }
+            } else {  // 16-bit storage: every operand exact in TF32, one MMA per tile
+                const void* Hw = Hb + c * UT * SROW;
+                auto hget = [&](int row, int e) { return Elem<IN>::load_shared(Hw, (size_t)row * SROW + e); };
+                const size_t ybase = (size_t)f * n_sym * pl.B + ct.off;
+#pragma unroll
+                for (int ks = 0; ks < KA; ++ks) {
+                    const int e = 4 * ks + tig;
+                    uint32_t ah[4];
+                    a_frag_exact(hget(gid, e), hget(gid + 8, e), ah);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float2 hv = hget(8 * j + gid, e);
+                        mma_exact(accG[j], ah, hv, false);
+                        mma_exact(accG[2 + j], ah, hv, true);
+                    }
+                    if constexpr (UL) {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int n = 8 * j + gid;
+                            const float2 yy = n < n_sym ? Elem<IN>::load(d.Y, ybase + (size_t)n * pl.B + e)
+                                                        : make_float2(0.f, 0.f);
+                            mma_exact(accZ[j], ah, yy, false);
+                            mma_exact(accZ[2 + j], ah, yy, true);
+                        }
+                    }
                 }
             }
             // G rows (pair-planar, zero diagonal) with m_u and p_u^2 from the diagonal; rows u = gid,
@@ -495,7 +554,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                 nf = v < (unsigned)pl.n_sc ? (int)v : pl.n_sc;
             }
             nxt[b] = nf;
-            if (nf < pl.n_sc) arm_channel_copy<CDMIMO_C64>(pl, &bar[b ^ 1]);
+            if (nf < pl.n_sc) arm_channel_copy<IN>(pl, &bar[b ^ 1]);
         }
         __syncthreads();
         if constexpr (MODE == kTcFrame) {
@@ -512,9 +571,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         // Downlink, per cluster (one warp): x_c = H_c w for all symbols (MT x 4 tiles), normalized
         // per symbol.  Then the uplink fusion.
         const int fn = nxt[b];
-        if (fn < pl.n_sc) issue_channel_copy_tc(pl, tab, d.H, fn, Hbuf(b ^ 1), SROW, &bar[b ^ 1]);
-        if (UL && tid == 32 && fn < pl.n_sc)
-            bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * 8u, (uint32_t)n_sym * pl.B * 8u);
+        if (fn < pl.n_sc) issue_channel_copy_tc<IN>(pl, tab, d.H, fn, Hbuf(b ^ 1), SROW, &bar[b ^ 1]);
+        if (UL && tid == 32 && fn < pl.n_sc) {
+            constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;
+            bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)fn * n_sym * pl.B * eb, (uint32_t)n_sym * pl.B * eb);
+        }
         constexpr int kSv = 2;
         const bool ld_s = DL && fn < pl.n_sc;
         const float2* s_src = DL ? io.S + (size_t)min(fn, pl.n_sc - 1) * n_s : nullptr;
@@ -533,24 +594,50 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                 for (int t = 0; t < 4; ++t)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[m][t][q] = 0.f;
-#pragma unroll
-            for (int ks = 0; ks < KC; ++ks) {
-                const int u = 4 * ks + tig;  // the lane's user of this k-step
-                BFrag br[2], bi[2];         // per n-tile: (Re w, -Im w) and (Im w, Re w)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int n = 8 * j + gid;
-                    const float2 w = (u < U && n < n_sym) ? Ws[u * xs + c * n_sym + n] : make_float2(0.f, 0.f);
-                    b_frags(make_float2(w.y, w.x), bi[j], br[j]);  // rot(Im w, Re w) = (Re w, -Im w)
+            if constexpr (IN == CDMIMO_C64) {
+    #pragma unroll
+                for (int ks = 0; ks < KC; ++ks) {
+                    const int u = 4 * ks + tig;  // the lane's user of this k-step
+                    BFrag br[2], bi[2];         // per n-tile: (Re w, -Im w) and (Im w, Re w)
+    #pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int n = 8 * j + gid;
+                        const float2 w = (u < U && n < n_sym) ? Ws[u * xs + c * n_sym + n] : make_float2(0.f, 0.f);
+                        b_frags(make_float2(w.y, w.x), bi[j], br[j]);  // rot(Im w, Re w) = (Re w, -Im w)
+                    }
+    #pragma unroll
+                    for (int m = 0; m < MT; ++m) {
+                        uint32_t ah[4], al[4];
+                        a_frag(Hc2[u * SR2 + 16 * m + gid], Hc2[u * SR2 + 16 * m + gid + 8], ah, al);
+    #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            mma_3xtf32(acc[m][j], ah, al, br[j]);
+                            mma_3xtf32(acc[m][2 + j], ah, al, bi[j]);
+                        }
+                    }
                 }
+            } else {  // 16-bit storage: H exact in TF32, w split: two MMAs per tile
+                const void* Hw = Hb + c * UT * SROW;
 #pragma unroll
-                for (int m = 0; m < MT; ++m) {
-                    uint32_t ah[4], al[4];
-                    a_frag(Hc2[u * SR2 + 16 * m + gid], Hc2[u * SR2 + 16 * m + gid + 8], ah, al);
+                for (int ks = 0; ks < KC; ++ks) {
+                    const int u = 4 * ks + tig;
+                    BFrag br[2], bi[2];
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        mma_3xtf32(acc[m][j], ah, al, br[j]);
-                        mma_3xtf32(acc[m][2 + j], ah, al, bi[j]);
+                        const int n = 8 * j + gid;
+                        const float2 w = (u < U && n < n_sym) ? Ws[u * xs + c * n_sym + n] : make_float2(0.f, 0.f);
+                        b_frags(make_float2(w.y, w.x), bi[j], br[j]);
+                    }
+#pragma unroll
+                    for (int m = 0; m < MT; ++m) {
+                        uint32_t ah[4];
+                        a_frag_exact(Elem<IN>::load_shared(Hw, (size_t)u * SROW + 16 * m + gid),
+                                     Elem<IN>::load_shared(Hw, (size_t)u * SROW + 16 * m + gid + 8), ah);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            mma_2xtf32(acc[m][j], ah, br[j]);
+                            mma_2xtf32(acc[m][2 + j], ah, bi[j]);
+                        }
                     }
                 }
             }

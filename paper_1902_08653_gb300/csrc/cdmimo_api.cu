@@ -301,13 +301,13 @@ bool is_forced_gram(const cdmimo_params* p) { return p->form == CDMIMO_FORM_GRAM
 // Tensor-core plan (any mode of cd_frame_tc_kernel): the Gram frame plan's cluster table and
 // tiling, with the kernel's layout: two channel buffers of C x 16 rows of 2 B_c + 8 floats, the
 // Gram rows (later w per tile), m_u and p_u^2, z / x per tile, s.  UNSUPPORTED unless the shape is
-// the kernel's (c64 storage by bulk copy, every B_c = 16 or every B_c = 32, 8 < U <= 16,
-// n_sym <= 16, 2 C n_sym <= 256; a learned block only for op DETECT) and, for AUTO, the Gram form's
-// own rules hold.  p->form must be AUTO or GRAM_TC.
+// the kernel's (c64 or 16-bit storage by bulk copy, every B_c = 16 or every B_c = 32, 8 < U <= 16,
+// n_sym <= 16, 2 C n_sym <= 256; a learned block only for op DETECT with c64) and, for AUTO, the Gram
+// form's own rules hold.  p->form must be AUTO or GRAM_TC.
 int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
 {
     if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC) return CDMIMO_ERR_UNSUPPORTED;
-    if (p->in_dtype != CDMIMO_C64) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->in_dtype != CDMIMO_C64 && p->learned) return CDMIMO_ERR_UNSUPPORTED;
     if (op != CDMIMO_OP_DETECT && (p->learned || p->fuse == CDMIMO_FUSE_LEARNED)) return CDMIMO_ERR_UNSUPPORTED;
     if (p->U <= 8 || p->U > 16 || p->n_sym > 16 || 2 * p->C * p->n_sym > 256) return CDMIMO_ERR_UNSUPPORTED;
     if (int rc = build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, pl, op == CDMIMO_OP_FRAME)) return rc;
@@ -316,7 +316,7 @@ int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
     for (int c = 0; c < p->C; ++c)
         if (p->cluster_size[c] != Bc) return CDMIMO_ERR_UNSUPPORTED;
     const unsigned C = p->C, U = p->U, UT = 16, xs = tc_x_stride(pl->n_tiles), n_sym = p->n_sym;
-    const unsigned hbytes = align16(C * UT * tc_row_floats(Bc) * 4u);
+    const unsigned hbytes = align16(C * UT * tc_row_words(Bc, p->in_dtype) * 4u);
     unsigned o = 2u * hbytes;
     pl->off_H2 = hbytes;
     pl->off_H3 = 0u;
@@ -458,7 +458,7 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
         const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr,
                           p->learned, sched},
                          nullptr, nullptr};
-        return dispatch_frame_tc(pl, io, CDMIMO_OP_DETECT, s);
+        return dispatch_frame_tc(p->in_dtype, pl, io, CDMIMO_OP_DETECT, s);
     }
     if (int rc = plan_for(p, true, H, &pl)) {
         if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam || is_forced_gram(p)) return rc;
@@ -486,7 +486,7 @@ int precode_impl(const cdmimo_params* p, const void* H, const void* S, void* Xdl
     if (build_tc_plan(p, H, CDMIMO_OP_PRECODE, &pl) == CDMIMO_OK) {
         const FusedIO io{{H, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, sched},
                          reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
-        return dispatch_frame_tc(pl, io, CDMIMO_OP_PRECODE, s);
+        return dispatch_frame_tc(p->in_dtype, pl, io, CDMIMO_OP_PRECODE, s);
     }
     if (int rc = plan_for(p, false, H, &pl)) {
         if (rc != CDMIMO_ERR_UNSUPPORTED || is_forced_gram(p)) return rc;
@@ -893,7 +893,7 @@ int frame_impl(const cdmimo_params* p, const void* H, const void* Y, const float
     const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr, nullptr,
                       sched},
                      reinterpret_cast<const float2*>(S), reinterpret_cast<float2*>(Xdl)};
-    if (build_tc_plan(p, H, CDMIMO_OP_FRAME, &pl) == CDMIMO_OK) return dispatch_frame_tc(pl, io, CDMIMO_OP_FRAME, s);
+    if (build_tc_plan(p, H, CDMIMO_OP_FRAME, &pl) == CDMIMO_OK) return dispatch_frame_tc(p->in_dtype, pl, io, CDMIMO_OP_FRAME, s);
     if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
         build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)
         return dispatch_frame_gram(p->in_dtype, pl, io, s);
@@ -1334,7 +1334,7 @@ int cdmimo_device_status(int clear)
     unsigned v = 0;
     if (module_status(&v, clear) != CDMIMO_OK || gram_detect_module_status(&v, clear) != CDMIMO_OK ||
         gram_precode_module_status(&v, clear) != CDMIMO_OK || gram_frame_module_status(&v, clear) != CDMIMO_OK ||
-        frame_tc_module_status(&v, clear) != CDMIMO_OK)
+        frame_tc_module_status(&v, clear) != CDMIMO_OK || frame_tc16_module_status(&v, clear) != CDMIMO_OK)
         return CDMIMO_ERR_CUDA;
     return (int)v;
 }

@@ -1,6 +1,6 @@
-// Translation unit of the tensor-core Gram-form kernel (cd_frame_tc.cuh): instantiation for
-// clusters of 16 or 32 antennas and each mode (TDD frame, uplink alone, downlink alone, learned
-// uplink), and dispatch.
+// Translation unit of the tensor-core Gram-form kernel (cd_frame_tc.cuh) for c64 storage:
+// instantiation for clusters of 16 or 32 antennas and each mode (TDD frame, uplink alone, downlink
+// alone, learned uplink), and dispatch (16-bit storage: gram_frame_tc16.cu).
 #include "cd_frame_tc.cuh"
 #include "launch.h"
 
@@ -12,16 +12,17 @@ template <int MODE>
 int dispatch_mode(const CdPlan& pl, const FusedIO& io, cudaStream_t s)
 {
     switch (pl.A_uniform) {
-    case 1: return launch_persistent(cd_frame_tc_kernel<16, MODE>, pl, io, s);
-    case 2: return launch_persistent(cd_frame_tc_kernel<32, MODE>, pl, io, s);
+    case 1: return launch_persistent(cd_frame_tc_kernel<16, MODE, CDMIMO_C64>, pl, io, s);
+    case 2: return launch_persistent(cd_frame_tc_kernel<32, MODE, CDMIMO_C64>, pl, io, s);
     }
     return CDMIMO_ERR_UNSUPPORTED;
 }
 
 }  // namespace
 
-int dispatch_frame_tc(const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s)
+int dispatch_frame_tc(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s)
 {
+    if (in_dtype != CDMIMO_C64) return dispatch_frame_tc16(in_dtype, pl, io, op, s);
     switch (op) {
     case CDMIMO_OP_FRAME: return dispatch_mode<kTcFrame>(pl, io, s);
     case CDMIMO_OP_DETECT: return pl.learned ? dispatch_mode<kTcDetectLearned>(pl, io, s) : dispatch_mode<kTcDetect>(pl, io, s);

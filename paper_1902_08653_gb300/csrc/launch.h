@@ -72,10 +72,13 @@ int gram_detect_module_status(unsigned* v, int clear);
 int gram_precode_module_status(unsigned* v, int clear);
 int dispatch_frame_gram(int in_dtype, const CdPlan& pl, const FusedIO& io, cudaStream_t s);
 int gram_frame_module_status(unsigned* v, int clear);
-// Entry points of the tensor-core translation unit (gram_frame_tc.cu); op is CDMIMO_OP_FRAME,
-// CDMIMO_OP_DETECT (io.S, io.Xdl unused; learned sweeps and fusion when pl.learned) or
-// CDMIMO_OP_PRECODE (only io.d.H and io.d.sched of io.d used).
-int dispatch_frame_tc(const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
+// Entry points of the tensor-core translation units (gram_frame_tc.cu: c64 storage;
+// gram_frame_tc16.cu: fp16 / bf16 storage); op is CDMIMO_OP_FRAME, CDMIMO_OP_DETECT (io.S, io.Xdl
+// unused; learned sweeps and fusion when pl.learned, c64 only) or CDMIMO_OP_PRECODE (only io.d.H and
+// io.d.sched of io.d used).
+int dispatch_frame_tc(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
+int dispatch_frame_tc16(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
 int frame_tc_module_status(unsigned* v, int clear);
+int frame_tc16_module_status(unsigned* v, int clear);
 
 }  // namespace cdmimo

@@ -93,7 +93,13 @@ __host__ __device__ inline int gram_phase_threads(int C, int J, int AT)
 // Tile-row stride (entries) of z, x and w in the tensor-core frame kernel: at least n_tiles, 4 mod 16.
 __host__ __device__ constexpr unsigned tc_x_stride(int n_tiles) { return ((unsigned)n_tiles + 11u) / 16u * 16u + 4u; }
 
-// Floats per shared-memory channel row of the tensor-core frame kernel for clusters of Bc antennas.
-__host__ __device__ constexpr unsigned tc_row_floats(int Bc) { return 2u * (unsigned)Bc + 8u; }
+// 32-bit words per shared-memory channel row of the tensor-core kernel for clusters of Bc antennas:
+// c64 entries (two words each) padded by 8 words (the fragment loads of both contractions are then
+// bank-conflict free), 16-bit complex entries (one word) by 4 (conflict-free for z and G_c, two-way
+// for x_c = H_c w).
+__host__ __device__ constexpr unsigned tc_row_words(int Bc, int in_dtype)
+{
+    return in_dtype == CDMIMO_C64 ? 2u * (unsigned)Bc + 8u : (unsigned)Bc + 4u;
+}
 
 }  // namespace cdmimo

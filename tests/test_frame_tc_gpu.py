@@ -123,13 +123,15 @@ def test_frame_tc_k0_and_schedules(dev):
 
 
 def test_frame_tc_declines_other_shapes(dev):
-    """Shapes outside the kernel's (U <= 8, uneven or other cluster sizes, n_sym > 16, 16-bit
-    storage) run the FP32 Gram frame or the two calls."""
+    """Shapes outside the kernel's (U <= 8, uneven or other cluster sizes, n_sym > 16) run the FP32
+    Gram frame or the two calls; 16-bit storage takes it."""
     for args in ((8, 14, 128, 8, [32] * 4), (8, 14, 192, 16, [64, 64, 64]), (8, 17, 256, 16, [32] * 8),
                  (8, 14, 256, 16, [48, 16] * 4)):
         n_sc, n_sym, B, U, cs = args
         assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, 3) != "gram_tc"
-    assert cdmimo.selected_form(cdmimo.OP_FRAME, 8, 14, 256, 16, [32] * 8, 3, in_dtype=cdmimo.C16F) != "gram_tc"
+    for dt in (cdmimo.C16F, cdmimo.C16BF):
+        for op in (cdmimo.OP_FRAME, cdmimo.OP_DETECT, cdmimo.OP_PRECODE):
+            assert cdmimo.selected_form(op, 8, 14, 256, 16, [32] * 8, 3, in_dtype=dt) == "gram_tc"
 
 
 @pytest.mark.parametrize("name", ["cfg2_B256_C8x32_U16", "more_subcarriers_than_ctas", "Bc16_C16_U10_n_sym8",
@@ -203,4 +205,36 @@ def test_tc_bad_noise_variance_and_K0(dev):
     Nt = t(N0, dev)
     assert not cdmimo.detect(Ht, Yt, Nt, cs, 0, form="gram_tc").abs().any()
     assert not cdmimo.precode(Ht, St, cs, 0, form="gram_tc").abs().any()
+    assert cdmimo.device_status(clear=True) == 0
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("n_sc,n_sym,cs,U,K,snr", [(41, 14, [32] * 8, 16, 3, "sweep"), (17, 9, [16] * 6, 12, 2, 20.0)])
+def test_tc_16bit_storage(dev, kind, n_sc, n_sym, cs, U, K, snr):
+    """fp16 / bf16 channel and receive samples with per-subcarrier scales: each stored value is exact
+    in TF32, so z and G_c take one MMA per tile and x_c = H_c w two.  Frame, detection and precoding
+    against the FP64 oracle on the dequantized values (1e-4), and against the FP32 Gram kernels on the
+    same 16-bit data (2e-5) where B_c >= 2U."""
+    snr = wl.sweep_snr(n_sc) if snr == "sweep" else snr
+    d = wl.uplink(zlib.crc32(kind.encode()) % 1000 + n_sc, n_sc, n_sym, sum(cs), U, snr_db=snr)
+    qH, sH, H64 = wl.quantize_c16(d["H"], kind)
+    qY, sY, Y64 = wl.quantize_c16(d["Y"], kind)
+    tdt = torch.float16 if kind == "f16" else torch.bfloat16
+    Ht = t(qH.view(np.int16), dev).view(tdt)
+    Yt = t(qY.view(np.int16), dev).view(tdt)
+    S32, S64 = wl.as_c64(d["X"])
+    N0 = d["N0"].astype(np.float32)
+    sc = dict(h_scale=t(sH, dev), y_scale=t(sY, dev))
+    Nt, St = t(N0, dev), t(S32, dev)
+    X, P = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, K, form="gram_tc", **sc)
+    Xd = cdmimo.detect(Ht, Yt, Nt, cs, K, form="gram_tc", **sc)
+    Pd = cdmimo.precode(Ht, St, cs, K, form="gram_tc")
+    Xo, _, _ = orc.detect(H64, Y64, N0.astype(np.float64), cs, K, threads=8)
+    Po = orc.precode(H64, S64, cs, K, threads=8)
+    for got, ref, what in ((X, Xo, "frame Xhat"), (P, Po, "frame Xdl"), (Xd, Xo, "detect"), (Pd, Po, "precode")):
+        assert_vectors_close(got.cpu().numpy(), ref, TOL, f"tc {kind} {what}")
+    if min(cs) >= 2 * U:
+        Xg, Pg = cdmimo.detect_precode(Ht, Yt, Nt, St, cs, K, form="gram", **sc)
+        assert_vectors_close(X.cpu().numpy(), Xg.cpu().numpy(), 2e-5, f"tc vs fp32 gram {kind} Xhat")
+        assert_vectors_close(P.cpu().numpy(), Pg.cpu().numpy(), 2e-5, f"tc vs fp32 gram {kind} Xdl")
     assert cdmimo.device_status(clear=True) == 0
