@@ -366,8 +366,67 @@ def run_cuda(args, rank, world, local_rank):
         "clocks": clocks,
         "wall_s": wall,
     }
+    if frame and args.form in ("auto", "gram_tc"):
+        line["precision"] = precision_variants(up, dl, dev, stream, min(args.steps, 200), args.e2e_chunks)
     line["cpu_baseline"] = cpu_baseline(up, dl, frame) if world == 1 else None
     return line
+
+
+def precision_variants(up, dl, dev, stream, steps, e2e_chunks):
+    """The frame step with H and y stored as fp16 and as bf16 (per-subcarrier scales; every
+    arithmetic step FP32): device time (CUDA events, L2 flushed), MSE against the L-MMSE of the
+    unquantized data, and the end-to-end rate through cdmimo_detect_precode_host with 16-bit host
+    buffers (the uploads of H and y halve)."""
+    import torch
+
+    from paper_1902_08653_gb300 import cdmimo
+    from paper_1902_08653_gb300 import workload as wl
+
+    N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
+    S = torch.from_numpy(wl.as_c64(dl["S"])[0]).to(dev)
+    N0h = torch.from_numpy(up["N0"].astype(np.float32)).pin_memory()
+    Sh = torch.from_numpy(wl.as_c64(dl["S"])[0]).pin_memory()
+    out = {}
+    for kind, tdt, code in (("f16", torch.float16, cdmimo.C16F), ("bf16", torch.bfloat16, cdmimo.C16BF)):
+        qH, sH, _ = wl.quantize_c16(up["H"], kind)
+        qY, sY, _ = wl.quantize_c16(up["Y"], kind)
+        Hq = torch.from_numpy(qH.view(np.int16)).view(tdt)
+        Yq = torch.from_numpy(qY.view(np.int16)).view(tdt)
+        sHt, sYt = torch.from_numpy(sH), torch.from_numpy(sY)
+        H, Y, hs, ys = Hq.to(dev), Yq.to(dev), sHt.to(dev), sYt.to(dev)
+        X = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64, device=dev)
+        P = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64, device=dev)
+        fn = lambda: cdmimo.detect_precode(H, Y, N0, S, CS, K, out=X, out_dl=P, h_scale=hs, y_scale=ys)
+        _, ms = time_device(fn, steps, 5, dev)
+        fn()
+        mse, _ = mse_vs_mmse(up, X.cpu().numpy().astype(np.complex128))
+        Hh, Yh = Hq.pin_memory(), Yq.pin_memory()
+        Xh = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64).pin_memory()
+        Ph = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64).pin_memory()
+        ws = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_FRAME, N_SC, N_SYM, B, U, CS, K, in_dtype=code),
+                         dtype=torch.uint8, device=dev)
+        e2e = lambda: cdmimo.detect_precode_host(Hh, Yh, N0h, Sh, CS, K, Xh, Ph, ws, h_scale=sHt.pin_memory(),
+                                                  y_scale=sYt.pin_memory(), n_chunks=e2e_chunks, stream=stream)
+        for _ in range(2):
+            e2e()
+        torch.cuda.synchronize()
+        n_e2e = max(3, min(50, steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / n_e2e
+        out[kind] = {"kernel": "cd_frame_tc_kernel", "ms": ms, "vectors_per_s": N_SC * N_SYM / (ms * 1e-3),
+                     "mse_vs_mmse_mean": float(np.mean(list(mse.values()))),
+                     "e2e": {"vectors_per_s": N_SC * N_SYM / (e2e_ms * 1e-3), "ms_per_step": e2e_ms,
+                             "h2d_bytes_per_step": int(Hh.numel() * 2 + Yh.numel() * 2 + N0h.numel() * 4 +
+                                                       Sh.numel() * 8 + 8 * N_SC),
+                             "d2h_bytes_per_step": int(Xh.numel() * 8 + Ph.numel() * 8)}}
+    if cdmimo.device_status(clear=True) != 0:
+        raise RuntimeError("device status set by the 16-bit frame runs")
+    return out
 
 
 def cpu_baseline(up, dl, frame=True, min_seconds=10.0, threads=None):
