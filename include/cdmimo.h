@@ -81,8 +81,10 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             tensor cores (TF32 MMAs with each FP32 operand split into a TF32 part and its
  *             remainder, FP32 accumulation; the sweeps stay FP32), for cdmimo_detect (without
  *             Xc_opt / lambda_opt), cdmimo_precode and cdmimo_detect_precode.  That kernel takes
- *             c64 storage, every B_c = 16 or every B_c = 32, 8 < U <= 16, n_sym <= 16 and
- *             2 C n_sym <= 256, and a learned block in cdmimo_detect only; elsewhere GRAM_TC is GRAM.
+ *             c64, fp16 or bf16 storage (16-bit values are exact TF32 operands: one MMA where both
+ *             operands are stored values), every B_c = 16 or every B_c = 32, 8 < U <= 16,
+ *             n_sym <= 16 and 2 C n_sym <= 256, and a learned block (c64) in cdmimo_detect only;
+ *             elsewhere GRAM_TC is GRAM.
  *   AUTO      GRAM where it applies, every B_c >= 2 U (so G_c + (N0/Ex) I stays well conditioned
  *             in FP32) and it needs fewer complex MACs, on the tensor cores where GRAM_TC's kernel
  *             takes the call; else RESIDUAL.
