@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     constexpr bool LEARNED = MODE == kTcDetectLearned;
     constexpr int UT = kTcUT;
     constexpr int SROW = (int)tc_row_words(BC, IN);  // 32-bit words per channel row
-    constexpr int SR2 = SROW / 2;     // the same in complex entries
+    constexpr int SR2 = SROW / 2;     // c64: the same in complex entries
     constexpr int KA = BC / 4;        // phase A k-steps (4 antennas each)
     constexpr int MT = BC / 16;       // phase C m-tiles (16 antennas each)
     constexpr int KC = UT / 4;        // phase C k-steps (4 users each)

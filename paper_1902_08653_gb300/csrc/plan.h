@@ -45,8 +45,10 @@ struct CdPlan {
     float inv_Ex;
     float rho_c;      // downlink per-cluster norm rho / sqrt(C)
     // byte offsets of the shared-memory regions (channel blocks start at 0; the packed kernels keep
-    // a second channel buffer at off_H2 and per-tile coefficients at off_K)
-    // off_mlp: [C][CDMIMO_MAX_HIDDEN] floats of learned-fusion partial sums (learned plans only)
+    // a second channel buffer at off_H2 and per-tile coefficients at off_K; the tensor-core kernel's
+    // learned plans keep the per-sweep coefficient table [C][K][16] at off_K)
+    // off_mlp: [C][CDMIMO_MAX_HIDDEN] floats of learned-fusion partial sums (learned plans; the
+    // tensor-core kernel keeps only the C logits there)
     // off_G, off_E: Gram form, [C][UT][UT/2] pair-planar rows of G_c with zero diagonal and [C][UT]
     // column energies
     unsigned off_H2, off_H3, off_X, off_K, off_coef, off_e, off_lam, off_S, off_mlp, off_tab, off_bar, smem_bytes;
