@@ -676,13 +676,20 @@ def run_profile(args):
     t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
     H, Y, S = t(up["H"]), t(up["Y"]), t(up["X"])
     N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
+    sc = {}
+    if args.profile == "frame_f16":  # the same batch stored as fp16 with per-subcarrier scales
+        qH, sH, _ = wl.quantize_c16(up["H"], "f16")
+        qY, sY, _ = wl.quantize_c16(up["Y"], "f16")
+        H = torch.from_numpy(qH.view(np.int16)).to(dev).view(torch.float16)
+        Y = torch.from_numpy(qY.view(np.int16)).to(dev).view(torch.float16)
+        sc = dict(h_scale=torch.from_numpy(sH).to(dev), y_scale=torch.from_numpy(sY).to(dev))
     for _ in range(3):
         if args.profile == "detect":
             cdmimo.detect(H, Y, N0, CS, K, form=args.form)
         elif args.profile == "precode":
             cdmimo.precode(H, S, CS, K, form=args.form)
         else:
-            cdmimo.detect_precode(H, Y, N0, S, CS, K, form=args.form)
+            cdmimo.detect_precode(H, Y, N0, S, CS, K, form=args.form, **sc)
     torch.cuda.synchronize()
     assert cdmimo.device_status(clear=True) == 0
     print("ok", args.profile, args.form)
@@ -697,7 +704,7 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2 (default): UL detect + DL precode bench line; 1, 3, 4, 5: the other configurations")
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
-    ap.add_argument("--profile", choices=["detect", "precode", "frame"], default=None,
+    ap.add_argument("--profile", choices=["detect", "precode", "frame", "frame_f16"], default=None,
                     help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu")
     ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc"], default="auto", help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,
