@@ -338,6 +338,8 @@ def run_cuda(args, rank, world, local_rank):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms_step,
+        "step_ms_percentiles": {q: float(np.percentile(np.add(t_a, t_b), v)) for q, v in
+                                (("p10", 10), ("median", 50), ("p90", 90))},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
