@@ -7,7 +7,7 @@ A warp's lane l is (gid, tig) = (l // 4, l % 4).  32-bit accesses are served per
 4 bytes); 64-bit accesses per half-warp (16 lanes), an 8-byte word covering two banks.  Lanes that
 read the same address share it (broadcast).
 """
-
+import os
 
 PLAN_H = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1902_08653_gb300",
                            "csrc", "plan.h")).read()
