@@ -79,8 +79,9 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             the packed-kernel shapes) and no learned block; otherwise CDMIMO_ERR_UNSUPPORTED.
  *   GRAM_TC   GRAM, with the contractions z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w on the
  *             tensor cores (TF32 MMAs with each FP32 operand split into a TF32 part and its
- *             remainder, FP32 accumulation; the sweeps stay FP32), for cdmimo_detect (without
- *             Xc_opt / lambda_opt), cdmimo_precode and cdmimo_detect_precode.  That kernel takes
+ *             remainder, FP32 accumulation; the sweeps stay FP32), for cdmimo_detect (with a
+ *             learned block: without Xc_opt / lambda_opt), cdmimo_precode and cdmimo_detect_precode.
+ *             That kernel takes
  *             c64, fp16 or bf16 storage (16-bit values are exact TF32 operands: one MMA where both
  *             operands are stored values), every B_c = 16 or every B_c = 32, 8 < U <= 16,
  *             n_sym <= 16 and 2 C n_sym <= 256, and a learned block (c64) in cdmimo_detect only;
@@ -419,7 +420,7 @@ size_t cdmimo_workspace_size(const cdmimo_params* p, int op);
 size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
 
 /* The evaluation form (CDMIMO_FORM_RESIDUAL, CDMIMO_FORM_GRAM or CDMIMO_FORM_GRAM_TC) that
- * cdmimo_detect (op = CDMIMO_OP_DETECT, without Xc_opt / lambda_opt) or cdmimo_precode
+ * cdmimo_detect (op = CDMIMO_OP_DETECT) or cdmimo_precode
  * (CDMIMO_OP_PRECODE) would run for p and a channel at H (its alignment decides the staging path), or
  * a negative status (for example UNSUPPORTED for a forced GRAM that does not apply).
  * op = CDMIMO_OP_FRAME: the form of cdmimo_detect_precode's one-kernel frame, or, where it enqueues

@@ -681,6 +681,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
             } else {
                 fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
             }
+        } else if constexpr (MODE == kTcDetect) {
+            if (d.Xc || d.lam) fuse_subcarrier<false>(pl, d, f, lam, Zs, xs, out_scale);  // + per-cluster outputs
+            else fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
         } else if constexpr (UL) {
             fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
         }

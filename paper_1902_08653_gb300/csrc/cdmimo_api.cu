@@ -454,9 +454,9 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
         return p->in_dtype != CDMIMO_C64 ? CDMIMO_ERR_UNSUPPORTED : CDMIMO_ERR_INVALID_ARG;
     if (p->n_sc == 0) return CDMIMO_OK;
     CdPlan pl;
-    if (!Xc && !lam && build_tc_plan(p, H, CDMIMO_OP_DETECT, &pl) == CDMIMO_OK) {
-        const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat), nullptr, nullptr,
-                          p->learned, sched},
+    if ((!p->learned || (!Xc && !lam)) && build_tc_plan(p, H, CDMIMO_OP_DETECT, &pl) == CDMIMO_OK) {
+        const FusedIO io{{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat),
+                          reinterpret_cast<float2*>(Xc), lam, p->learned, sched},
                          nullptr, nullptr};
         return dispatch_frame_tc(p->in_dtype, pl, io, CDMIMO_OP_DETECT, s);
     }
