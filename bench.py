@@ -65,7 +65,7 @@ FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
 NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.806592e6 + 0.621568e6,
                "cd_precode_gram_kernel": 41.539072e6 + 0.377088e6,
                "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6,
-               "cd_frame_tc_kernel": 75.999488e6 + 5.082880e6}
+               "cd_frame_tc_kernel": 75.996672e6 + 4.606464e6}
 
 WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
             "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
