@@ -64,6 +64,28 @@ def test_learned_sweeps_are_sor(oracle, seed):
     assert np.all(lam > 0)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_learned_fusion_is_cluster_permutation_equivariant(oracle, seed):
+    """Relabelling equal-size clusters (permuting their antenna blocks) permutes the per-cluster
+    estimates and the fusion weights the same way and leaves the fused estimate unchanged: the MLP
+    sees each cluster's own features, and the softmax runs over clusters."""
+    g = np.random.default_rng(500 + seed)
+    U, K, Hd, C, Bc = 3, 2, 6, 4, 5
+    cs = [Bc] * C
+    H = crandn(g, 3, U, C * Bc)
+    Y = crandn(g, 3, 2, C * Bc)
+    N0 = g.uniform(0.1, 1.0, 3)
+    master = make_master(g, K, U, Hd)
+    X, Xc, lam = oracle.learned_forward(H, Y, N0, cs, K, master, Hd)
+    perm = np.roll(np.arange(C), 1 + seed)  # a non-trivial relabelling
+    cols = np.concatenate([np.arange(p * Bc, (p + 1) * Bc) for p in perm])
+    Xp, Xcp, lamp = oracle.learned_forward(H[:, :, cols], Y[:, :, cols], N0, cs, K, master, Hd)
+    np.testing.assert_allclose(lamp, lam[:, perm], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Xcp, Xc[:, perm], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(Xp, X, rtol=1e-12, atol=1e-14)
+    assert np.ptp(lam, axis=1).min() > 1e-3  # the weights do differ between clusters
+
+
 def test_reduces_to_plain_cd_with_equal_fusion(oracle):
     g = np.random.default_rng(7)
     d = wl.uplink(3, 5, 3, 64, 8, snr_db=wl.sweep_snr(5))
