@@ -236,6 +236,40 @@ def test_fusion_weights_sum_to_one_and_equal_rule(oracle):
             np.testing.assert_allclose(Xhat, Xc.mean(axis=1), rtol=1e-13)
 
 
+def test_antenna_and_cluster_relabelling(oracle):
+    """Permuting the antennas inside each cluster leaves detection (estimates, per-cluster estimates,
+    fusion weights) unchanged and permutes the precoder's output the same way; relabelling
+    equal-size clusters permutes the per-cluster outputs and weights and leaves the fused estimate
+    unchanged.  The algorithms see a cluster's antennas only through inner products over them."""
+    g = np.random.default_rng(41)
+    cs = [6, 9, 6, 5]
+    o = offsets(cs)
+    B, U = sum(cs), 4
+    H = crandn(g, 3, U, B)
+    Y = crandn(g, 3, 2, B)
+    S = crandn(g, 3, 2, U)
+    N0 = g.uniform(0.05, 0.8, 3)
+    cols = np.concatenate([o[c] + g.permutation(cs[c]) for c in range(len(cs))])  # within clusters
+    X, Xc, lam = oracle.detect(H, Y, N0, cs, 3)
+    Xp, Xcp, lamp = oracle.detect(H[:, :, cols], Y[:, :, cols], N0, cs, 3)
+    np.testing.assert_allclose(Xp, X, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(Xcp, Xc, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(lamp, lam, rtol=1e-12)
+    P = oracle.precode(H, S, cs, 3)
+    Pp = oracle.precode(H[:, :, cols], S, cs, 3)
+    np.testing.assert_allclose(Pp, P[:, :, cols], rtol=1e-12, atol=1e-14)
+    # equal-size clusters relabelled (blocks 0 and 2 swapped)
+    cs2 = [6, 6, 6]
+    H2, Y2 = H[:, :, :18], Y[:, :, :18]
+    blocks = np.concatenate([np.arange(12, 18), np.arange(6, 12), np.arange(0, 6)])
+    X2, Xc2, lam2 = oracle.detect(H2, Y2, N0, cs2, 3)
+    X2p, Xc2p, lam2p = oracle.detect(H2[:, :, blocks], Y2[:, :, blocks], N0, cs2, 3)
+    np.testing.assert_allclose(lam2p, lam2[:, ::-1], rtol=1e-12)
+    np.testing.assert_allclose(Xc2p, Xc2[:, ::-1], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(X2p, X2, rtol=1e-12, atol=1e-14)
+    assert np.ptp(lam2, axis=1).min() > 1e-4  # the clusters do get different weights
+
+
 def test_fusion_identical_clusters(oracle):
     g = np.random.default_rng(13)
     Hh = crandn(g, 2, 4, 8)
