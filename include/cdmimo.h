@@ -435,6 +435,14 @@ const char* cdmimo_status_string(int status);
  * cdmimo_status if the read itself fails. */
 int cdmimo_device_status(int clear);
 
+/* Failure-path check of the kernels' bounded waits (the paper has no counterpart).  Enqueues on
+ * `stream` one thread that waits, through the same bounded-wait routine the kernels use for their
+ * asynchronous copies, on a barrier that nothing completes.  After timeout_us microseconds the wait
+ * gives up, sets CDMIMO_DEV_TIMEOUT in the device status word (read it with cdmimo_device_status) and
+ * the kernel returns: no trap, and the context stays usable.  timeout_us must be in
+ * [1, 2000000] (else CDMIMO_ERR_INVALID_ARG); CDMIMO_ERR_CUDA if the launch fails. */
+int cdmimo_check_bounded_wait(unsigned timeout_us, void* stream);
+
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int cdmimo_version(void);
 

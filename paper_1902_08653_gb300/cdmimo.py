@@ -94,6 +94,7 @@ def lib():
             "cdmimo_status_string": ([I], ctypes.c_char_p),
             "cdmimo_device_status": ([I], I),
             "cdmimo_version": ([], I),
+            "cdmimo_check_bounded_wait": ([ctypes.c_uint, P], I),
             "cdmimo_learned_param_count": ([I, I, I], S),
             "cdmimo_learned_pack": ([P, I, I, I, P, P], I),
             "cdmimo_learned_grad": ([PP, I, P, P, P, P, P, P, P, S, P], I),
@@ -475,3 +476,9 @@ def synth_uplink(seed, n_sc, n_sym, B, U, snr_db, M=16, device="cuda", labels=Fa
     if labels:
         out["labels"] = lab
     return out
+
+
+def check_bounded_wait(timeout_us=20000, stream=None):
+    """cdmimo_check_bounded_wait: one thread's bounded wait on a barrier nothing completes expires
+    after timeout_us and sets DEV_TIMEOUT (read it with device_status)."""
+    _check("cdmimo_check_bounded_wait", lib().cdmimo_check_bounded_wait(int(timeout_us), _stream(stream)))

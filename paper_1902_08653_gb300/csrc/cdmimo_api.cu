@@ -862,7 +862,26 @@ int streaming_launch(const cdmimo_params* p, int op, const void* H, const void* 
 
 }  // namespace
 
+// One thread waits on an mbarrier that nothing completes, for at most limit_ns, and gives up the way
+// every bounded wait of the kernels does (status bit CDMIMO_DEV_TIMEOUT); the kernel then returns.
+__global__ void bounded_wait_check_kernel(unsigned long long limit_ns)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async_smem();
+        mbar_wait_bounded(&bar, 0u, limit_ns);
+    }
+}
+
 extern "C" {
+
+int cdmimo_check_bounded_wait(unsigned timeout_us, void* stream)
+{
+    if (timeout_us < 1u || timeout_us > 2000000u) return CDMIMO_ERR_INVALID_ARG;
+    bounded_wait_check_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(1000ull * timeout_us);
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
 
 int cdmimo_detect(const cdmimo_params* p, const void* H, const void* Y, const float* N0, void* Xhat, void* Xc_opt,
                   float* lambda_opt, void* workspace, size_t ws_bytes, void* stream)

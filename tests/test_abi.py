@@ -167,3 +167,9 @@ def test_learned_block_layout_and_param_count():
     L = cdmimo.lib()
     assert L.cdmimo_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == cdmimo.ERR_INVALID_ARG
     assert L.cdmimo_learned_pack(None, 2, 16, 64, None, None) == cdmimo.ERR_INVALID_ARG
+
+
+def test_check_bounded_wait_rejects_limits_out_of_range():
+    L = cdmimo.lib()
+    for us in (0, 2000001, 4000000000):
+        assert L.cdmimo_check_bounded_wait(us, None) == cdmimo.ERR_INVALID_ARG
