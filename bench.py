@@ -370,7 +370,11 @@ def run_cuda(args, rank, world, local_rank):
     }
     if frame and args.form in ("auto", "gram_tc"):
         line["precision"] = precision_variants(up, dl, dev, stream, min(args.steps, 200), args.e2e_chunks)
-    line["cpu_baseline"] = cpu_baseline(up, dl, frame) if world == 1 else None
+    cb = cpu_baseline(up, dl, frame) if world == 1 else None
+    if cb is not None:  # and on one host thread
+        st = cpu_baseline(up, dl, frame, min_seconds=3.0, threads=1)
+        cb["single_thread"] = {"value": st["value"], "unit": st["unit"], "cores": 1, "sample": st["sample"]}
+    line["cpu_baseline"] = cb
     return line
 
 
