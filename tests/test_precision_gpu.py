@@ -2,8 +2,10 @@
 unquantized inputs, per SNR and K (config-3 shape: B = 256 in 8 x 32, U = 32, 64-QAM, 14 symbols).
 
 This is the total error of storing H and y in fp16 / bf16 (with per-subcarrier scales) and
-computing in FP32.  The bounds asserted are the ones stated in the design doc; set CDMIMO_REPORT_DIR to
-write the per-SNR table as JSON.
+computing in FP32.  Asserted: the median relative L2 error per vector stays below a per-type bound
+of the order of that type's unit roundoff times the conditioning (BOUNDS below), and the hard-decision
+BER stays within 5% (plus 1e-4) of the oracle's; set CDMIMO_REPORT_DIR to write the per-SNR table as
+JSON.
 """
 import json
 import os
