@@ -8,8 +8,9 @@ The arithmetic lives in ``cdmimo_oracle.c`` (plain C99, double precision); this 
 it with gcc, loads it with ctypes and marshals numpy arrays.  ctypes releases the GIL during a
 call, so ``threads > 1`` splits the subcarriers over a thread pool.
 
-Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` (closed forms,
-library solves, matrix-splitting forms, invariants, brute force), except the fusion-weight rule
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_learned.py`` (closed forms, library solves, matrix-splitting forms, invariants,
+brute force; the learned fusion by hand-set weights whose logits are derived by hand), except the fusion-weight rule
 for ``fuse="colnorm"``, whose formula is a reading of an under-specified passage (Sec. III): it is
 pinned only by its invariants (weights sum to one, equal clusters get equal weights, a scaled
 cluster gets the closed-form weight), not by a value the paper prints.

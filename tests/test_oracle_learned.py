@@ -136,3 +136,107 @@ def test_gradient_matches_central_differences(oracle, seed):
     F = U + 1
     groups = np.split(grad, np.cumsum([K, K, Hd * F, Hd, Hd]))
     assert all(np.any(np.abs(gr) > 0) for gr in groups)
+
+
+# --- Hand-computed pins of the learned fusion (features, MLP, ReLU, softmax) -------------------------
+#
+# A 3-subcarrier case whose cluster energies are small integers, with hand-set weights, so that every
+# logit is a number derived by hand below.  U = 2, clusters of B_c = 2, 4, 2 antennas (uneven, so a
+# dropped 1/B_c changes the features), F = U + 1 = 3 features phi_c = [e_{0,c}/B_c, e_{1,c}/B_c,
+# log10(max(alpha, 1e-6))], hidden width 4.
+#
+#   user 0:  cluster 0 [1, 1j] -> e = 2, /2 = 1.0;  cluster 1 [1, 0, 0, 1] -> 2, /4 = 0.5;
+#            cluster 2 [2, 0] -> 4, /2 = 2.0
+#   user 1:  cluster 0 [0, 1] -> 1, /2 = 0.5;  cluster 1 [1, 1, 1, 1] -> 4, /4 = 1.0;
+#            cluster 2 [1j, 1] -> 2, /2 = 1.0
+#
+# Hidden units (W1 row, b1) and output weights w2, b2 = -0.5:
+#   k = 0: [1, 0, 0],  0   -> relu(phi_0)                            w2 = 1
+#   k = 1: [0, 1, 1],  2   -> relu(phi_1 + log10 alpha + 2)          w2 = 2
+#   k = 2: [-1, 0, 0], -0.25 -> always negative: ReLU off            w2 = 10
+#   k = 3: [1, 0, -1], -7  -> relu(phi_0 - log10 alpha - 7)          w2 = 1
+# Subcarrier 0, N0 = 0.01 (log10 alpha = -2): units 0, 1, 3 give [1, .5, 2], [.5, 1, 1], 0
+#   -> logits [1 + 1, .5 + 2, 2 + 2] - 0.5 = [1.5, 2.0, 3.5]
+# Subcarrier 1, N0 = 0 (alpha clamped to 1e-6, feature -6): unit 1 gives relu(phi_1 - 4) = 0, unit 3
+#   relu(phi_0 - 1) = [0, 0, 1] -> logits [1, .5, 2 + 1] - 0.5 = [0.5, 0.0, 2.5]
+# Subcarrier 2, N0 = 10 (feature 1): unit 1 gives [3.5, 4, 4], unit 3 is off
+#   -> logits [1 + 7, .5 + 8, 2 + 8] - 0.5 = [7.5, 8.0, 9.5]
+HAND_CS = [2, 4, 2]
+HAND_N0 = np.array([0.01, 0.0, 10.0])
+HAND_LOGITS = np.array([[1.5, 2.0, 3.5], [0.5, 0.0, 2.5], [7.5, 8.0, 9.5]])
+
+
+def hand_channel():
+    row0 = [1, 1j, 1, 0, 0, 1, 2, 0]
+    row1 = [0, 1, 1, 1, 1, 1, 1j, 1]
+    return np.tile(np.array([row0, row1], complex), (3, 1, 1))
+
+
+def hand_master(K, tau=1.0, graw=GRAW_ONE):
+    W1 = np.array([[1, 0, 0], [0, 1, 1], [-1, 0, 0], [1, 0, -1]], float)
+    b1 = np.array([0.0, 2.0, -0.25, -7.0])
+    w2 = np.array([1.0, 2.0, 10.0, 1.0])
+    return np.concatenate([np.full(K, tau), np.full(K, graw), W1.ravel(), b1, w2, [-0.5]])
+
+
+def softmax_rows(z):
+    e = np.exp(z - z.max(axis=1, keepdims=True))
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def test_learned_fusion_hand_computed_weights(oracle):
+    """The fusion weights of the hand-set MLP equal the softmax of the logits derived by hand above:
+    this fixes the features (1/B_c, log10 and its clamp at 1e-6), the row-major W1, the ReLU, w2, b2
+    and the softmax over clusters."""
+    g = np.random.default_rng(41)
+    H = hand_channel()
+    Y = crandn(g, 3, 2, 8)
+    _, _, lam = oracle.learned_forward(H, Y, HAND_N0, HAND_CS, 1, hand_master(1), 4)
+    np.testing.assert_allclose(lam, softmax_rows(HAND_LOGITS), rtol=1e-13, atol=1e-15)
+    # the literal values of subcarrier 0: exp([0, .5, 2]) / (1 + e^0.5 + e^2)
+    np.testing.assert_allclose(lam[0], [0.09962364, 0.16425163, 0.73612473], rtol=1e-7)
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_learned_fused_estimate_hand_computed(oracle, K):
+    """With tau = gamma = 1 the per-cluster estimates are Gauss-Seidel iterates (library triangular
+    solves of the splitting), and the fused estimate is their combination with the hand-derived
+    weights."""
+    g = np.random.default_rng(43 + K)
+    H = hand_channel()
+    Y = crandn(g, 3, 2, 8)
+    X, Xc, lam = oracle.learned_forward(H, Y, HAND_N0, HAND_CS, K, hand_master(K), 4)
+    lam_ref = softmax_rows(HAND_LOGITS)
+    o = np.concatenate([[0], np.cumsum(HAND_CS)])
+    for f in range(3):
+        want = np.zeros((2, 2), complex)
+        for c in range(3):
+            for n in range(2):
+                xc = sor_reference(H[f, :, o[c]:o[c + 1]], Y[f, n, o[c]:o[c + 1]], HAND_N0[f], [1.0] * K, [1.0] * K)
+                np.testing.assert_allclose(Xc[f, c, n], xc, rtol=1e-11, atol=1e-12)
+                want[n] += lam_ref[f, c] * xc
+        np.testing.assert_allclose(X[f], want, rtol=1e-11, atol=1e-12)
+
+
+def test_learned_fusion_scaled_cluster_closed_form(oracle):
+    """Random channels, a single hidden unit selecting user j's normalized energy: lambda_c is
+    proportional to exp(w ||h_{j,c}||^2 / B_c), with the energies summed directly from H."""
+    g = np.random.default_rng(47)
+    U, K, Hd, cs = 4, 2, 3, [6, 10, 8, 12]
+    B = sum(cs)
+    H = crandn(g, 2, U, B)
+    o = np.concatenate([[0], np.cumsum(cs)])
+    for c, s in enumerate([0.5, 1.0, 1.3, 0.8]):  # distinct cluster gains
+        H[:, :, o[c]:o[c + 1]] *= s
+    Y = crandn(g, 2, 3, B)
+    N0 = np.array([0.2, 0.05])
+    j, w = 2, 0.7
+    F = U + 1
+    W1 = np.zeros((Hd, F))
+    W1[1, j] = 1.0                      # hidden unit 1 = relu(e_{j,c} / B_c) = e_{j,c} / B_c
+    b1 = np.array([-1.0, 0.0, -3.0])    # units 0 and 2 have zero weights and negative bias: off
+    w2 = np.array([5.0, w, -4.0])
+    master = np.concatenate([g.uniform(0.8, 1.2, K), g.uniform(-0.5, 0.5, K), W1.ravel(), b1, w2, [0.9]])
+    _, _, lam = oracle.learned_forward(H, Y, N0, cs, K, master, Hd)
+    energy = np.array([[np.sum(np.abs(H[f, j, o[c]:o[c + 1]]) ** 2) / cs[c] for c in range(4)] for f in range(2)])
+    np.testing.assert_allclose(lam, softmax_rows(w * energy), rtol=1e-12, atol=1e-15)
