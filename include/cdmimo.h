@@ -48,7 +48,7 @@ typedef enum {
 /* Bits of the device-side status word (cdmimo_device_status). */
 #define CDMIMO_DEV_TIMEOUT 0x1   /* a bounded wait on an async copy or work queue expired */
 #define CDMIMO_DEV_BAD_N0 0x2    /* some N0[f] was negative or NaN: that subcarrier's output is NaN */
-#define CDMIMO_DEV_BAD_LEARNED 0x4 /* the learned block does not match p->K or p->U: output is NaN */
+#define CDMIMO_DEV_BAD_LEARNED 0x4 /* the learned block does not match p->K, p->U (or hidden): output is NaN */
 #define CDMIMO_DEV_BAD_SCHED 0x8  /* a workspace's schedule counters were not zero: output incomplete */
 
 #define CDMIMO_MAX_CLUSTERS 64
@@ -350,7 +350,8 @@ int cdmimo_learned_pack(const float* master, int K, int U, int hidden, void* blo
  * through the K unfolded sweeps, the softmax and the perceptron (p->fuse is ignored).  Xtarget DEVICE c64 [n_sc][n_sym][U]; grad DEVICE float
  * [param_count] (overwritten); loss DEVICE float [1] (overwritten).  workspace DEVICE scratch of
  * cdmimo_learned_workspace_size(p) bytes (per-subcarrier partial sums, reduced in a fixed order, so
- * the result is deterministic).
+ * the result is deterministic).  A block whose K, U or hidden differs from p->K, p->U, hidden sets
+ * CDMIMO_DEV_BAD_LEARNED, and grad and loss come out NaN.
  */
 int cdmimo_learned_grad(const cdmimo_params* p, int hidden, const void* H, const void* Y, const float* N0,
                         const void* Xtarget, float* grad, float* loss, void* workspace, size_t ws_bytes,
@@ -374,6 +375,9 @@ size_t cdmimo_learned_workspace_size(const cdmimo_params* p, int hidden);
  *     start at zero).  Calls that overlap on the GPU (other streams, other host threads) race on
  *     it: serialize them.
  *   - It allocates nothing and frees nothing.
+ *   - The looked-up address is kept per device for the life of the process: do not use this entry
+ *     point on a device after cudaDeviceReset() has been called on it.
+ *   - A block that does not match (p->K, p->U, hidden) is flagged as in cdmimo_learned_grad.
  */
 #define CDMIMO_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 int cdmimo_learned_grad_noalloc(const cdmimo_params* p, int hidden, const void* H, const void* Y, const float* N0,

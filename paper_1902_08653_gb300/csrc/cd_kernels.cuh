@@ -320,7 +320,12 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_detect
 
         bool ok = true;
         if (pl.bulk) ok = mbar_wait_bounded(bar, phase);
-        if (__syncthreads_or(!ok)) return;
+        if (__syncthreads_or(!ok)) {
+            // copy timeout: give the copy in flight one last bounded wait so that no CTA leaves with
+            // its own bulk copy still writing into its shared memory
+            if (threadIdx.x == 0) mbar_wait_bounded(bar, phase);
+            return;
+        }
 
         // Preprocessing (decentralized): column energies, then m and n.
         column_energies(pl, tab, Hs, esum);
@@ -440,7 +445,12 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
 
         bool ok = true;
         if (pl.bulk) ok = mbar_wait_bounded(bar, phase);
-        if (__syncthreads_or(!ok)) return;
+        if (__syncthreads_or(!ok)) {
+            // copy timeout: give the copy in flight one last bounded wait so that no CTA leaves with
+            // its own bulk copy still writing into its shared memory
+            if (threadIdx.x == 0) mbar_wait_bounded(bar, phase);
+            return;
+        }
 
         column_energies(pl, tab, Hs, esum);
         __syncthreads();

@@ -99,6 +99,16 @@ __global__ void __launch_bounds__(512) learned_grad_kernel(const CdPlan pl, cons
     const cdmimo_learned* blk = io.blk;
     const int f = blockIdx.x;
 
+    // A block packed for other dimensions than the caller's (K, U, hidden) would be read with the
+    // wrong strides: flag it and give this subcarrier a NaN row, so the gradient and loss are NaN.
+    // The test depends only on the block, so every thread of the CTA leaves here or none does.
+    if (__ldg(&blk->K) != K || __ldg(&blk->U) != U || __ldg(&blk->hidden) != Hd) {
+        if (tid == 0 && f == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_LEARNED);
+        float* row = io.ws + (size_t)f * gl.ws_stride;
+        for (int i = tid; i <= gl.n_params; i += blockDim.x) row[i] = __int_as_float(0x7fc00000);
+        return;
+    }
+
     if (tid < C) tab[tid] = pl.cl[tid];
     __syncthreads();
     zero_padding(pl, tab, Hs);

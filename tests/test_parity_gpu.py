@@ -116,22 +116,6 @@ def test_detect_bad_noise_variance_flags(dev):
     assert cdmimo.device_status(clear=True) == 0
 
 
-def test_detect_full_size_sampled(dev):
-    """The bench workload (1200 subcarriers x 14 symbols, B = 256, C = 8 x 32, U = 16, K = 3, SNR sweep,
-    COLNORM fusion), checked on a sample of subcarriers the oracle recomputes one by one."""
-    n_sc, n_sym, B, U, cs = 1200, 14, 256, 16, [32] * 8
-    d = wl.uplink(wl.DEFAULT_SEED, n_sc, n_sym, B, U, snr_db=wl.sweep_snr(n_sc), M=16)
-    H32, H64 = wl.as_c64(d["H"])
-    Y32, Y64 = wl.as_c64(d["Y"])
-    N0 = d["N0"].astype(np.float32)
-    Xg = cdmimo.detect(to_dev(H32, dev), to_dev(Y32, dev), to_dev(N0, dev), cs, 3).cpu().numpy()
-    idx = np.random.default_rng(0).choice(n_sc, 48, replace=False)
-    idx = np.unique(np.concatenate([idx, [0, n_sc - 1]]))
-    Xo, _, _ = orc.detect(H64[idx], Y64[idx], N0[idx].astype(np.float64), cs, 3, threads=8)
-    assert_vectors_close(Xg[idx], Xo, TOL, "full-size sample")
-    assert_decisions_match(Xg[idx], Xo, 16)
-
-
 def test_detect_low_precision_storage(dev):
     """16-bit H and y with per-subcarrier scales: parity against the oracle run on the exact
     dequantized values."""
@@ -177,23 +161,6 @@ def test_precode_parity(dev, name):
     for c in range(len(cs)):
         np.testing.assert_allclose(np.linalg.norm(Xg[..., o[c]:o[c + 1]], axis=-1), rho / np.sqrt(len(cs)), rtol=1e-5)
     assert cdmimo.device_status(clear=True) == 0
-
-
-def test_precode_full_size_sampled_and_low_precision(dev):
-    n_sc, n_sym, B, U, cs = 1200, 14, 256, 16, [32] * 8
-    d = wl.downlink(wl.DEFAULT_SEED, n_sc, n_sym, B, U)
-    H32, H64 = wl.as_c64(d["H"])
-    S32, S64 = wl.as_c64(d["S"])
-    Xg = cdmimo.precode(to_dev(H32, dev), to_dev(S32, dev), cs, 3).cpu().numpy()
-    idx = np.unique(np.concatenate([np.random.default_rng(1).choice(n_sc, 48, replace=False), [0, n_sc - 1]]))
-    Xo = orc.precode(H64[idx], S64[idx], cs, 3, threads=8)
-    assert_vectors_close(Xg[idx], Xo, TOL, "full-size sample")
-    for kind, tdt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
-        qH, _, dH = wl.quantize_c16(H64[:16], kind)
-        Xg = cdmimo.precode(torch.from_numpy(qH.view(np.int16)).to(dev).view(tdt), to_dev(S32[:16], dev), cs,
-                            3).cpu().numpy()
-        Xo = orc.precode(dH, S64[:16], cs, 3)
-        assert_vectors_close(Xg, Xo, TOL, f"{kind} precode")
 
 
 def test_precode_K0_and_zero_column(dev):
