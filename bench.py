@@ -46,14 +46,16 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 #   subcarrier for the Hermitian G_c, shared by the n_sym symbols (and by both directions of a frame).
 GRAM_G = C * (U * (U + 1) // 2) * (B // C) / N_SYM
 FLOP_PER_VEC = {"residual": 2 * K * U * B * 8, "gram": 8 * (K * C * U * U + U * B + GRAM_G)}
-FLOP_PER_VEC["gram_tc"] = FLOP_PER_VEC["gram"]  # the same algorithm; its contractions run on the tensor cores
+FLOP_PER_VEC["gram_tc"] = FLOP_PER_VEC["gram_tc_phased"] = FLOP_PER_VEC["gram"]  # the same algorithm; its contractions run on the tensor cores
 FRAME_FLOP_PER_VEC = {"residual": 2 * FLOP_PER_VEC["residual"], "gram": 8 * (2 * K * C * U * U + 2 * U * B + GRAM_G)}
 KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
            "gram": ("cd_detect_gram_kernel", "cd_precode_gram_kernel"),
-           "gram_tc": ("cd_frame_tc_kernel<uplink>", "cd_frame_tc_kernel<downlink>")}
+           "gram_tc": ("cd_frame_ws_kernel<uplink>", "cd_frame_ws_kernel<downlink>"),
+           "gram_tc_phased": ("cd_frame_tc_kernel<uplink>", "cd_frame_tc_kernel<downlink>")}
 # One-kernel TDD frames by form: FP32 Gram form, and Gram form with z, G_c and x_c = H_c w on the
 # tensor cores (split-TF32 MMAs; the sweeps, K C U^2 of the flops above, stay on the FP32 pipes).
-FRAME_KERNELS = {"gram": "cd_frame_gram_kernel", "gram_tc": "cd_frame_tc_kernel"}
+FRAME_KERNELS = {"gram": "cd_frame_gram_kernel", "gram_tc": "cd_frame_ws_kernel",
+                 "gram_tc_phased": "cd_frame_tc_kernel"}
 # Algorithmic HBM bytes per vector: uplink H/14 + y + xhat; downlink H/14 + s + x; frame H/14 once.
 UL_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8
 DL_BYTES_PER_VEC = U * B * 8 / N_SYM + U * 8 + B * 8
@@ -712,7 +714,8 @@ def main():
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
     ap.add_argument("--profile", choices=["detect", "precode", "frame", "frame_f16"], default=None,
                     help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu")
-    ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc"], default="auto", help="CD evaluation form")
+    ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc", "gram_tc_phased"], default="auto",
+                    help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="chunks of the pipelined host-buffer frame in the e2e leg (0: the library's default)")
     ap.add_argument("--step", choices=["frame", "separate"], default="frame",

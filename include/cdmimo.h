@@ -85,7 +85,13 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             c64, fp16 or bf16 storage (16-bit values are exact TF32 operands: one MMA where both
  *             operands are stored values), every B_c = 16 or every B_c = 32, 8 < U <= 16,
  *             n_sym <= 16 and 2 C n_sym <= 256, and a learned block (c64) in cdmimo_detect only;
- *             elsewhere GRAM_TC is GRAM.
+ *             elsewhere GRAM_TC is GRAM.  Without a learned block, and where C n_sym <= 128 and
+ *             its buffers fit in shared memory (not for cdmimo_detect with Xc_opt / lambda_opt),
+ *             a warp-specialized kernel runs: one CTA per SM whose MMA warps form G_c and z of the
+ *             next subcarrier and x_c = H_c w of the previous one while its other warps sweep the
+ *             current one; its results equal the phased kernel's bit for bit.
+ *   GRAM_TC_PHASED  GRAM_TC always on the phased kernel (the phases of a subcarrier one after the
+ *             other, two CTAs per SM), e.g. to compare the two kernels.
  *   AUTO      GRAM where it applies, every B_c >= 2 U (so G_c + (N0/Ex) I stays well conditioned
  *             in FP32) and it needs fewer complex MACs, on the tensor cores where GRAM_TC's kernel
  *             takes the call; else RESIDUAL.
@@ -94,7 +100,8 @@ typedef enum {
     CDMIMO_FORM_AUTO = 0,
     CDMIMO_FORM_RESIDUAL = 1,
     CDMIMO_FORM_GRAM = 2,
-    CDMIMO_FORM_GRAM_TC = 3
+    CDMIMO_FORM_GRAM_TC = 3,
+    CDMIMO_FORM_GRAM_TC_PHASED = 4
 } cdmimo_form;
 
 /*

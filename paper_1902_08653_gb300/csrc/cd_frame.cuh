@@ -74,8 +74,8 @@ __device__ __forceinline__ void fuse_range(const CdPlan& pl, const DetectIO& io,
     for (int c = 0; c < C; ++c) tot += lam[c];
     const bool equal = pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f);
     const float inv = equal ? 1.f / (float)C : 1.f / tot;
-    for (int i = r; i < n_sym * U; i += nt) {
-        const int n = i / U, u = i - n * U;
+    for (int i = r; i < n_sym * U; i += nt) {  // symbols fastest: a warp's loads of x hit distinct banks
+        const int u = i / n_sym, n = i - u * n_sym;
         float2 acc = make_float2(0.f, 0.f);
         for (int c = 0; c < C; ++c) {
             const float l = equal ? inv : lam[c] * inv;

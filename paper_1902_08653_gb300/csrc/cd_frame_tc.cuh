@@ -293,6 +293,234 @@ __device__ __forceinline__ void gram_sweeps2(int U, int K, const float4* Grow, c
     }
 }
 
+// Phase A of one cluster, on one warp: G_c = H_c^H H_c (4 n-tiles: Re and Im of columns 0-7, 8-15)
+// and, for the uplink, z = H_c^H y_c (4 n-tiles: Re and Im of symbols 0-7, 8-15), over KA k-steps.
+// Hc: the cluster's UT channel rows (SROW words each); y of symbol n at element ybase + n B of Y.
+// Writes the pair-planar zero-diagonal rows Gc[UT][UT/2], the sweep coefficients Dm[u] = m_u and
+// Dp[u] = p_u^2 from the diagonal (learned: Dp[u] = ||h_u||^2 and the per-sweep table LAc[K][UT]),
+// and z of the cluster's tiles at Zc[u xs + n].  With ypre, the lane's receive samples (entry
+// 4 ks + tig of symbols 8 j + gid, as FP32) were loaded by the caller into ypre[2 ks + j].
+template <int BC, int IN, bool UL, bool LEARNED>
+__device__ __forceinline__ void tc_phase_a(const CdPlan& pl, const float* Hc, const void* Y, size_t ybase, float alpha,
+                                           float4* Gc, float* Dm, float* Dp, float2* Zc, uint32_t xs,
+                                           const cdmimo_learned* blk, float2* LAc, const float2* ypre = nullptr)
+{
+    constexpr int UT = kTcUT;
+    constexpr int SROW = (int)tc_row_words(BC, IN);
+    constexpr int SR2 = SROW / 2;
+    constexpr int KA = BC / 4;
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int U = pl.U, n_sym = pl.n_sym;
+    const float2* Hc2 = reinterpret_cast<const float2*>(Hc);
+    const float2* Yc = UL ? reinterpret_cast<const float2*>(Y) + ybase : nullptr;
+    float accG[4][4], accZ[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) accG[t][q] = accZ[t][q] = 0.f;
+    if constexpr (IN == CDMIMO_C64) {
+        // receive samples of the B fragments (entry 4 ks + tig of symbols 8 j + gid), two k-steps
+        // ahead: [stage][n-tile]
+        float2 yv[2][2];
+        auto load_y = [&](int ks, float2 (&dst)[2]) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int n = 8 * j + gid;
+                dst[j] = n < n_sym ? __ldg(Yc + (size_t)n * pl.B + 4 * ks + tig) : make_float2(0.f, 0.f);
+            }
+        };
+        if (UL && !ypre) {
+            load_y(0, yv[0]);
+            if (KA > 1) load_y(1, yv[1]);
+        }
+#pragma unroll
+        for (int ks = 0; ks < KA; ++ks) {
+            const int e = 4 * ks + tig;  // the lane's complex entry of this k-step
+            uint32_t ah[4], al[4];
+            a_frag(Hc2[gid * SR2 + e], Hc2[(gid + 8) * SR2 + e], ah, al);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                BFrag bp, br;
+                b_frags(Hc2[(8 * j + gid) * SR2 + e], bp, br);
+                mma_3xtf32(accG[j], ah, al, bp);
+                mma_3xtf32(accG[2 + j], ah, al, br);
+            }
+            if constexpr (UL) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    BFrag bp, br;
+                    b_frags(ypre ? ypre[2 * ks + j] : yv[ks & 1][j], bp, br);
+                    mma_3xtf32(accZ[j], ah, al, bp);
+                    mma_3xtf32(accZ[2 + j], ah, al, br);
+                }
+                if (!ypre && ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
+            }
+        }
+    } else {  // 16-bit storage: every operand exact in TF32, one MMA per tile
+        auto hget = [&](int row, int e) { return Elem<IN>::load_shared(Hc, (size_t)row * SROW + e); };
+#pragma unroll
+        for (int ks = 0; ks < KA; ++ks) {
+            const int e = 4 * ks + tig;
+            uint32_t ah[4];
+            a_frag_exact(hget(gid, e), hget(gid + 8, e), ah);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float2 hv = hget(8 * j + gid, e);
+                mma_exact(accG[j], ah, hv, false);
+                mma_exact(accG[2 + j], ah, hv, true);
+            }
+            if constexpr (UL) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int n = 8 * j + gid;
+                    const float2 yy = ypre ? ypre[2 * ks + j]
+                                           : (n < n_sym ? Elem<IN>::load(Y, ybase + (size_t)n * pl.B + e) : make_float2(0.f, 0.f));
+                    mma_exact(accZ[j], ah, yy, false);
+                    mma_exact(accZ[2 + j], ah, yy, true);
+                }
+            }
+        }
+    }
+    // G rows (pair-planar, zero diagonal) with m_u and p_u^2 from the diagonal; rows u = gid,
+    // gid + 8, columns v = 8 j + 2 tig, +1 (accumulator element 2 r + e)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int u = gid + 8 * r, v = 8 * j + 2 * tig;
+            float g0 = accG[j][2 * r], g1 = accG[j][2 * r + 1];
+            float i0 = accG[2 + j][2 * r], i1 = accG[2 + j][2 * r + 1];
+            if (v == u || v + 1 == u) {
+                const float e = v == u ? g0 : g1, den = e + alpha;
+                Dm[u] = (u < U && den > 0.f) ? __fdividef(1.f, den) : 0.f;
+                if constexpr (LEARNED) {
+                    Dp[u] = e;
+                    for (int t = 0; t < pl.K; ++t) {  // learned coefficients of every sweep
+                        const float tau = __ldg(&blk->tau[t]), dl = e + __ldg(&blk->gamma[t]) * alpha;
+                        LAc[t * UT + u] = dl > 0.f ? make_float2(tau * __fdividef(1.f, dl), 1.f - tau)
+                                                   : make_float2(0.f, 1.f);
+                    }
+                } else {
+                    Dp[u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
+                }
+                if (v == u) g0 = i0 = 0.f;
+                else g1 = i1 = 0.f;
+            }
+            Gc[u * (UT / 2) + (v >> 1)] = make_float4(g0, g1, i0, i1);
+        }
+    // z for tile (c, n): rows u = gid, gid + 8, symbols n = 8 j + 2 tig, +1
+    if constexpr (UL) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int u = gid + 8 * r, n = 8 * j + 2 * tig;
+                if (u < U) {
+                    float2* z = Zc + u * xs;
+                    if (n < n_sym) z[n] = make_float2(accZ[j][2 * r], accZ[2 + j][2 * r]);
+                    if (n + 1 < n_sym) z[n + 1] = make_float2(accZ[j][2 * r + 1], accZ[2 + j][2 * r + 1]);
+                }
+            }
+    }
+}
+
+// Phase C of one cluster, on one warp: x_c = H_c w for all symbols (MT x 4 tiles) from the cluster's
+// channel rows Hc and its tiles' w at Wc[u xs + n], each symbol's x_c normalized to rho_c (a zero x_c
+// stays zero) and written to out[n B + b] (out: the subcarrier's Xdl rows at the cluster's offset).
+template <int BC, int IN>
+__device__ __forceinline__ void tc_phase_c(const CdPlan& pl, const float* Hc, const float2* Wc, uint32_t xs, float2* out)
+{
+    constexpr int UT = kTcUT;
+    constexpr int SROW = (int)tc_row_words(BC, IN);
+    constexpr int SR2 = SROW / 2;
+    constexpr int MT = BC / 16;  // m-tiles (16 antennas each)
+    constexpr int KC = UT / 4;   // k-steps (4 users each)
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int U = pl.U, n_sym = pl.n_sym;
+    const float2* Hc2 = reinterpret_cast<const float2*>(Hc);
+    float acc[MT][4][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[m][t][q] = 0.f;
+    if constexpr (IN == CDMIMO_C64) {
+#pragma unroll
+        for (int ks = 0; ks < KC; ++ks) {
+            const int u = 4 * ks + tig;  // the lane's user of this k-step
+            BFrag br[2], bi[2];         // per n-tile: (Re w, -Im w) and (Im w, Re w)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int n = 8 * j + gid;
+                const float2 w = (u < U && n < n_sym) ? Wc[u * xs + n] : make_float2(0.f, 0.f);
+                b_frags(make_float2(w.y, w.x), bi[j], br[j]);  // rot(Im w, Re w) = (Re w, -Im w)
+            }
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                uint32_t ah[4], al[4];
+                a_frag(Hc2[u * SR2 + 16 * m + gid], Hc2[u * SR2 + 16 * m + gid + 8], ah, al);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    mma_3xtf32(acc[m][j], ah, al, br[j]);
+                    mma_3xtf32(acc[m][2 + j], ah, al, bi[j]);
+                }
+            }
+        }
+    } else {  // 16-bit storage: H exact in TF32, w split: two MMAs per tile
+#pragma unroll
+        for (int ks = 0; ks < KC; ++ks) {
+            const int u = 4 * ks + tig;
+            BFrag br[2], bi[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int n = 8 * j + gid;
+                const float2 w = (u < U && n < n_sym) ? Wc[u * xs + n] : make_float2(0.f, 0.f);
+                b_frags(make_float2(w.y, w.x), bi[j], br[j]);
+            }
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                uint32_t ah[4];
+                a_frag_exact(Elem<IN>::load_shared(Hc, (size_t)u * SROW + 16 * m + gid),
+                             Elem<IN>::load_shared(Hc, (size_t)u * SROW + 16 * m + gid + 8), ah);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    mma_2xtf32(acc[m][j], ah, br[j]);
+                    mma_2xtf32(acc[m][2 + j], ah, bi[j]);
+                }
+            }
+        }
+    }
+    // rows b = 16 m + gid (+8), symbols n = 8 j + 2 tig + e; norm over the cluster's antennas
+    // (the thread's rows, then the eight lanes of the same tig)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float nr = 0.f;
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float xr = acc[m][j][2 * r + e], xi = acc[m][2 + j][2 * r + e];
+                    nr = fmaf(xr, xr, fmaf(xi, xi, nr));
+                }
+            nr += __shfl_xor_sync(0xffffffffu, nr, 4);
+            nr += __shfl_xor_sync(0xffffffffu, nr, 8);
+            nr += __shfl_xor_sync(0xffffffffu, nr, 16);
+            const float sc = nr > 0.f ? pl.rho_c * rsqrtf(nr) : 0.f;
+            const int n = 8 * j + 2 * tig + e;
+            if (n < n_sym) {
+                float2* o = out + (size_t)n * pl.B;
+#pragma unroll
+                for (int m = 0; m < MT; ++m)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        o[16 * m + 8 * r + gid] = make_float2(acc[m][j][2 * r + e] * sc, acc[m][2 + j][2 * r + e] * sc);
+            }
+        }
+}
+
 template <int BC, int MODE, int IN>
 __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan pl, const FusedIO io)
 {
@@ -300,10 +528,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
     constexpr bool LEARNED = MODE == kTcDetectLearned;
     constexpr int UT = kTcUT;
     constexpr int SROW = (int)tc_row_words(BC, IN);  // 32-bit words per channel row
-    constexpr int SR2 = SROW / 2;     // c64: the same in complex entries
-    constexpr int KA = BC / 4;        // phase A k-steps (4 antennas each)
-    constexpr int MT = BC / 16;       // phase C m-tiles (16 antennas each)
-    constexpr int KC = UT / 4;        // phase C k-steps (4 users each)
     static_assert(BC == 16 || BC == 32, "cluster size 16 or 32");
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -390,124 +614,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         }
         const float* Hb = Hbuf(b);
 
-        // Phase A: per cluster (one warp), G_c (4 n-tiles: Re and Im of columns 0-7, 8-15) and, for
-        // the uplink, z (4 n-tiles: Re and Im of symbols 0-7, 8-15), over KA k-steps.
+        // Phase A: per cluster (one warp), G_c and (uplink) z.
         for (int c = warp; c < C; c += kTcThreads / 32) {
-            const float2* Hc2 = reinterpret_cast<const float2*>(Hb + c * UT * SROW);
             const ClusterTile ct = tab[c];
-            const float2* Yc = UL ? reinterpret_cast<const float2*>(d.Y) + (size_t)f * n_sym * pl.B + ct.off : nullptr;
-            float accG[4][4], accZ[4][4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) accG[t][q] = accZ[t][q] = 0.f;
-            // receive samples of the B fragments (entry 4 ks + tig of symbols 8 j + gid), two k-steps
-            // ahead: [stage][n-tile]
-            float2 yv[2][2];
-            auto load_y = [&](int ks, float2 (&dst)[2]) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int n = 8 * j + gid;
-                    dst[j] = n < n_sym ? __ldg(Yc + (size_t)n * pl.B + 4 * ks + tig) : make_float2(0.f, 0.f);
-                }
-            };
-            if constexpr (IN == CDMIMO_C64) {
-                if constexpr (UL) {
-                    load_y(0, yv[0]);
-                    if (KA > 1) load_y(1, yv[1]);
-                }
-    #pragma unroll
-                for (int ks = 0; ks < KA; ++ks) {
-                    const int e = 4 * ks + tig;  // the lane's complex entry of this k-step
-                    uint32_t ah[4], al[4];
-                    a_frag(Hc2[gid * SR2 + e], Hc2[(gid + 8) * SR2 + e], ah, al);
-    #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        BFrag bp, br;
-                        b_frags(Hc2[(8 * j + gid) * SR2 + e], bp, br);
-                        mma_3xtf32(accG[j], ah, al, bp);
-                        mma_3xtf32(accG[2 + j], ah, al, br);
-                    }
-                    if constexpr (UL) {
-    #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            BFrag bp, br;
-                            b_frags(yv[ks & 1][j], bp, br);
-                            mma_3xtf32(accZ[j], ah, al, bp);
-                            mma_3xtf32(accZ[2 + j], ah, al, br);
-                        }
-                        if (ks + 2 < KA) load_y(ks + 2, yv[ks & 1]);
-                    }
-                }
-            } else {  // 16-bit storage: every operand exact in TF32, one MMA per tile
-                const void* Hw = Hb + c * UT * SROW;
-                auto hget = [&](int row, int e) { return Elem<IN>::load_shared(Hw, (size_t)row * SROW + e); };
-                const size_t ybase = (size_t)f * n_sym * pl.B + ct.off;
-#pragma unroll
-                for (int ks = 0; ks < KA; ++ks) {
-                    const int e = 4 * ks + tig;
-                    uint32_t ah[4];
-                    a_frag_exact(hget(gid, e), hget(gid + 8, e), ah);
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const float2 hv = hget(8 * j + gid, e);
-                        mma_exact(accG[j], ah, hv, false);
-                        mma_exact(accG[2 + j], ah, hv, true);
-                    }
-                    if constexpr (UL) {
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const int n = 8 * j + gid;
-                            const float2 yy = n < n_sym ? Elem<IN>::load(d.Y, ybase + (size_t)n * pl.B + e)
-                                                        : make_float2(0.f, 0.f);
-                            mma_exact(accZ[j], ah, yy, false);
-                            mma_exact(accZ[2 + j], ah, yy, true);
-                        }
-                    }
-                }
-            }
-            // G rows (pair-planar, zero diagonal) with m_u and p_u^2 from the diagonal; rows u = gid,
-            // gid + 8, columns v = 8 j + 2 tig, +1 (accumulator element 2 r + e)
-            float4* Gc = Gs + (size_t)c * UT * (UT / 2);
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int u = gid + 8 * r, v = 8 * j + 2 * tig;
-                    float g0 = accG[j][2 * r], g1 = accG[j][2 * r + 1];
-                    float i0 = accG[2 + j][2 * r], i1 = accG[2 + j][2 * r + 1];
-                    if (v == u || v + 1 == u) {
-                        const float e = v == u ? g0 : g1, den = e + alpha;
-                        Dm[c * UT + u] = (u < U && den > 0.f) ? __fdividef(1.f, den) : 0.f;
-                        if constexpr (LEARNED) {
-                            Dp[c * UT + u] = e;
-                            for (int t = 0; t < pl.K; ++t) {  // learned coefficients of every sweep
-                                const float tau = __ldg(&blk->tau[t]), dl = e + __ldg(&blk->gamma[t]) * alpha;
-                                LA[(c * pl.K + t) * UT + u] = dl > 0.f ? make_float2(tau * __fdividef(1.f, dl), 1.f - tau)
-                                                                      : make_float2(0.f, 1.f);
-                            }
-                        } else {
-                            Dp[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
-                        }
-                        if (v == u) g0 = i0 = 0.f;
-                        else g1 = i1 = 0.f;
-                    }
-                    Gc[u * (UT / 2) + (v >> 1)] = make_float4(g0, g1, i0, i1);
-                }
-            // z for tile (c, n): rows u = gid, gid + 8, symbols n = 8 j + 2 tig, +1
-            if constexpr (UL) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const int u = gid + 8 * r, n = 8 * j + 2 * tig;
-                        if (u < U) {
-                            float2* z = Zs + u * xs + c * n_sym;
-                            if (n < n_sym) z[n] = make_float2(accZ[j][2 * r], accZ[2 + j][2 * r]);
-                            if (n + 1 < n_sym) z[n + 1] = make_float2(accZ[j][2 * r + 1], accZ[2 + j][2 * r + 1]);
-                        }
-                    }
-            }
+            tc_phase_a<BC, IN, UL, LEARNED>(pl, Hb + c * UT * SROW, d.Y, (size_t)f * n_sym * pl.B + ct.off, alpha,
+                                           Gs + (size_t)c * UT * (UT / 2), Dm + c * UT, Dp + c * UT, Zs + c * n_sym,
+                                           xs, blk, LA + c * pl.K * UT);
         }
         __syncthreads();
 
@@ -584,93 +696,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         for (int q = 0; q < kSv; ++q)
             sv[q] = (ld_s && tid + q * kTcThreads < n_s) ? s_src[tid + q * kTcThreads] : make_float2(0.f, 0.f);
 
-        for (int c = warp; DL && c < C; c += kTcThreads / 32) {
-            const float2* Hc2 = reinterpret_cast<const float2*>(Hb + c * UT * SROW);
-            const ClusterTile ct = tab[c];
-            float acc[MT][4][4];
-#pragma unroll
-            for (int m = 0; m < MT; ++m)
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[m][t][q] = 0.f;
-            if constexpr (IN == CDMIMO_C64) {
-    #pragma unroll
-                for (int ks = 0; ks < KC; ++ks) {
-                    const int u = 4 * ks + tig;  // the lane's user of this k-step
-                    BFrag br[2], bi[2];         // per n-tile: (Re w, -Im w) and (Im w, Re w)
-    #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int n = 8 * j + gid;
-                        const float2 w = (u < U && n < n_sym) ? Ws[u * xs + c * n_sym + n] : make_float2(0.f, 0.f);
-                        b_frags(make_float2(w.y, w.x), bi[j], br[j]);  // rot(Im w, Re w) = (Re w, -Im w)
-                    }
-    #pragma unroll
-                    for (int m = 0; m < MT; ++m) {
-                        uint32_t ah[4], al[4];
-                        a_frag(Hc2[u * SR2 + 16 * m + gid], Hc2[u * SR2 + 16 * m + gid + 8], ah, al);
-    #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            mma_3xtf32(acc[m][j], ah, al, br[j]);
-                            mma_3xtf32(acc[m][2 + j], ah, al, bi[j]);
-                        }
-                    }
-                }
-            } else {  // 16-bit storage: H exact in TF32, w split: two MMAs per tile
-                const void* Hw = Hb + c * UT * SROW;
-#pragma unroll
-                for (int ks = 0; ks < KC; ++ks) {
-                    const int u = 4 * ks + tig;
-                    BFrag br[2], bi[2];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int n = 8 * j + gid;
-                        const float2 w = (u < U && n < n_sym) ? Ws[u * xs + c * n_sym + n] : make_float2(0.f, 0.f);
-                        b_frags(make_float2(w.y, w.x), bi[j], br[j]);
-                    }
-#pragma unroll
-                    for (int m = 0; m < MT; ++m) {
-                        uint32_t ah[4];
-                        a_frag_exact(Elem<IN>::load_shared(Hw, (size_t)u * SROW + 16 * m + gid),
-                                     Elem<IN>::load_shared(Hw, (size_t)u * SROW + 16 * m + gid + 8), ah);
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            mma_2xtf32(acc[m][j], ah, br[j]);
-                            mma_2xtf32(acc[m][2 + j], ah, bi[j]);
-                        }
-                    }
-                }
-            }
-            // rows b = 16 m + gid (+8), symbols n = 8 j + 2 tig + e; norm over the cluster's antennas
-            // (the thread's rows, then the eight lanes of the same tig)
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    float nr = 0.f;
-#pragma unroll
-                    for (int m = 0; m < MT; ++m)
-#pragma unroll
-                        for (int r = 0; r < 2; ++r) {
-                            const float xr = acc[m][j][2 * r + e], xi = acc[m][2 + j][2 * r + e];
-                            nr = fmaf(xr, xr, fmaf(xi, xi, nr));
-                        }
-                    nr += __shfl_xor_sync(0xffffffffu, nr, 4);
-                    nr += __shfl_xor_sync(0xffffffffu, nr, 8);
-                    nr += __shfl_xor_sync(0xffffffffu, nr, 16);
-                    const float sc = nr > 0.f ? pl.rho_c * rsqrtf(nr) : 0.f;
-                    const int n = 8 * j + 2 * tig + e;
-                    if (n < n_sym) {
-                        float2* out = io.Xdl + ((size_t)f * n_sym + n) * pl.B + ct.off;
-#pragma unroll
-                        for (int m = 0; m < MT; ++m)
-#pragma unroll
-                            for (int r = 0; r < 2; ++r)
-                                out[16 * m + 8 * r + gid] =
-                                    make_float2(acc[m][j][2 * r + e] * sc, acc[m][2 + j][2 * r + e] * sc);
-                    }
-                }
-        }
+        for (int c = warp; DL && c < C; c += kTcThreads / 32)
+            tc_phase_c<BC, IN>(pl, Hb + c * UT * SROW, Ws + c * n_sym, xs, io.Xdl + (size_t)f * n_sym * pl.B + tab[c].off);
         if constexpr (LEARNED) {
             if (pl.fuse == CDMIMO_FUSE_LEARNED) {  // lambda = softmax of the MLP on ||h_u||^2 / B_c and log10 alpha
                 if (!mlp_now) {

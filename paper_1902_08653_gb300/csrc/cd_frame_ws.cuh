@@ -1,0 +1,288 @@
+// Warp-specialized tensor-core Gram-form kernel: the TDD frame (uplink detection, Algorithm 1 +
+// fusion of Sec. III, and downlink precoding, Algorithm 2 + normalization of Sec. IV-B, on one
+// channel per subcarrier), or either direction alone, with the same arithmetic as
+// cd_frame_tc_kernel (the contractions z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w as split-TF32
+// MMAs, the Gauss-Seidel sweeps in FP32; see cd_frame_tc.cuh), but with the phases of consecutive
+// subcarriers overlapped inside one CTA per SM instead of run one after the other.
+//
+// Roles.  Eight "MMA" warps own the clusters (warp c takes clusters c, c + 8, ...): for its clusters
+// a warp forms G_c and z of subcarrier s + 1 (phase A), and x_c = H_c w of subcarrier s - 1
+// (phase C), while the "sweep" warps (one lane per (cluster, symbol) tile, 4 warps at C n_sym = 112)
+// run the K sweeps of subcarrier s.  The MMA warps also fuse the uplink estimates of s - 1 and stage
+// the downlink symbols of s + 1.  A subcarrier then costs the longer of the two roles' work, not
+// their sum, and the sweep warps (the FP32 pipes) and the MMA warps (the tensor pipes) issue on the
+// same SM sub-partitions at the same time.
+//
+// Pipeline, for the CTA's subcarriers s = 0, 1, ... (f = blockIdx.x + s gridDim.x):
+//   MMA stage j:    [j >= 2] wait sweeps(j - 2); phase C and fusion of j - 2; copy the channel of j + 1
+//                   into the buffer j - 2 used;  [j < n] wait channel(j); phase A of j; signal A(j).
+//   sweep stage j:  wait A(j); sweeps of j; signal sweeps(j).
+// Buffers: the channel rows of subcarrier s live from phase A(s) to phase C(s), two stages later, so
+// there are three (s mod 3); G_c, m_u, p_u^2, z / x, w, s and the fusion weights are double
+// buffered (s mod 2).  The hand-overs between roles are mbarriers (release / acquire), each with a
+// bounded wait; within the MMA warps a named barrier separates the fusion of j - 2 (which reads every
+// cluster's x) from phase A of j (which overwrites those rows with z), and its reduction makes a
+// timed-out wait leave the loop on all MMA warps together.
+#pragma once
+#include "cd_frame_tc.cuh"
+
+namespace cdmimo {
+
+constexpr int kWsMmaWarps = 8;
+constexpr int kWsMaxThreads = 32 * kWsMmaWarps + 128;  // 8 MMA warps + up to 4 sweep warps
+
+// Shared-memory layout of cd_frame_ws_kernel (byte offsets), built on the host.  Buffer i of a
+// region starts at off + i * stride (three channel buffers, two of everything else).
+struct WsLayout {
+    unsigned off_H, st_H;      // channel rows, [C][UT][SROW] words each
+    unsigned off_G, st_G;      // [C][UT][UT/2] float4 Gram rows with zero diagonal
+    unsigned off_D, st_D;      // [2][C][UT] floats: m_u, then p_u^2
+    unsigned off_Z, st_Z;      // [UT][xs] float2: z, then each tile's x (uplink)
+    unsigned off_W, st_W;      // [UT][xs] float2: w per tile (downlink)
+    unsigned off_S, st_S;      // [U][n_sym] float2: s of the subcarrier, transposed (downlink)
+    unsigned off_lam, st_lam;  // [C] floats: fusion weights 1 / sum_u m_u
+    unsigned off_tab, off_bar, smem_bytes;  // off_bar: [8] mbarriers, then [2] floats: the uplink output
+                                            // scale of the subcarrier in each z / x buffer
+    int sweep_warps;  // warps of the sweep role (a multiple of four)
+    int slot;         // sweep lanes per cluster (8 or 16, >= n_sym): a cluster's tiles fill a quarter or
+                      // half warp, so that no quarter warp reads two clusters' Gram rows
+};
+
+// Sweep lanes per cluster for n_sym symbols (n_sym <= 16).
+__host__ __device__ constexpr int ws_slot(int n_sym) { return n_sym <= 8 ? 8 : 16; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier 1 over the MMA warps, returning the AND of every participant's `ok`.
+__device__ __forceinline__ bool mma_group_and(bool ok)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "n"(32 * kWsMmaWarps)
+        : "memory");
+    return r != 0;
+}
+
+template <int BC, int MODE, int IN>
+__global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdPlan pl, const WsLayout wl,
+                                                                       const FusedIO io)
+{
+    constexpr bool UL = MODE != kTcPrecode, DL = MODE != kTcDetect;
+    static_assert(MODE == kTcFrame || MODE == kTcDetect || MODE == kTcPrecode, "plain modes only");
+    static_assert(BC == 16 || BC == 32, "cluster size 16 or 32");
+    constexpr int UT = kTcUT;
+    constexpr int SROW = (int)tc_row_words(BC, IN);
+    constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;  // bytes per stored complex entry
+    constexpr int kMmaThreads = 32 * kWsMmaWarps;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    ClusterTile* tab = reinterpret_cast<ClusterTile*>(smem + wl.off_tab);
+    uint64_t* barH = reinterpret_cast<uint64_t*>(smem + wl.off_bar);  // [3] channel copies landed
+    uint64_t* barA = barH + 3;                                         // [2] phase A done
+    uint64_t* barS = barH + 5;                                         // [2] sweeps done
+    auto Hb = [&](int s) { return reinterpret_cast<float*>(smem + wl.off_H + (unsigned)(s % 3) * wl.st_H); };
+    auto Gb = [&](int s) { return reinterpret_cast<float4*>(smem + wl.off_G + (unsigned)(s & 1) * wl.st_G); };
+    auto Dmb = [&](int s) { return reinterpret_cast<float*>(smem + wl.off_D + (unsigned)(s & 1) * wl.st_D); };
+    auto Dpb = [&](int s) { return Dmb(s) + pl.C * UT; };
+    auto Zb = [&](int s) { return reinterpret_cast<float2*>(smem + wl.off_Z + (unsigned)(s & 1) * wl.st_Z); };
+    auto Wb = [&](int s) { return reinterpret_cast<float2*>(smem + wl.off_W + (unsigned)(s & 1) * wl.st_W); };
+    auto Sb = [&](int s) { return reinterpret_cast<float2*>(smem + wl.off_S + (unsigned)(s & 1) * wl.st_S); };
+    auto Lb = [&](int s) { return reinterpret_cast<float*>(smem + wl.off_lam + (unsigned)(s & 1) * wl.st_lam); };
+    const DetectIO& d = io.d;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int U = pl.U, C = pl.C, n_sym = pl.n_sym, n_s = n_sym * U;
+    const uint32_t xs = tc_x_stride(pl.n_tiles);
+    const int n_sw = 32 * wl.sweep_warps;
+    // this CTA's subcarriers: f(s) = blockIdx.x + s gridDim.x for s < n_mine (static schedule)
+    const int n_mine = (int)blockIdx.x < pl.n_sc ? (pl.n_sc - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto fof = [&](int s) { return (int)blockIdx.x + s * (int)gridDim.x; };
+
+    // Setup: cluster table, barriers, zero channel rows U..UT-1 of the three buffers (never copied).
+    if (tid < C) tab[tid] = pl.cl[tid];
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) mbar_init(&barH[i], (uint32_t)C);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&barA[i], (uint32_t)kMmaThreads);
+            mbar_init(&barS[i], (uint32_t)n_sw);
+        }
+        fence_proxy_async_smem();
+    }
+    for (int j = 0; j < 3; ++j) {
+        float* hb = Hb(j);
+        const int per_c = (UT - U) * SROW;
+        for (int i = tid; i < C * per_c; i += blockDim.x) {
+            const int c = i / per_c, r = i - c * per_c;
+            hb[(c * UT + U) * SROW + r] = 0.f;
+        }
+    }
+    __syncthreads();
+
+    if (warp < kWsMmaWarps) {
+        // ------------------------------------------------------------------ MMA role
+        constexpr int KA = BC / 4;
+        float* osc = reinterpret_cast<float*>(barH + 8);  // [2] uplink output scale per z / x buffer
+        // Copies of subcarrier s's channel rows for this warp's clusters into buffer s mod 3: lane 0
+        // announces the bytes on the buffer's barrier (one arrival per cluster) and copies the U rows.
+        auto issue_copy = [&](int s) {
+            const int f = fof(s);
+            const char* Hf = reinterpret_cast<const char*>(d.H) + (size_t)f * U * pl.B * eb;
+            float* dst = Hb(s);
+            if (lane == 0) {
+                for (int c = warp; c < C; c += kWsMmaWarps) {
+                    const ClusterTile ct = tab[c];
+                    mbar_arrive_expect_tx(&barH[s % 3], (uint32_t)U * ct.size * eb);
+                    fence_proxy_async_smem();
+                    for (int u = 0; u < U; ++u)
+                        bulk_g2s(dst + (size_t)(c * UT + u) * SROW, Hf + ((size_t)u * pl.B + ct.off) * eb,
+                                 (uint32_t)ct.size * eb, &barH[s % 3]);
+                }
+                if (warp == 0) {  // this subcarrier's receive samples and downlink symbols into L2
+                    if (UL) bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)f * n_sym * pl.B * eb,
+                                             (uint32_t)n_sym * pl.B * eb);
+                    if (DL) bulk_prefetch_l2(io.S + (size_t)f * n_s, (uint32_t)n_s * 8u);
+                }
+            }
+        };
+        const int gid = lane >> 2, tig = lane & 3;
+        int issued = 0, landed = 0;  // channel copies issued / waited for (subcarriers 0 .. issued - 1)
+        if (n_mine > 0) issue_copy(issued++);
+        bool ok = true;
+        for (int j = 0; ok && j < n_mine + 2; ++j) {
+            // Loads for phase A of j, issued before phase C and the fusion of j - 2 so that their
+            // latency is spent there: N0 (and scales), the downlink symbols, and the receive samples
+            // of the warp's first cluster in MMA fragment order.
+            const bool do_a = j < n_mine;
+            const int fa = do_a ? fof(j) : 0;
+            float n0 = 0.f, hs = 1.f, ys = 1.f;
+            float2 yv[UL ? 2 * KA : 1];
+            float2 sv = make_float2(0.f, 0.f);
+            if (do_a) {
+                if constexpr (UL) {
+                    n0 = __ldg(d.N0 + fa);
+                    if constexpr (IN != CDMIMO_C64) {
+                        hs = __ldg(d.h_scale + fa);
+                        ys = __ldg(d.y_scale + fa);
+                    }
+                    if (warp < C) {
+                        const size_t ybase = (size_t)fa * n_sym * pl.B + tab[warp].off;
+#pragma unroll
+                        for (int ks = 0; ks < KA; ++ks)
+#pragma unroll
+                            for (int jj = 0; jj < 2; ++jj) {
+                                const int n = 8 * jj + gid;
+                                yv[2 * ks + jj] = n < n_sym ? Elem<IN>::load(d.Y, ybase + (size_t)n * pl.B + 4 * ks + tig)
+                                                            : make_float2(0.f, 0.f);
+                            }
+                    }
+                }
+                if (DL && tid < n_s) sv = __ldg(io.S + (size_t)fa * n_s + tid);
+            }
+            if (j >= 2) {
+                const int s = j - 2, f = fof(s);
+                ok = mma_group_and(mbar_wait_bounded(&barS[s & 1], (uint32_t)(s >> 1) & 1u));
+                if (!ok) break;
+                if constexpr (DL) {
+                    for (int c = warp; c < C; c += kWsMmaWarps)
+                        tc_phase_c<BC, IN>(pl, Hb(s) + c * UT * SROW, Wb(s) + c * n_sym, xs,
+                                           io.Xdl + (size_t)f * n_sym * pl.B + tab[c].off);
+                }
+                if constexpr (UL) fuse_range(pl, d, f, Lb(s), Zb(s), xs, osc[s & 1], 0, kMmaThreads);
+            }
+            __syncwarp();
+            if (j + 1 < n_mine) issue_copy(issued++);  // into the buffer that phase C of j - 2 released
+            if (do_a) {
+                float alpha = 0.f;
+                if constexpr (UL) {
+                    alpha = n0 * pl.inv_Ex;
+                    float out_scale = 1.f;
+                    if (!(alpha >= 0.f)) {  // negative or NaN noise variance: this subcarrier's estimate is NaN
+                        if (lane == 0 && warp == 0) atomicOr(&g_dev_status, (unsigned)CDMIMO_DEV_BAD_N0);
+                        out_scale = __int_as_float(0x7fc00000);
+                        alpha = 0.f;
+                    }
+                    if constexpr (IN != CDMIMO_C64) {  // solve with alpha / a_f^2, scale x by b_f / a_f
+                        alpha = alpha / (hs * hs);
+                        out_scale = out_scale * (ys / hs);
+                    }
+                    if (tid == 0) osc[j & 1] = out_scale;  // read by the fusion of j, two stages on
+                }
+                // every MMA warp has finished reading x and the output scale (fusion of j - 2) before
+                // phase A overwrites them
+                ok = mma_group_and(mbar_wait_bounded(&barH[j % 3], (uint32_t)(j / 3) & 1u));
+                if (!ok) break;
+                ++landed;
+                for (int c = warp; c < C; c += kWsMmaWarps) {
+                    const ClusterTile ct = tab[c];
+                    float* Dm = Dmb(j) + c * UT;
+                    tc_phase_a<BC, IN, UL, false>(pl, Hb(j) + c * UT * SROW, d.Y, (size_t)fa * n_sym * pl.B + ct.off,
+                                                  alpha, Gb(j) + (size_t)c * UT * (UT / 2), Dm, Dpb(j) + c * UT,
+                                                  Zb(j) + c * n_sym, xs, nullptr, nullptr,
+                                                  (UL && c == warp) ? yv : nullptr);
+                    if constexpr (UL) {
+                        __syncwarp();
+                        if (lane == 0) {  // fusion weight 1 / sum_u m_u (a skipped column counts as infinite)
+                            float msum = 0.f;
+                            for (int u = 0; u < U; ++u) msum += Dm[u] > 0.f ? Dm[u] : __int_as_float(0x7f800000);
+                            Lb(j)[c] = 1.f / msum;
+                        }
+                    }
+                }
+                if constexpr (DL) {  // s of j, transposed to [u][n]
+                    float2* Ss = Sb(j);
+                    if (tid < n_s) Ss[(tid % U) * n_sym + tid / U] = sv;
+                    for (int i = tid + kMmaThreads; i < n_s; i += kMmaThreads)
+                        Ss[(i % U) * n_sym + i / U] = __ldg(io.S + (size_t)fa * n_s + i);
+                }
+                mbar_arrive(&barA[j & 1]);
+            }
+        }
+        // A copy still in flight (the loop left early): wait for it (bounded) before the CTA exits.
+        if (!ok && tid == 0)
+            for (int s = landed; s < issued; ++s) mbar_wait_bounded(&barH[s % 3], (uint32_t)(s / 3) & 1u, 100000000ull);
+    } else {
+        // ------------------------------------------------------------------ sweep role
+        // One lane per (cluster, symbol) tile: the uplink x (right-hand side z) and the downlink w
+        // (right-hand side s) side by side in the frame, reading the same rows of G_c.  Cluster
+        // sc = 32 / slot clusters per warp, each in its own quarter or half warp.
+        const int sw = warp - kWsMmaWarps, cpw = 32 / wl.slot;
+        const int sc = sw * cpw + lane / wl.slot, n_b = lane % wl.slot;
+        const bool active = sc < C && n_b < n_sym;
+        const int tile = sc * n_sym + n_b;
+        for (int s = 0; s < n_mine; ++s) {
+            if (!mbar_wait_bounded(&barA[s & 1], (uint32_t)(s >> 1) & 1u)) break;
+            if (active) {
+                float4 x[UT / 2], w[UT / 2];
+                const float4* Gc = Gb(s) + (size_t)sc * UT * (UT / 2);
+                const float* Dm = Dmb(s) + sc * UT;
+                const float* Dp = Dpb(s) + sc * UT;
+                if constexpr (MODE == kTcFrame)
+                    gram_sweeps2<UT>(U, pl.K, Gc, Dm, Dp, Zb(s) + tile, xs, Sb(s) + n_b, (uint32_t)n_sym, x, w);
+                else if constexpr (MODE == kTcDetect)
+                    gram_sweeps<UT>(U, pl.K, Gc, Dm, Zb(s) + tile, xs, x);
+                else
+                    gram_sweeps<UT>(U, pl.K, Gc, Dp, Sb(s) + n_b, (uint32_t)n_sym, w);
+#pragma unroll
+                for (int u = 0; u < UT; ++u) {
+                    if (u < U) {
+                        if constexpr (UL) Zb(s)[tile + u * xs] = slice_entry<UT, 1>(x, u);
+                        if constexpr (DL) Wb(s)[tile + u * xs] = slice_entry<UT, 1>(w, u);
+                    }
+                }
+            }
+            mbar_arrive(&barS[s & 1]);
+        }
+    }
+    __syncthreads();
+    sched_finish(d.sched, n_mine, pl.n_sc);
+}
+
+}  // namespace cdmimo

@@ -65,7 +65,7 @@ int validate(const cdmimo_params* p)
     if (p->fuse != CDMIMO_FUSE_EQUAL && p->fuse != CDMIMO_FUSE_COLNORM && p->fuse != CDMIMO_FUSE_LEARNED)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_RESIDUAL && p->form != CDMIMO_FORM_GRAM &&
-        p->form != CDMIMO_FORM_GRAM_TC)
+        p->form != CDMIMO_FORM_GRAM_TC && p->form != CDMIMO_FORM_GRAM_TC_PHASED)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
     if (!p->cluster_size || p->C > CDMIMO_MAX_CLUSTERS) return CDMIMO_ERR_BAD_PARTITION;
@@ -296,7 +296,10 @@ int build_gram_plan(const cdmimo_params* p, bool detect, const void* H, bool aut
 constexpr unsigned kTcTwoCtaSmem = (228u * 1024u - 2u * 1024u) / 2u;
 
 // GRAM and GRAM_TC ask for the Gram form (UNSUPPORTED where it does not apply).
-bool is_forced_gram(const cdmimo_params* p) { return p->form == CDMIMO_FORM_GRAM || p->form == CDMIMO_FORM_GRAM_TC; }
+bool is_forced_gram(const cdmimo_params* p)
+{
+    return p->form == CDMIMO_FORM_GRAM || p->form == CDMIMO_FORM_GRAM_TC || p->form == CDMIMO_FORM_GRAM_TC_PHASED;
+}
 
 // Tensor-core plan (any mode of cd_frame_tc_kernel): the Gram frame plan's cluster table and
 // tiling, with the kernel's layout: two channel buffers of C x 16 rows of 2 B_c + 8 floats, the
@@ -306,7 +309,8 @@ bool is_forced_gram(const cdmimo_params* p) { return p->form == CDMIMO_FORM_GRAM
 // form's own rules hold.  p->form must be AUTO or GRAM_TC.
 int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
 {
-    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC && p->form != CDMIMO_FORM_GRAM_TC_PHASED)
+        return CDMIMO_ERR_UNSUPPORTED;
     if (p->in_dtype != CDMIMO_C64 && p->learned) return CDMIMO_ERR_UNSUPPORTED;
     if (op != CDMIMO_OP_DETECT && (p->learned || p->fuse == CDMIMO_FUSE_LEARNED)) return CDMIMO_ERR_UNSUPPORTED;
     if (p->U <= 8 || p->U > 16 || p->n_sym > 16 || 2 * p->C * p->n_sym > 256) return CDMIMO_ERR_UNSUPPORTED;
@@ -348,6 +352,7 @@ int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
     if (pl->learned && pl->smem_bytes > kTcTwoCtaSmem) return CDMIMO_ERR_UNSUPPORTED;  // long learned schedules
     pl->threads = 256;
     pl->UT = 16;
+    pl->phased = p->form == CDMIMO_FORM_GRAM_TC_PHASED;
     return CDMIMO_OK;
 }
 
@@ -1058,7 +1063,8 @@ int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
     if (int rc = validate(p)) return rc;
     if (op != CDMIMO_OP_DETECT && op != CDMIMO_OP_PRECODE && op != CDMIMO_OP_FRAME) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
-    if (build_tc_plan(p, H, op, &pl) == CDMIMO_OK) return CDMIMO_FORM_GRAM_TC;
+    if (build_tc_plan(p, H, op, &pl) == CDMIMO_OK)
+        return p->form == CDMIMO_FORM_GRAM_TC_PHASED ? CDMIMO_FORM_GRAM_TC_PHASED : CDMIMO_FORM_GRAM_TC;
     if (op == CDMIMO_OP_FRAME) {
         if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
             build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)
@@ -1353,7 +1359,8 @@ int cdmimo_device_status(int clear)
     unsigned v = 0;
     if (module_status(&v, clear) != CDMIMO_OK || gram_detect_module_status(&v, clear) != CDMIMO_OK ||
         gram_precode_module_status(&v, clear) != CDMIMO_OK || gram_frame_module_status(&v, clear) != CDMIMO_OK ||
-        frame_tc_module_status(&v, clear) != CDMIMO_OK || frame_tc16_module_status(&v, clear) != CDMIMO_OK)
+        frame_tc_module_status(&v, clear) != CDMIMO_OK || frame_tc16_module_status(&v, clear) != CDMIMO_OK ||
+        frame_ws_module_status(&v, clear) != CDMIMO_OK || frame_ws16_module_status(&v, clear) != CDMIMO_OK)
         return CDMIMO_ERR_CUDA;
     return (int)v;
 }

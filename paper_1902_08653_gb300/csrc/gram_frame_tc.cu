@@ -1,6 +1,8 @@
 // Translation unit of the tensor-core Gram-form kernel (cd_frame_tc.cuh) for c64 storage:
 // instantiation for clusters of 16 or 32 antennas and each mode (TDD frame, uplink alone, downlink
-// alone, learned uplink), and dispatch (16-bit storage: gram_frame_tc16.cu).
+// alone, learned uplink), and dispatch of every tensor-core plan: the warp-specialized kernel
+// (gram_frame_ws.cu) where it takes the call, else this phased kernel (16-bit storage:
+// gram_frame_tc16.cu).
 #include "cd_frame_tc.cuh"
 #include "launch.h"
 
@@ -22,6 +24,10 @@ int dispatch_mode(const CdPlan& pl, const FusedIO& io, cudaStream_t s)
 
 int dispatch_frame_tc(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s)
 {
+    if (!pl.learned && !pl.phased) {  // the warp-specialized kernel where it takes the call
+        const int rc = dispatch_frame_ws(in_dtype, pl, io, op, s);
+        if (rc != CDMIMO_ERR_UNSUPPORTED) return rc;
+    }
     if (in_dtype != CDMIMO_C64) return dispatch_frame_tc16(in_dtype, pl, io, op, s);
     switch (op) {
     case CDMIMO_OP_FRAME: return dispatch_mode<kTcFrame>(pl, io, s);

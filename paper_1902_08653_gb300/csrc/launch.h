@@ -80,5 +80,12 @@ int dispatch_frame_tc(int in_dtype, const CdPlan& pl, const FusedIO& io, int op,
 int dispatch_frame_tc16(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
 int frame_tc_module_status(unsigned* v, int clear);
 int frame_tc16_module_status(unsigned* v, int clear);
+// The warp-specialized tensor-core kernel (gram_frame_ws.cu: c64, gram_frame_ws16.cu: fp16 / bf16),
+// for the same plans and ops (not learned); CDMIMO_ERR_UNSUPPORTED, with nothing launched, where it
+// does not take the call.
+int dispatch_frame_ws(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
+int dispatch_frame_ws16(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
+int frame_ws_module_status(unsigned* v, int clear);
+int frame_ws16_module_status(unsigned* v, int clear);
 
 }  // namespace cdmimo

@@ -42,6 +42,8 @@ struct CdPlan {
     int UT;           // Gram form: users padded to 8 or 16 (compile-time register count of x)
     int fuse;         // cdmimo_fuse_rule
     int learned;      // 1: learned sweeps (and possibly learned fusion) from a cdmimo_learned block
+    int phased;       // tensor-core plans: 1 = the phased kernel (cd_frame_tc_kernel) even where the
+                      // warp-specialized one (cd_frame_ws_kernel) would take the call
     float inv_Ex;
     float rho_c;      // downlink per-cluster norm rho / sqrt(C)
     // byte offsets of the shared-memory regions (channel blocks start at 0; the packed kernels keep
