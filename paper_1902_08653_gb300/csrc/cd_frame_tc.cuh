@@ -295,19 +295,18 @@ __device__ __forceinline__ void gram_sweeps2(int U, int K, const float4* Grow, c
 
 // Phase A of one cluster, on one warp: G_c = H_c^H H_c (4 n-tiles: Re and Im of columns 0-7, 8-15)
 // and, for the uplink, z = H_c^H y_c (4 n-tiles: Re and Im of symbols 0-7, 8-15), over KA k-steps.
-// Hc: the cluster's UT channel rows (SROW words each); y of symbol n at element ybase + n B of Y.
+// Hc: the cluster's UT channel rows, srow 32-bit words apart; y of symbol n at element ybase + n B of Y.
 // Writes the pair-planar zero-diagonal rows Gc[UT][UT/2], the sweep coefficients Dm[u] = m_u and
 // Dp[u] = p_u^2 from the diagonal (learned: Dp[u] = ||h_u||^2 and the per-sweep table LAc[K][UT]),
 // and z of the cluster's tiles at Zc[u xs + n].  With ypre, the lane's receive samples (entry
 // 4 ks + tig of symbols 8 j + gid, as FP32) were loaded by the caller into ypre[2 ks + j].
 template <int BC, int IN, bool UL, bool LEARNED>
-__device__ __forceinline__ void tc_phase_a(const CdPlan& pl, const float* Hc, const void* Y, size_t ybase, float alpha,
-                                           float4* Gc, float* Dm, float* Dp, float2* Zc, uint32_t xs,
+__device__ __forceinline__ void tc_phase_a(const CdPlan& pl, const float* Hc, int srow, const void* Y, size_t ybase,
+                                           float alpha, float4* Gc, float* Dm, float* Dp, float2* Zc, uint32_t xs,
                                            const cdmimo_learned* blk, float2* LAc, const float2* ypre = nullptr)
 {
     constexpr int UT = kTcUT;
-    constexpr int SROW = (int)tc_row_words(BC, IN);
-    constexpr int SR2 = SROW / 2;
+    const int SROW = srow, SR2 = srow / 2;
     constexpr int KA = BC / 4;
     const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
     const int U = pl.U, n_sym = pl.n_sym;
@@ -425,14 +424,15 @@ __device__ __forceinline__ void tc_phase_a(const CdPlan& pl, const float* Hc, co
 }
 
 // Phase C of one cluster, on one warp: x_c = H_c w for all symbols (MT x 4 tiles) from the cluster's
-// channel rows Hc and its tiles' w at Wc[u xs + n], each symbol's x_c normalized to rho_c (a zero x_c
-// stays zero) and written to out[n B + b] (out: the subcarrier's Xdl rows at the cluster's offset).
+// channel rows Hc (srow words apart) and its tiles' w at Wc[u xs + n], each symbol's x_c normalized to
+// rho_c (a zero x_c stays zero) and written to out[n B + b] (out: the subcarrier's Xdl rows at the
+// cluster's offset).
 template <int BC, int IN>
-__device__ __forceinline__ void tc_phase_c(const CdPlan& pl, const float* Hc, const float2* Wc, uint32_t xs, float2* out)
+__device__ __forceinline__ void tc_phase_c(const CdPlan& pl, const float* Hc, int srow, const float2* Wc, uint32_t xs,
+                                           float2* out)
 {
     constexpr int UT = kTcUT;
-    constexpr int SROW = (int)tc_row_words(BC, IN);
-    constexpr int SR2 = SROW / 2;
+    const int SROW = srow, SR2 = srow / 2;
     constexpr int MT = BC / 16;  // m-tiles (16 antennas each)
     constexpr int KC = UT / 4;   // k-steps (4 users each)
     const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
         // Phase A: per cluster (one warp), G_c and (uplink) z.
         for (int c = warp; c < C; c += kTcThreads / 32) {
             const ClusterTile ct = tab[c];
-            tc_phase_a<BC, IN, UL, LEARNED>(pl, Hb + c * UT * SROW, d.Y, (size_t)f * n_sym * pl.B + ct.off, alpha,
+            tc_phase_a<BC, IN, UL, LEARNED>(pl, Hb + c * UT * SROW, SROW, d.Y, (size_t)f * n_sym * pl.B + ct.off, alpha,
                                            Gs + (size_t)c * UT * (UT / 2), Dm + c * UT, Dp + c * UT, Zs + c * n_sym,
                                            xs, blk, LA + c * pl.K * UT);
         }
@@ -697,7 +697,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
             sv[q] = (ld_s && tid + q * kTcThreads < n_s) ? s_src[tid + q * kTcThreads] : make_float2(0.f, 0.f);
 
         for (int c = warp; DL && c < C; c += kTcThreads / 32)
-            tc_phase_c<BC, IN>(pl, Hb + c * UT * SROW, Ws + c * n_sym, xs, io.Xdl + (size_t)f * n_sym * pl.B + tab[c].off);
+            tc_phase_c<BC, IN>(pl, Hb + c * UT * SROW, SROW, Ws + c * n_sym, xs,
+                               io.Xdl + (size_t)f * n_sym * pl.B + tab[c].off);
         if constexpr (LEARNED) {
             if (pl.fuse == CDMIMO_FUSE_LEARNED) {  // lambda = softmax of the MLP on ||h_u||^2 / B_c and log10 alpha
                 if (!mlp_now) {

@@ -34,7 +34,7 @@ constexpr int kWsMaxThreads = 32 * kWsMmaWarps + 128;  // 8 MMA warps + up to 4 
 // Shared-memory layout of cd_frame_ws_kernel (byte offsets), built on the host.  Buffer i of a
 // region starts at off + i * stride (three channel buffers, two of everything else).
 struct WsLayout {
-    unsigned off_H, st_H;      // channel rows, [C][UT][SROW] words each
+    unsigned off_H, st_H;      // channel rows [UT][srow] words: user u's B antennas, all clusters
     unsigned off_G, st_G;      // [C][UT][UT/2] float4 Gram rows with zero diagonal
     unsigned off_D, st_D;      // [2][C][UT] floats: m_u, then p_u^2
     unsigned off_Z, st_Z;      // [UT][xs] float2: z, then each tile's x (uplink)
@@ -46,7 +46,19 @@ struct WsLayout {
     int sweep_warps;  // warps of the sweep role (a multiple of four)
     int slot;         // sweep lanes per cluster (8 or 16, >= n_sym): a cluster's tiles fill a quarter or
                       // half warp, so that no quarter warp reads two clusters' Gram rows
+    int srow;         // 32-bit words per channel row (ws_row_words)
 };
+
+// Words per channel row of the warp-specialized kernel: the row's B entries (c64: two words each,
+// 16-bit: one) padded to 8 (c64) or 4 (16-bit) mod 32, the residue of tc_row_words, so that the
+// fragment loads of phases A and C keep the phased kernel's bank pattern.  Each row arrives by one
+// bulk copy of its B entries (16 rows per subcarrier rather than one per cluster and user: the copy
+// engine's cost per instruction made 8 U small copies a stage's largest stall).
+__host__ __device__ constexpr unsigned ws_row_words(int B, int in_dtype)
+{
+    return in_dtype == CDMIMO_C64 ? 2u * (unsigned)B + ((8u - 2u * (unsigned)B % 32u) % 32u)
+                                  : (unsigned)B + ((36u - (unsigned)B % 32u) % 32u);
+}
 
 // Sweep lanes per cluster for n_sym symbols (n_sym <= 16).
 __host__ __device__ constexpr int ws_slot(int n_sym) { return n_sym <= 8 ? 8 : 16; }
@@ -79,8 +91,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
     static_assert(MODE == kTcFrame || MODE == kTcDetect || MODE == kTcPrecode, "plain modes only");
     static_assert(BC == 16 || BC == 32, "cluster size 16 or 32");
     constexpr int UT = kTcUT;
-    constexpr int SROW = (int)tc_row_words(BC, IN);
+    const int SROW = wl.srow;
     constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;  // bytes per stored complex entry
+    constexpr int ew = IN == CDMIMO_C64 ? 2 : 1;         // 32-bit words per stored complex entry
     constexpr int kMmaThreads = 32 * kWsMmaWarps;
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -109,7 +122,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
     // Setup: cluster table, barriers, zero channel rows U..UT-1 of the three buffers (never copied).
     if (tid < C) tab[tid] = pl.cl[tid];
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) mbar_init(&barH[i], (uint32_t)C);
+        for (int i = 0; i < 3; ++i) mbar_init(&barH[i], (uint32_t)kWsMmaWarps);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&barA[i], (uint32_t)kMmaThreads);
             mbar_init(&barS[i], (uint32_t)n_sw);
@@ -117,12 +130,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         fence_proxy_async_smem();
     }
     for (int j = 0; j < 3; ++j) {
-        float* hb = Hb(j);
-        const int per_c = (UT - U) * SROW;
-        for (int i = tid; i < C * per_c; i += blockDim.x) {
-            const int c = i / per_c, r = i - c * per_c;
-            hb[(c * UT + U) * SROW + r] = 0.f;
-        }
+        float* hb = Hb(j) + U * SROW;
+        for (int i = tid; i < (UT - U) * SROW; i += blockDim.x) hb[i] = 0.f;
     }
     __syncthreads();
 
@@ -130,21 +139,19 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         // ------------------------------------------------------------------ MMA role
         constexpr int KA = BC / 4;
         float* osc = reinterpret_cast<float*>(barH + 8);  // [2] uplink output scale per z / x buffer
-        // Copies of subcarrier s's channel rows for this warp's clusters into buffer s mod 3: lane 0
-        // announces the bytes on the buffer's barrier (one arrival per cluster) and copies the U rows.
+        // Copies of subcarrier s's channel rows into buffer s mod 3: warp w copies users w, w + 8, ...
+        // (whole rows of B entries); its lane 0 announces their bytes on the buffer's barrier (one
+        // arrival per MMA warp).
         auto issue_copy = [&](int s) {
             const int f = fof(s);
             const char* Hf = reinterpret_cast<const char*>(d.H) + (size_t)f * U * pl.B * eb;
             float* dst = Hb(s);
             if (lane == 0) {
-                for (int c = warp; c < C; c += kWsMmaWarps) {
-                    const ClusterTile ct = tab[c];
-                    mbar_arrive_expect_tx(&barH[s % 3], (uint32_t)U * ct.size * eb);
-                    fence_proxy_async_smem();
-                    for (int u = 0; u < U; ++u)
-                        bulk_g2s(dst + (size_t)(c * UT + u) * SROW, Hf + ((size_t)u * pl.B + ct.off) * eb,
-                                 (uint32_t)ct.size * eb, &barH[s % 3]);
-                }
+                const int rows = warp < U ? (U - 1 - warp) / kWsMmaWarps + 1 : 0;
+                mbar_arrive_expect_tx(&barH[s % 3], (uint32_t)rows * pl.B * eb);
+                fence_proxy_async_smem();
+                for (int u = warp; u < U; u += kWsMmaWarps)
+                    bulk_g2s(dst + (size_t)u * SROW, Hf + (size_t)u * pl.B * eb, (uint32_t)pl.B * eb, &barH[s % 3]);
                 if (warp == 0) {  // this subcarrier's receive samples and downlink symbols into L2
                     if (UL) bulk_prefetch_l2(static_cast<const char*>(d.Y) + (size_t)f * n_sym * pl.B * eb,
                                              (uint32_t)n_sym * pl.B * eb);
@@ -159,11 +166,25 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         for (int j = 0; ok && j < n_mine + 2; ++j) {
             // Loads for phase A of j, issued before phase C and the fusion of j - 2 so that their
             // latency is spent there: N0 (and scales), the downlink symbols, and the receive samples
-            // of the warp's first cluster in MMA fragment order.
+            // of the warp's first cluster for the first KP k-steps, in MMA fragment order (the rest
+            // are loaded as phase A starts; holding all of them through phase C costs registers).
+            constexpr int KP = KA / 2;
             const bool do_a = j < n_mine;
             const int fa = do_a ? fof(j) : 0;
             float n0 = 0.f, hs = 1.f, ys = 1.f;
             float2 yv[UL ? 2 * KA : 1];
+            const size_t ybase0 = (size_t)fa * n_sym * pl.B + (warp < C ? tab[warp].off : 0);
+            auto load_yv = [&](int k0, int k1) {
+#pragma unroll
+                for (int ks = 0; ks < KA; ++ks)
+#pragma unroll
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int n = 8 * jj + gid;
+                        if (ks >= k0 && ks < k1)
+                            yv[2 * ks + jj] = n < n_sym ? Elem<IN>::load(d.Y, ybase0 + (size_t)n * pl.B + 4 * ks + tig)
+                                                        : make_float2(0.f, 0.f);
+                    }
+            };
             float2 sv = make_float2(0.f, 0.f);
             if (do_a) {
                 if constexpr (UL) {
@@ -172,17 +193,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                         hs = __ldg(d.h_scale + fa);
                         ys = __ldg(d.y_scale + fa);
                     }
-                    if (warp < C) {
-                        const size_t ybase = (size_t)fa * n_sym * pl.B + tab[warp].off;
-#pragma unroll
-                        for (int ks = 0; ks < KA; ++ks)
-#pragma unroll
-                            for (int jj = 0; jj < 2; ++jj) {
-                                const int n = 8 * jj + gid;
-                                yv[2 * ks + jj] = n < n_sym ? Elem<IN>::load(d.Y, ybase + (size_t)n * pl.B + 4 * ks + tig)
-                                                            : make_float2(0.f, 0.f);
-                            }
-                    }
+                    if (warp < C) load_yv(0, KP);
                 }
                 if (DL && tid < n_s) sv = __ldg(io.S + (size_t)fa * n_s + tid);
             }
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                 if (!ok) break;
                 if constexpr (DL) {
                     for (int c = warp; c < C; c += kWsMmaWarps)
-                        tc_phase_c<BC, IN>(pl, Hb(s) + c * UT * SROW, Wb(s) + c * n_sym, xs,
+                        tc_phase_c<BC, IN>(pl, Hb(s) + tab[c].off * ew, SROW, Wb(s) + c * n_sym, xs,
                                            io.Xdl + (size_t)f * n_sym * pl.B + tab[c].off);
                 }
                 if constexpr (UL) fuse_range(pl, d, f, Lb(s), Zb(s), xs, osc[s & 1], 0, kMmaThreads);
@@ -220,10 +231,11 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                 ok = mma_group_and(mbar_wait_bounded(&barH[j % 3], (uint32_t)(j / 3) & 1u));
                 if (!ok) break;
                 ++landed;
+                if (UL && warp < C) load_yv(KP, KA);
                 for (int c = warp; c < C; c += kWsMmaWarps) {
                     const ClusterTile ct = tab[c];
                     float* Dm = Dmb(j) + c * UT;
-                    tc_phase_a<BC, IN, UL, false>(pl, Hb(j) + c * UT * SROW, d.Y, (size_t)fa * n_sym * pl.B + ct.off,
+                    tc_phase_a<BC, IN, UL, false>(pl, Hb(j) + ct.off * ew, SROW, d.Y, (size_t)fa * n_sym * pl.B + ct.off,
                                                   alpha, Gb(j) + (size_t)c * UT * (UT / 2), Dm, Dpb(j) + c * UT,
                                                   Zb(j) + c * n_sym, xs, nullptr, nullptr,
                                                   (UL && c == warp) ? yv : nullptr);

@@ -25,8 +25,8 @@ inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl)
     if (warps * 32 + 32 * kWsMmaWarps > kWsMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
     const bool ul = op != CDMIMO_OP_PRECODE, dl = op != CDMIMO_OP_DETECT;
     const unsigned C = pl.C, U = pl.U, UT = kTcUT, n_sym = pl.n_sym, xs = tc_x_stride(pl.n_tiles);
-    const int Bc = pl.cl[0].size;
-    const unsigned hbytes = ws_align(C * UT * tc_row_words(Bc, in_dtype) * 4u, 128u);
+    const unsigned srow = ws_row_words(pl.B, in_dtype);
+    const unsigned hbytes = ws_align(UT * srow * 4u, 128u);
     unsigned o = 0;
     auto region = [&](unsigned& off, unsigned& st, unsigned bytes, unsigned align, int n) {
         st = ws_align(bytes, align);
@@ -47,6 +47,7 @@ inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl)
     wl->smem_bytes = o;
     wl->sweep_warps = warps;
     wl->slot = slot;
+    wl->srow = (int)srow;
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
