@@ -13,8 +13,10 @@ and precoded) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--step frame|separate]
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
-workload (the oracle is the reference implementation of this path).  Under torchrun (N > 1) every
+--impl reference times the FP64 CPU oracle on the host cores on the same workload, the whole batch
+every step (the oracle is the reference implementation of this path).  The default line also
+carries a per-pipe roofline of the frame kernel (pipe rates probed on the same GPU) and condensed
+runs of configurations 1, 3, 4 and 5 (--no-configs leaves them out).  Under torchrun (N > 1) every
 rank runs its own batch (weak scaling, no collective on the data path) and rank 0 prints one JSON
 line with the max-over-ranks time.
 """
@@ -56,6 +58,18 @@ KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
 # tensor cores (split-TF32 MMAs; the sweeps, K C U^2 of the flops above, stay on the FP32 pipes).
 FRAME_KERNELS = {"gram": "cd_frame_gram_kernel", "gram_tc": "cd_frame_ws_kernel",
                  "gram_tc_phased": "cd_frame_tc_kernel"}
+# Per-pipe work of the one-kernel frame (Gram form on the tensor cores), per frame vector:
+#   FP32 pipes: the Gauss-Seidel sweeps, K U^2 complex MACs per cluster and direction;
+#   tensor pipes: z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w, algorithmically the rest of
+#   FRAME_FLOP_PER_VEC["gram"]; executed as split-TF32 mma.sync m16n8k8 tiles, 288 per cluster and
+#   subcarrier at B_c = 32 (phase A: 8 k-steps x 24, phase C: 4 k-steps x 24; 3 MMAs per product,
+#   16-row user tiles and 16-column symbol tiles), 2048 flop each.
+SWEEP_FLOP_PER_VEC = 2 * 8 * K * C * U * U
+CONTRACTION_FLOP_PER_VEC = FRAME_FLOP_PER_VEC["gram"] - SWEEP_FLOP_PER_VEC
+MMA_PER_CLUSTER_SUBCARRIER = 288
+MMA_FLOP_PER_VEC = C * MMA_PER_CLUSTER_SUBCARRIER * 2048 / N_SYM
+# tcgen05 TF32 dense rate implied by the measured cuBLAS bf16 rate and the nominal tf32 / bf16 ratio
+TF32_PER_BF16_NOMINAL = 1.1 / 2.25
 # Algorithmic HBM bytes per vector: uplink H/14 + y + xhat; downlink H/14 + s + x; frame H/14 once.
 UL_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8
 DL_BYTES_PER_VEC = U * B * 8 / N_SYM + U * 8 + B * 8
@@ -66,8 +80,7 @@ FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
 # L2 when a kernel ends are written back after it, outside the launch.
 NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.806592e6 + 0.621568e6,
                "cd_precode_gram_kernel": 41.539072e6 + 0.377088e6,
-               "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6,
-               "cd_frame_tc_kernel": 75.996672e6 + 4.606464e6}
+               "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6}
 
 WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
             "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
@@ -84,6 +97,37 @@ def load_peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def load_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def measure_pipes(dev, stream):
+    """Throughput of the packed-FP32 FMA and TF32 mma.sync pipes on this GPU (cdmimo_pipe_probe:
+    eight independent chains per thread or warp on every SM), best of five launches, TFLOP/s."""
+    import torch
+
+    from paper_1902_08653_gb300 import cdmimo
+
+    sink = torch.empty(cdmimo.pipe_probe_sink_floats(), dtype=torch.float32, device=dev)
+    out = {}
+    for name, kind, iters in (("ffma2", cdmimo.PROBE_FFMA2, 4096), ("mma_tf32", cdmimo.PROBE_MMA_TF32, 1024)):
+        cdmimo.pipe_probe(kind, 64, sink, stream)
+        best = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = cdmimo.pipe_probe(kind, iters, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name] = best
+    return out
 
 
 class ClockSampler:
@@ -156,6 +200,14 @@ def whole_job_value(vectors_per_rank, world, max_ms):
 def rank_seed(rank):
     """Each rank's batch seed (independent synthetic batches, the same shape)."""
     return 20190222 + rank
+
+
+def bench_config(step, world):
+    """The line's workload description, the same for the CUDA arm and the reference arm."""
+    return {"workload": WORKLOAD if step == "frame" else WORKLOAD_SEPARATE, "step": step, "n_sc": N_SC,
+            "n_sym": N_SYM, "B": B, "C": C, "B_c": B // C, "U": U, "K": K, "fusion": "colnorm", "qam": M,
+            "l2": "GPU arm: flushed between timed steps (256 MB write, untimed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def make_inputs(seed):
@@ -332,6 +384,45 @@ def run_cuda(args, rank, world, local_rank):
         dom = max(kernels, key=lambda k: k["ms"])
         dom_bytes = (UL_BYTES_PER_VEC if dom is kernels[0] else DL_BYTES_PER_VEC) * vec_step
     achieved = dom["flop_per_vector"] * vec_step / (dom["ms"] * 1e-3) / 1e12
+    pipes = measure_pipes(dev, stream)
+    roof = {"bound": "alu", "kernel": dom["kernel"], "flop_per_vector": dom["flop_per_vector"],
+            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "hbm": {"achieved_gbs": dom_bytes / (dom["ms"] * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                    "frac": dom_bytes / (dom["ms"] * 1e-3) / 1e9 / hbm_peak, "peak_source": peak_src},
+            "traffic": NCU_TRAFFIC.get(dom["kernel"]), "pipe_probe_tflops": pipes}
+    if frame and dom["kernel"] in ("cd_frame_ws_kernel", "cd_frame_tc_kernel"):
+        # The tensor-core frame, pipe by pipe: the sweeps (FP32) bind; contractions and bytes follow.
+        t_s = dom["ms"] * 1e-3
+        bf16, bf16_src = load_bf16_peak()
+        sw = SWEEP_FLOP_PER_VEC * vec_step
+        mma = MMA_FLOP_PER_VEC * vec_step
+        roof.update({"flop_per_vector": SWEEP_FLOP_PER_VEC, "achieved": sw / t_s / 1e12,
+                     "frac": sw / t_s / 1e12 / FP32_PEAK_TFLOPS,
+                     "what": "FP32 pipes: the Gauss-Seidel sweeps' flops (K U^2 complex MACs per cluster and "
+                             "direction) against the FP32 ALU peak; the other pipes are in 'pipes'"})
+        roof["pipes"] = {
+            "fp32_sweeps": {"flop_per_vector": SWEEP_FLOP_PER_VEC, "achieved_tflops": sw / t_s / 1e12,
+                            "peak_derived_tflops": FP32_PEAK_TFLOPS, "frac_derived": sw / t_s / 1e12 / FP32_PEAK_TFLOPS,
+                            "peak_probe_tflops": pipes["ffma2"], "frac_probe": sw / t_s / 1e12 / pipes["ffma2"],
+                            "t_min_us": sw / (pipes["ffma2"] * 1e12) * 1e6},
+            "tensor_mma_sync_tf32": {"flop_per_vector_algorithmic": CONTRACTION_FLOP_PER_VEC,
+                                     "mma_flop_per_vector_executed": MMA_FLOP_PER_VEC,
+                                     "achieved_tflops_executed": mma / t_s / 1e12,
+                                     "peak_probe_tflops": pipes["mma_tf32"],
+                                     "frac_probe": mma / t_s / 1e12 / pipes["mma_tf32"],
+                                     "t_min_us": mma / (pipes["mma_tf32"] * 1e12) * 1e6,
+                                     "tcgen05_tf32_tflops_from_bf16": bf16 * TF32_PER_BF16_NOMINAL,
+                                     "frac_vs_tcgen05_tf32": mma / t_s / 1e12 / (bf16 * TF32_PER_BF16_NOMINAL),
+                                     "peak_source": f"probe (mma.sync); tcgen05 figure = {bf16_src} bf16 x 1.1/2.25"},
+            "hbm": {"bytes_per_vector": FRAME_BYTES_PER_VEC, "achieved_gbs": dom_bytes / t_s / 1e9,
+                    "peak_gbs": hbm_peak, "frac": dom_bytes / t_s / 1e9 / hbm_peak,
+                    "t_min_us": dom_bytes / (hbm_peak * 1e9) * 1e6, "peak_source": peak_src},
+        }
+        roof["l2_writeback_note"] = (
+            "the outputs (%.1f MB) can still be in L2 at the end event; their write-back (at most %.1f us of HBM "
+            "time) then falls into the untimed L2 flush" % (vec_step * (U + B) * 8 / 1e6,
+                                                             vec_step * (U + B) * 8 / (hbm_peak * 1e9) * 1e6))
     line = {
         "metric": METRIC,
         "value": value,
@@ -347,19 +438,10 @@ def run_cuda(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded i.i.d. Rayleigh, 16-QAM, AWGN)",
-        "config": {"workload": WORKLOAD if frame else WORKLOAD_SEPARATE, "step": args.step, "n_sc": N_SC,
-                   "n_sym": N_SYM, "B": B, "C": C, "B_c": B // C, "U": U, "K": K, "fusion": "colnorm", "qam": M,
-                   "l2": "flushed between timed steps (256 MB write, untimed)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": bench_config(args.step, world),
         "gbps": value * BITS / 1e9,
         "kernels": kernels,
-        "roofline": {"bound": "alu", "kernel": dom["kernel"], "flop_per_vector": dom["flop_per_vector"],
-                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                     "hbm": {"achieved_gbs": dom_bytes / (dom["ms"] * 1e-3) / 1e9, "peak_gbs": hbm_peak,
-                             "frac": dom_bytes / (dom["ms"] * 1e-3) / 1e9 / hbm_peak, "peak_source": peak_src},
-                     "traffic": NCU_TRAFFIC.get(dom["kernel"])},
+        "roofline": roof,
         "mse_vs_mmse": mse,
         "ber": ber,
         "e2e": {"value": whole_job_value(vec_step, world, e2e_ms), "unit": "vectors/s", "ms_per_step": e2e_ms,
@@ -377,6 +459,8 @@ def run_cuda(args, rank, world, local_rank):
         st = cpu_baseline(up, dl, frame, min_seconds=3.0, threads=1)
         cb["single_thread"] = {"value": st["value"], "unit": st["unit"], "cores": 1, "sample": st["sample"]}
     line["cpu_baseline"] = cb
+    if world == 1 and frame and args.form == "auto" and not args.no_configs:
+        line["configs"] = config_summaries(args, dev)
     return line
 
 
@@ -464,25 +548,21 @@ def run_reference(args):
     oracle.build()
     up, dl = make_inputs(20190222)
     threads = os.cpu_count() or 1
-    n_sub = 120
     for _ in range(args.warmup):
         oracle.detect(up["H"][:8], up["Y"][:8], up["N0"][:8], CS, K, threads=threads)
     times = []
-    for i in range(args.steps):
-        f0 = (i * n_sub) % N_SC
-        sl = slice(f0, f0 + n_sub)
+    for i in range(args.steps):  # every step is the whole batch, as on the GPU
         t0 = time.perf_counter()
-        oracle.detect(up["H"][sl], up["Y"][sl], up["N0"][sl], CS, K, threads=threads)
-        oracle.precode((up if args.step == "frame" else dl)["H"][sl], dl["S"][sl], CS, K, threads=threads)
+        oracle.detect(up["H"], up["Y"], up["N0"], CS, K, threads=threads)
+        oracle.precode((up if args.step == "frame" else dl)["H"], dl["S"], CS, K, threads=threads)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
-    value = n_sub * N_SYM / (ms * 1e-3)
-    sample = f"{n_sub} subcarriers x {N_SYM} symbols per step (UL detect + DL precode), FP64 C oracle"
+    value = N_SC * N_SYM / (ms * 1e-3)
+    sample = f"the full batch ({N_SC} subcarriers x {N_SYM} symbols, UL detect + DL precode) per step, FP64 C oracle"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded i.i.d. Rayleigh)",
-            "config": {"workload": WORKLOAD if args.step == "frame" else WORKLOAD_SEPARATE, "step": args.step,
-                       "n_sc": N_SC, "n_sym": N_SYM, "B": B, "C": C, "U": U, "K": K},
+            "config": bench_config(args.step, 1),
             "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -555,8 +635,18 @@ def run_config3(args, dev):
                        torch.from_numpy(qY.view(np.int16)).to(dev).view(tdt),
                        torch.from_numpy(sH).to(dev), torch.from_numpy(sY).to(dev))
     X = torch.empty((N_SC, N_SYM, Uc), dtype=torch.complex64, device=dev)
-    res, ref = {}, {}
+    # the FP64 oracle (benchmark-side check only) on the exact values each storage delivers, and on
+    # the unquantized channel: the per-vector error of the GPU path against it
+    import oracle
+
+    oracle.build()
+    exact = {"c64": (wl.as_c64(up["H"])[1], wl.as_c64(up["Y"])[1])}
+    for kind in ("f16", "bf16"):
+        exact[kind] = (wl.quantize_c16(up["H"], kind)[2], wl.quantize_c16(up["Y"], kind)[2])
+    thr = os.cpu_count() or 1
+    res, ref, orc_unq = {}, {}, {}
     for K3 in (3, 5):
+        orc_unq[K3] = oracle.detect(exact["c64"][0], exact["c64"][1], up["N0"], CS, K3, threads=thr)[0]
         for kind, (Ht, Yt, sH, sY) in store.items():
             fn = lambda: cdmimo.detect(Ht, Yt, N0, CS, K3, h_scale=sH, y_scale=sY, out=X)
             med, _ = time_device(fn, args.steps, args.warmup, dev)
@@ -565,11 +655,17 @@ def run_config3(args, dev):
             if kind == "c64":
                 ref[K3] = xh
             rel = np.linalg.norm(xh - ref[K3], axis=-1) / np.linalg.norm(ref[K3], axis=-1)
+            xo = oracle.detect(exact[kind][0], exact[kind][1], up["N0"], CS, K3, threads=thr)[0]
+            e_kernel = np.linalg.norm(xh - xo, axis=-1) / np.linalg.norm(xo, axis=-1)
+            e_total = np.linalg.norm(xh - orc_unq[K3], axis=-1) / np.linalg.norm(orc_unq[K3], axis=-1)
             mse, ber = mse_vs_mmse_U(up, xh, Uc, M3)
             in_bytes = (Ht.numel() * Ht.element_size() + Yt.numel() * Yt.element_size()) / (N_SC * N_SYM)
             res[f"{kind}_K{K3}"] = {"ms": med, "vectors_per_s": N_SC * N_SYM / (med * 1e-3),
                                     "gbps": N_SC * N_SYM * Uc * 6 / (med * 1e-3) / 1e9,
                                     "input_bytes_per_vector": in_bytes,
+                                    "rel_l2_vs_oracle_same_inputs_max": float(e_kernel.max()),
+                                    "rel_l2_vs_oracle_unquantized_median": float(np.median(e_total)),
+                                    "rel_l2_vs_oracle_unquantized_max": float(e_total.max()),
                                     "rel_l2_vs_c64_median": float(np.median(rel)), "rel_l2_vs_c64_max": float(rel.max()),
                                     "mse_vs_mmse_mean": float(np.mean(list(mse.values()))), "ber": ber}
     best = res["f16_K3"]
@@ -671,6 +767,39 @@ def run_config5(args, dev):
                      training={k: v for k, v in info.items() if k != "loss"}, gpu_launches=1 * args.steps)
 
 
+def config_summaries(args, dev):
+    """Configurations 1, 3, 4 and 5 on the benchmark's GPU (short runs), condensed for the default
+    line: latency (1), storage precision at U = 32 (3), batched uneven blocks (4), learned vs plain
+    CD (5)."""
+    import copy
+
+    sub = copy.copy(args)
+    sub.steps, sub.warmup = max(10, min(args.steps, 30)), 3
+    out = {}
+    c1 = run_config1(sub, dev)
+    out["1"] = {"workload": c1["config"]["workload"], "latency_us": c1["latency_us"], "vectors_per_s": c1["value"]}
+    c3 = run_config3(sub, dev)
+    v = c3["variants"]
+    out["3"] = {"workload": c3["config"]["workload"],
+                "variants": {k: {q: x[q] for q in ("ms", "vectors_per_s", "mse_vs_mmse_mean",
+                                                    "rel_l2_vs_oracle_same_inputs_max",
+                                                    "rel_l2_vs_oracle_unquantized_median")} for k, x in v.items()},
+                "reduced_precision_faster_than_c64": {f"K{k}": {kind: v[f"{kind}_K{k}"]["ms"] < v[f"c64_K{k}"]["ms"]
+                                                             for kind in ("f16", "bf16")} for k in (3, 5)}}
+    c4 = run_config4(sub, dev)
+    out["4"] = {"workload": c4["config"]["workload"], "ms": c4["ms_per_step"], "vectors_per_s": c4["value"],
+                "fp32_frac": c4["roofline"]["frac"], "autotune_chosen": c4["autotune"]["chosen"],
+                "speedup_over_separate_launches": c4["separate_launches"]["speedup_of_one_launch"]}
+    c5 = run_config5(sub, dev)
+    v5 = c5["variants"]
+    out["5"] = {"workload": c5["config"]["workload"],
+                "variants": {k: {q: x[q] for q in ("ms", "vectors_per_s", "mse_vs_mmse_mean")} for k, x in v5.items()},
+                "learned_K2_faster_than_plain_K5": v5["learned_K2"]["ms"] < v5["plain_K5"]["ms"],
+                "learned_K2_mse_at_most_plain_K5": v5["learned_K2"]["mse_vs_mmse_mean"] <= v5["plain_K5"]["mse_vs_mmse_mean"],
+                "training": c5["training"]}
+    return out
+
+
 def run_profile(args):
     """Three untimed calls of one direction on the step's workload (the launches an ncu capture of
     this command selects with -k / -s / -c)."""
@@ -718,6 +847,8 @@ def main():
                     help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="chunks of the pipelined host-buffer frame in the e2e leg (0: the library's default)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the condensed runs of configurations 1, 3, 4 and 5 from the default line")
     ap.add_argument("--step", choices=["frame", "separate"], default="frame",
                     help="frame (default): UL + DL on one channel, one call; separate: two calls, two channels")
     args = ap.parse_args()

@@ -438,6 +438,22 @@ size_t cdmimo_host_workspace_size(const cdmimo_params* p, int op);
  * two calls, the uplink's form.  Host only: nothing is launched. */
 int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H);
 
+/*
+ * Throughput probes of the SM pipes the CD kernels compute on.  The paper has no counterpart: these
+ * give the benchmark its per-pipe roofline denominators, measured on the running GPU.
+ *   CDMIMO_PROBE_FFMA2     fma.rn.f32x2 dependency chains (the sweeps' packed FP32 FMA);
+ *   CDMIMO_PROBE_MMA_TF32  mma.sync m16n8k8 TF32 chains (the split-TF32 contractions).
+ * Enqueues one launch on `stream`: cdmimo_pipe_probe_sink_floats() threads (four 256-thread CTAs
+ * per SM) each run `iters` (>= 1) iterations of 8 independent chains and write one float to sink
+ * (DEVICE float[sink_floats], at least cdmimo_pipe_probe_sink_floats()).  *flops (HOST) receives
+ * the launch's flop count; time the launch with events on `stream`.  Errors: INVALID_ARG (kind,
+ * iters, NULL pointers), WORKSPACE (sink too small), CUDA_ERROR.
+ */
+#define CDMIMO_PROBE_FFMA2 0
+#define CDMIMO_PROBE_MMA_TF32 1
+size_t cdmimo_pipe_probe_sink_floats(void);
+int cdmimo_pipe_probe(int kind, int iters, float* sink, size_t sink_floats, double* flops, void* stream);
+
 /* Static name of a status code. */
 const char* cdmimo_status_string(int status);
 

@@ -105,6 +105,8 @@ def lib():
             "cdmimo_batch_build": ([ctypes.POINTER(BatchDesc), I, ctypes.POINTER(BatchPlan), P, S], I),
             "cdmimo_detect_batched": ([ctypes.POINTER(BatchPlan), P, P, P], I),
             "cdmimo_synth_uplink": ([ctypes.c_ulonglong, I, I, I, I, I, P, P, P, P, P, P, P], I),
+            "cdmimo_pipe_probe_sink_floats": ([], S),
+            "cdmimo_pipe_probe": ([I, I, P, S, ctypes.POINTER(ctypes.c_double), P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -482,3 +484,20 @@ def check_bounded_wait(timeout_us=20000, stream=None):
     """cdmimo_check_bounded_wait: one thread's bounded wait on a barrier nothing completes expires
     after timeout_us and sets DEV_TIMEOUT (read it with device_status)."""
     _check("cdmimo_check_bounded_wait", lib().cdmimo_check_bounded_wait(int(timeout_us), _stream(stream)))
+
+
+PROBE_FFMA2, PROBE_MMA_TF32 = 0, 1
+
+
+def pipe_probe(kind, iters, sink, stream=None):
+    """cdmimo_pipe_probe: enqueue one pipe-throughput probe launch; returns its flop count.  sink: a
+    float32 device tensor of at least cdmimo_pipe_probe_sink_floats() elements."""
+    _need(sink, "sink")
+    fl = ctypes.c_double(0.0)
+    _check("cdmimo_pipe_probe", lib().cdmimo_pipe_probe(int(kind), int(iters), _ptr(sink), sink.numel(),
+                                                        ctypes.byref(fl), _stream(stream)))
+    return fl.value
+
+
+def pipe_probe_sink_floats():
+    return int(lib().cdmimo_pipe_probe_sink_floats())
