@@ -356,6 +356,46 @@ int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
     return CDMIMO_OK;
 }
 
+// Tensor-core plan for 16 < U <= 32 users (cd_detect_tc32_kernel, detection only): every B_c = 16,
+// 32 or 64, n_sym <= 16, no learned block, H 16-byte aligned with rows of a multiple of 16 bytes
+// (whole-row bulk copies), and a layout that fits shared memory.  With AUTO it also needs
+// U <= 2 B_c (the sweeps' FP32 work, K U^2 complex MACs per cluster and vector, at most the residual
+// form's 2 K U B_c) and, where B_c < 2U, K <= 8: with few sweeps the Gram-form iterate stays within
+// FP32 rounding of the algorithm's even when G_c + (N0/Ex) I is poorly conditioned (an emulation of
+// the split-TF32 Gram form gave 6e-7 relative at U = B_c = 32 and 64, K = 5).
+int build_tc32_plan(const cdmimo_params* p, const void* H, CdPlan* pl)
+{
+    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->U <= 16 || p->U > 32 || p->n_sym > 16 || p->learned || p->fuse == CDMIMO_FUSE_LEARNED)
+        return CDMIMO_ERR_UNSUPPORTED;
+    const int Bc = p->cluster_size[0];
+    if (Bc != 16 && Bc != 32 && Bc != 64) return CDMIMO_ERR_UNSUPPORTED;
+    for (int c = 0; c < p->C; ++c)
+        if (p->cluster_size[c] != Bc) return CDMIMO_ERR_UNSUPPORTED;
+    if (!aligned(H, 16) || ((size_t)p->B * elem_bytes(p->in_dtype)) % 16 != 0) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->form == CDMIMO_FORM_AUTO && (p->U > 2 * Bc || (Bc < 2 * p->U && p->K > 8))) return CDMIMO_ERR_UNSUPPORTED;
+    std::memset(pl, 0, sizeof(*pl));
+    pl->n_sc = p->n_sc;
+    pl->n_sym = p->n_sym;
+    pl->B = p->B;
+    pl->U = p->U;
+    pl->C = p->C;
+    pl->K = p->K;
+    pl->fuse = p->fuse;
+    pl->inv_Ex = 1.f / p->Ex;
+    pl->rho_c = (float)(p->rho / std::sqrt((double)p->C));
+    for (int c = 0; c < p->C; ++c) {
+        pl->cl[c].off = c * Bc;
+        pl->cl[c].size = Bc;
+    }
+    pl->n_tiles = p->C * p->n_sym;
+    pl->bulk = 1;
+    pl->gram = 1;
+    pl->UT = 32;
+    pl->threads = 256;
+    return tc32_layout_fits(*pl, p->in_dtype);
+}
+
 // The plan for p->form: GRAM where requested, or (AUTO) where the Gram form applies and pays,
 // else the residual form.
 int plan_for(const cdmimo_params* p, bool detect, const void* H, CdPlan* pl)
@@ -464,6 +504,12 @@ int detect_impl(const cdmimo_params* p, const void* H, const void* Y, const floa
                           reinterpret_cast<float2*>(Xc), lam, p->learned, sched},
                          nullptr, nullptr};
         return dispatch_frame_tc(p->in_dtype, pl, io, CDMIMO_OP_DETECT, s);
+    }
+    if (build_tc32_plan(p, H, &pl) == CDMIMO_OK) {
+        const DetectIO io{H, Y, N0, p->h_scale, p->y_scale, reinterpret_cast<float2*>(Xhat),
+                          reinterpret_cast<float2*>(Xc), lam, nullptr, sched};
+        const int rc = dispatch_detect_tc32(p->in_dtype, pl, io, s);
+        if (rc != CDMIMO_ERR_UNSUPPORTED) return rc;
     }
     if (int rc = plan_for(p, true, H, &pl)) {
         if (rc != CDMIMO_ERR_UNSUPPORTED || Xc || lam || is_forced_gram(p)) return rc;
@@ -1065,6 +1111,8 @@ int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
     CdPlan pl;
     if (build_tc_plan(p, H, op, &pl) == CDMIMO_OK)
         return p->form == CDMIMO_FORM_GRAM_TC_PHASED ? CDMIMO_FORM_GRAM_TC_PHASED : CDMIMO_FORM_GRAM_TC;
+    if ((op == CDMIMO_OP_DETECT || op == CDMIMO_OP_FRAME) && build_tc32_plan(p, H, &pl) == CDMIMO_OK)
+        return CDMIMO_FORM_GRAM_TC;  // the frame then runs as two calls, the uplink's on this kernel
     if (op == CDMIMO_OP_FRAME) {
         if (p->form != CDMIMO_FORM_RESIDUAL && !p->learned && p->fuse != CDMIMO_FUSE_LEARNED &&
             build_gram_plan(p, true, H, p->form == CDMIMO_FORM_AUTO, &pl, true) == CDMIMO_OK)
@@ -1360,7 +1408,8 @@ int cdmimo_device_status(int clear)
     if (module_status(&v, clear) != CDMIMO_OK || gram_detect_module_status(&v, clear) != CDMIMO_OK ||
         gram_precode_module_status(&v, clear) != CDMIMO_OK || gram_frame_module_status(&v, clear) != CDMIMO_OK ||
         frame_tc_module_status(&v, clear) != CDMIMO_OK || frame_tc16_module_status(&v, clear) != CDMIMO_OK ||
-        frame_ws_module_status(&v, clear) != CDMIMO_OK || frame_ws16_module_status(&v, clear) != CDMIMO_OK)
+        frame_ws_module_status(&v, clear) != CDMIMO_OK || frame_ws16_module_status(&v, clear) != CDMIMO_OK ||
+        tc32_module_status(&v, clear) != CDMIMO_OK)
         return CDMIMO_ERR_CUDA;
     return (int)v;
 }

@@ -87,5 +87,10 @@ int dispatch_frame_ws(int in_dtype, const CdPlan& pl, const FusedIO& io, int op,
 int dispatch_frame_ws16(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s);
 int frame_ws_module_status(unsigned* v, int clear);
 int frame_ws16_module_status(unsigned* v, int clear);
+// Tensor-core Gram-form detection for 16 < U <= 32 (gram_tc32.cu), on a plan of build_tc32_plan;
+// tc32_layout_fits: CDMIMO_OK where its shared-memory layout fits the device.
+int dispatch_detect_tc32(int in_dtype, const CdPlan& pl, const DetectIO& io, cudaStream_t s);
+int tc32_layout_fits(const CdPlan& pl, int in_dtype);
+int tc32_module_status(unsigned* v, int clear);
 
 }  // namespace cdmimo
