@@ -80,7 +80,8 @@ FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
 # L2 when a kernel ends are written back after it, outside the launch.
 NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.806592e6 + 0.621568e6,
                "cd_precode_gram_kernel": 41.539072e6 + 0.377088e6,
-               "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6}
+               "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6,
+               "cd_frame_ws_kernel": 75.993344e6 + 4.826112e6}
 
 WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
             "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
@@ -809,20 +810,21 @@ def run_profile(args):
     from paper_1902_08653_gb300 import workload as wl
 
     dev = torch.device("cuda:0")
-    up = wl.uplink(20190222, N_SC, N_SYM, B, U, snr_db=wl.sweep_snr(N_SC), M=M)
+    Up, Mp = (32, 64) if args.profile.startswith("detect_u32") else (U, M)  # configuration 3's users
+    up = wl.uplink(20190222, N_SC, N_SYM, B, Up, snr_db=wl.sweep_snr(N_SC), M=Mp)
     t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
     H, Y, S = t(up["H"]), t(up["Y"]), t(up["X"])
     N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
     sc = {}
-    if args.profile == "frame_f16":  # the same batch stored as fp16 with per-subcarrier scales
+    if args.profile in ("frame_f16", "detect_u32_f16"):  # the same batch stored as fp16 with per-subcarrier scales
         qH, sH, _ = wl.quantize_c16(up["H"], "f16")
         qY, sY, _ = wl.quantize_c16(up["Y"], "f16")
         H = torch.from_numpy(qH.view(np.int16)).to(dev).view(torch.float16)
         Y = torch.from_numpy(qY.view(np.int16)).to(dev).view(torch.float16)
         sc = dict(h_scale=torch.from_numpy(sH).to(dev), y_scale=torch.from_numpy(sY).to(dev))
     for _ in range(3):
-        if args.profile == "detect":
-            cdmimo.detect(H, Y, N0, CS, K, form=args.form)
+        if args.profile.startswith("detect"):
+            cdmimo.detect(H, Y, N0, CS, K, form=args.form, **sc)
         elif args.profile == "precode":
             cdmimo.precode(H, S, CS, K, form=args.form)
         else:
@@ -841,8 +843,10 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2 (default): UL detect + DL precode bench line; 1, 3, 4, 5: the other configurations")
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
-    ap.add_argument("--profile", choices=["detect", "precode", "frame", "frame_f16"], default=None,
-                    help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu")
+    ap.add_argument("--profile", choices=["detect", "precode", "frame", "frame_f16", "detect_u32", "detect_u32_f16"],
+                    default=None,
+                    help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu "
+                         "(detect_u32*: configuration 3's U = 32, 64-QAM batch, K = 3)")
     ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc", "gram_tc_phased"], default="auto",
                     help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,

@@ -200,7 +200,10 @@ __global__ void __launch_bounds__(kTc32Threads, 1) cd_detect_tc32_kernel(const C
             bulk_prefetch_l2(static_cast<const char*>(io.Y) + (size_t)f * n_sym * pl.B * eb, (uint32_t)n_sym * pl.B * eb);
     };
 
-    const GLane gb = frame_lane(0, C, n_sym, 1);  // phase B: one lane per (cluster, symbol)
+    // phase B: one lane per (cluster, symbol), each cluster's symbols in their own quarter or half
+    // warp so that no quarter warp reads two clusters' Gram rows
+    const int slot = ws_slot(n_sym), sc = warp * (32 / slot) + lane / slot, sn = lane % slot;
+    const bool sweep_lane = sc < C && sn < n_sym;
     int f = blockIdx.x, done = 0;
     if (f < pl.n_sc) issue_copy(f, 0);
     for (int k = 0; f < pl.n_sc; ++k) {
@@ -234,18 +237,18 @@ __global__ void __launch_bounds__(kTc32Threads, 1) cd_detect_tc32_kernel(const C
         __syncthreads();
 
         // Phase B: K sweeps per tile; x replaces z.
-        if (gb.active) {
-            const int n_b = gb.j, tile = gb.c * n_sym + n_b;
-            const float* dd = Dm + gb.c * UT;
+        if (sweep_lane) {
+            const int tile = sc * n_sym + sn;
+            const float* dd = Dm + sc * UT;
             float4 x[NP];
-            gram_sweeps<UT>(U, pl.K, Gs + (size_t)gb.c * UT * NP, dd, Zs + tile, xs, x);
+            gram_sweeps<UT>(U, pl.K, Gs + (size_t)sc * UT * NP, dd, Zs + tile, xs, x);
 #pragma unroll
             for (int u = 0; u < UT; ++u)
                 if (u < U) Zs[tile + u * xs] = slice_entry<UT, 1>(x, u);
-            if (n_b == 0) {
+            if (sn == 0) {
                 float msum = 0.f;
                 for (int u = 0; u < U; ++u) msum += dd[u] > 0.f ? dd[u] : __int_as_float(0x7f800000);
-                lam[gb.c] = 1.f / msum;
+                lam[sc] = 1.f / msum;
             }
         }
         __syncthreads();

@@ -368,6 +368,7 @@ int build_tc32_plan(const cdmimo_params* p, const void* H, CdPlan* pl)
     if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC) return CDMIMO_ERR_UNSUPPORTED;
     if (p->U <= 16 || p->U > 32 || p->n_sym > 16 || p->learned || p->fuse == CDMIMO_FUSE_LEARNED)
         return CDMIMO_ERR_UNSUPPORTED;
+    if (p->C > 8 * (32 / (p->n_sym <= 8 ? 8 : 16))) return CDMIMO_ERR_UNSUPPORTED;  // sweep lanes: 8 warps
     const int Bc = p->cluster_size[0];
     if (Bc != 16 && Bc != 32 && Bc != 64) return CDMIMO_ERR_UNSUPPORTED;
     for (int c = 0; c < p->C; ++c)
