@@ -203,12 +203,20 @@ def rank_seed(rank):
     return 20190222 + rank
 
 
-def bench_config(step, world):
+def bench_config(step, world, scaling="weak"):
     """The line's workload description, the same for the CUDA arm and the reference arm."""
+    par = "single GPU"
+    if world > 1:
+        par = f"subcarrier shards of one batch x{world}" if scaling == "strong" else f"replicas x{world}"
     return {"workload": WORKLOAD if step == "frame" else WORKLOAD_SEPARATE, "step": step, "n_sc": N_SC,
             "n_sym": N_SYM, "B": B, "C": C, "B_c": B // C, "U": U, "K": K, "fusion": "colnorm", "qam": M,
-            "l2": "GPU arm: flushed between timed steps (256 MB write, untimed)",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+            "l2": "GPU arm: flushed between timed steps (256 MB write, untimed)", "parallelism": par}
+
+
+def shard_batch(d, lo, hi):
+    """The subcarriers [lo, hi) of a workload dict (arrays indexed by subcarrier first)."""
+    return {k: (v[lo:hi] if isinstance(v, np.ndarray) and v.ndim >= 1 and v.shape[0] == N_SC else v)
+            for k, v in d.items()}
 
 
 def make_inputs(seed):
@@ -247,16 +255,24 @@ def run_cuda(args, rank, world, local_rank):
     from paper_1902_08653_gb300 import workload as wl
 
     frame = args.step == "frame"
+    strong = args.scaling == "strong"
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     cdmimo.lib()
-    up, dl = make_inputs(rank_seed(rank))
+    if strong:  # one batch, its subcarriers split over the ranks (no collective on the data path)
+        from paper_1902_08653_gb300 import parallel
+
+        lo, hi = parallel.subcarrier_shard(N_SC, world, rank)
+        up, dl = (shard_batch(x, lo, hi) for x in make_inputs(rank_seed(0)))
+    else:
+        up, dl = make_inputs(rank_seed(rank))
+    n_loc = up["H"].shape[0]
     t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
     H, Y, S = t(up["H"]), t(up["Y"]), t(dl["S"])
     Hd = H if frame else t(dl["H"])
     N0 = torch.from_numpy(up["N0"].astype(np.float32)).to(dev)
-    Xhat = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64, device=dev)
-    Xdl = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64, device=dev)
+    Xhat = torch.empty((n_loc, N_SYM, U), dtype=torch.complex64, device=dev)
+    Xdl = torch.empty((n_loc, N_SYM, B), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -320,19 +336,19 @@ def run_cuda(args, rank, world, local_rank):
     N0h = torch.from_numpy(up["N0"].astype(np.float32)).pin_memory()
     Sh = torch.from_numpy(wl.as_c64(dl["S"])[0]).pin_memory()
     Hdh = Hh if frame else torch.from_numpy(wl.as_c64(dl["H"])[0]).pin_memory()
-    Xh = torch.empty((N_SC, N_SYM, U), dtype=torch.complex64).pin_memory()
-    Xdh = torch.empty((N_SC, N_SYM, B), dtype=torch.complex64).pin_memory()
+    Xh = torch.empty((n_loc, N_SYM, U), dtype=torch.complex64).pin_memory()
+    Xdh = torch.empty((n_loc, N_SYM, B), dtype=torch.complex64).pin_memory()
     if frame:  # cdmimo_detect_precode_host: chunked; uploads, kernels and downloads overlap
-        ws_fr = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_FRAME, N_SC, N_SYM, B, U, CS, K), dtype=torch.uint8,
+        ws_fr = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_FRAME, n_loc, N_SYM, B, U, CS, K), dtype=torch.uint8,
                             device=dev)
 
         def e2e_step():
             cdmimo.detect_precode_host(Hh, Yh, N0h, Sh, CS, K, Xh, Xdh, ws_fr, n_chunks=args.e2e_chunks,
                                        stream=stream, form=args.form)
     else:
-        ws_ul = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K),
+        ws_ul = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_DETECT, n_loc, N_SYM, B, U, CS, K),
                             dtype=torch.uint8, device=dev)
-        ws_dl = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K),
+        ws_dl = torch.empty(cdmimo.host_workspace_size(cdmimo.OP_PRECODE, n_loc, N_SYM, B, U, CS, K),
                             dtype=torch.uint8, device=dev)
 
         def e2e_step():
@@ -361,10 +377,10 @@ def run_cuda(args, rank, world, local_rank):
     mse, ber = mse_vs_mmse(up, Xh.numpy().astype(np.complex128))
     hbm_peak, peak_src = load_peaks()
     ms_step = dev_ms / args.steps
-    vec_step = N_SC * N_SYM
-    value = whole_job_value(vec_step, world, ms_step)
-    form_ul = cdmimo.selected_form(cdmimo.OP_DETECT, N_SC, N_SYM, B, U, CS, K, form=args.form, H=H)
-    form_dl = cdmimo.selected_form(cdmimo.OP_PRECODE, N_SC, N_SYM, B, U, CS, K, form=args.form, H=Hd)
+    vec_step = n_loc * N_SYM  # this rank's vectors per step
+    value = N_SC * N_SYM / (ms_step * 1e-3) if strong else whole_job_value(vec_step, world, ms_step)
+    form_ul = cdmimo.selected_form(cdmimo.OP_DETECT, n_loc, N_SYM, B, U, CS, K, form=args.form, H=H)
+    form_dl = cdmimo.selected_form(cdmimo.OP_PRECODE, n_loc, N_SYM, B, U, CS, K, form=args.form, H=Hd)
 
     def kernel_line(name, form, ms, flop, nbytes):
         return {"kernel": name, "form": form, "ms": ms, "flop_per_vector": flop,
@@ -372,7 +388,7 @@ def run_cuda(args, rank, world, local_rank):
                 "hbm_frac": nbytes * vec_step / (ms * 1e-3) / 1e9 / hbm_peak}
 
     if frame:
-        form_fr = cdmimo.selected_form(cdmimo.OP_FRAME, N_SC, N_SYM, B, U, CS, K, form=args.form, H=H)
+        form_fr = cdmimo.selected_form(cdmimo.OP_FRAME, n_loc, N_SYM, B, U, CS, K, form=args.form, H=H)
         fused = form_fr in FRAME_KERNELS
         name = FRAME_KERNELS[form_fr] if fused else "+".join(KERNELS[form_ul][:1] + KERNELS[form_dl][1:])
         fl = FRAME_FLOP_PER_VEC["gram"] if fused else FLOP_PER_VEC[form_ul] + FLOP_PER_VEC[form_dl]
@@ -435,17 +451,18 @@ def run_cuda(args, rank, world, local_rank):
         "step_ms_percentiles": {q: float(np.percentile(np.add(t_a, t_b), v)) for q, v in
                                 (("p10", 10), ("median", 50), ("p90", 90))},
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": args.scaling,
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded i.i.d. Rayleigh, 16-QAM, AWGN)",
-        "config": bench_config(args.step, world),
+        "config": bench_config(args.step, world, args.scaling),
         "gbps": value * BITS / 1e9,
         "kernels": kernels,
         "roofline": roof,
         "mse_vs_mmse": mse,
         "ber": ber,
-        "e2e": {"value": whole_job_value(vec_step, world, e2e_ms), "unit": "vectors/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": N_SC * N_SYM / (e2e_ms * 1e-3) if strong else whole_job_value(vec_step, world, e2e_ms),
+                "unit": "vectors/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "api": "cdmimo_detect_precode_host (chunks: %s)" % (args.e2e_chunks or "default") if frame
                 else "cdmimo_detect_host + cdmimo_precode_host"},
@@ -453,7 +470,7 @@ def run_cuda(args, rank, world, local_rank):
         "clocks": clocks,
         "wall_s": wall,
     }
-    if frame and args.form in ("auto", "gram_tc"):
+    if frame and args.form in ("auto", "gram_tc") and n_loc == N_SC:
         line["precision"] = precision_variants(up, dl, dev, stream, min(args.steps, 200), args.e2e_chunks)
     cb = cpu_baseline(up, dl, frame) if world == 1 else None
     if cb is not None:  # and on one host thread
@@ -851,6 +868,9 @@ def main():
                     help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="chunks of the pipelined host-buffer frame in the e2e leg (0: the library's default)")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="N > 1: weak (default: every rank its own 1200-subcarrier batch) or strong (one batch, "
+                         "its subcarriers split over the ranks); neither has a collective on the data path")
     ap.add_argument("--no-configs", action="store_true",
                     help="leave out the condensed runs of configurations 1, 3, 4 and 5 from the default line")
     ap.add_argument("--step", choices=["frame", "separate"], default="frame",

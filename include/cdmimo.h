@@ -86,7 +86,8 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             operands are stored values), every B_c = 16 or every B_c = 32, 8 < U <= 16,
  *             n_sym <= 16 and 2 C n_sym <= 256, and a learned block (c64) in cdmimo_detect only;
  *             elsewhere GRAM_TC is GRAM.  Without a learned block, and where C n_sym <= 128 and
- *             its buffers fit in shared memory (not for cdmimo_detect with Xc_opt / lambda_opt),
+ *             its buffers fit in shared memory (not for cdmimo_detect with Xc_opt / lambda_opt,
+ *             nor with a schedule workspace: it walks subcarriers in a static order),
  *             a warp-specialized kernel runs: one CTA per SM whose MMA warps form G_c and z of the
  *             next subcarrier and x_c = H_c w of the previous one while its other warps sweep the
  *             current one; its results equal the phased kernel's bit for bit.
@@ -205,6 +206,20 @@ int cdmimo_detect_precode(const cdmimo_params* p, const void* H, const void* Y, 
  */
 int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* w, int weights_are_lambda,
                 void* Xhat, void* stream);
+
+/*
+ * Unnormalized fusion weights (Sec. III) of every (subcarrier, cluster) of p, in the true units of H,
+ * for fusing estimates made by separate calls or on separate devices (the paper's cluster-per-GPU
+ * deployment): lambda_c = w_c / sum_c' w_c' over the clusters of all calls, and the weights of
+ * disjoint cluster sets may simply be concatenated.  p->fuse COLNORM: w_c = 1 / sum_u m_{u,c} with
+ * m_{u,c} = (||h_{u,c}||^2 + N0/Ex)^{-1} (sigma_c^2 up to the common factor N0/U; a user whose
+ * denominator is not positive makes w_c = 0, as in the fusing kernels); EQUAL: w_c = 1; LEARNED:
+ * UNSUPPORTED.  If every cluster of a subcarrier has w_c = 0 the fusing kernels use equal weights.
+ * H DEVICE [n_sc][U][B] (16-bit storage scaled by p->h_scale); N0 DEVICE float [n_sc] (a negative or
+ * NaN N0 gives NaN weights); w DEVICE float [n_sc][C] (written).  Enqueued on `stream`; allocates
+ * nothing.
+ */
+int cdmimo_fusion_weights(const cdmimo_params* p, const void* H, const float* N0, float* w, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- */
 /* Host-buffer variants (end-to-end calls).                                                        */

@@ -105,6 +105,7 @@ def lib():
             "cdmimo_batch_build": ([ctypes.POINTER(BatchDesc), I, ctypes.POINTER(BatchPlan), P, S], I),
             "cdmimo_detect_batched": ([ctypes.POINTER(BatchPlan), P, P, P], I),
             "cdmimo_synth_uplink": ([ctypes.c_ulonglong, I, I, I, I, I, P, P, P, P, P, P, P], I),
+            "cdmimo_fusion_weights": ([PP, P, P, P, P], I),
             "cdmimo_pipe_probe_sink_floats": ([], S),
             "cdmimo_pipe_probe": ([I, I, P, S, ctypes.POINTER(ctypes.c_double), P], I),
         }
@@ -501,3 +502,21 @@ def pipe_probe(kind, iters, sink, stream=None):
 
 def pipe_probe_sink_floats():
     return int(lib().cdmimo_pipe_probe_sink_floats())
+
+
+def fusion_weights(H, N0, cluster_size, *, Ex=1.0, fuse="colnorm", h_scale=None, out=None, stream=None):
+    """cdmimo_fusion_weights: unnormalized Sec. III fusion weights [n_sc, C] (float32, device) of the
+    clusters of H, in H's true units: the weights of cluster sets held by separate calls or devices
+    concatenate, and lambda is their normalization over all clusters."""
+    _need(H, "H")
+    _need(N0, "N0")
+    dt = _dtype_of(H)
+    n_sc, U, B = H.shape[0], H.shape[1], H.shape[2]
+    C = len(cluster_size)
+    if out is None:
+        out = torch.empty((n_sc, C), dtype=torch.float32, device=H.device)
+    p, keep = make_params(n_sc, 1, B, U, cluster_size, 1, Ex=Ex, fuse=fuse, in_dtype=dt, h_scale=h_scale)
+    _check("cdmimo_fusion_weights", lib().cdmimo_fusion_weights(ctypes.byref(p), _ptr(H), _ptr(N0), _ptr(out),
+                                                                _stream(stream)))
+    return out
+

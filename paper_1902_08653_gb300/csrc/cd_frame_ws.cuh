@@ -13,7 +13,8 @@
 // their sum, and the sweep warps (the FP32 pipes) and the MMA warps (the tensor pipes) issue on the
 // same SM sub-partitions at the same time.
 //
-// Pipeline, for the CTA's subcarriers s = 0, 1, ... (f = blockIdx.x + s gridDim.x):
+// Pipeline, for the CTA's subcarriers s = 0, 1, ... (f = blockIdx.x + s gridDim.x, a static schedule;
+// calls with schedule counters run the phased kernel):
 //   MMA stage j:    [j >= 2] wait sweeps(j - 2); phase C and fusion of j - 2; copy the channel of j + 1
 //                   into the buffer j - 2 used;  [j < n] wait channel(j); phase A of j; signal A(j).
 //   sweep stage j:  wait A(j); sweeps of j; signal sweeps(j).
@@ -294,7 +295,6 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         }
     }
     __syncthreads();
-    sched_finish(d.sched, n_mine, pl.n_sc);
 }
 
 }  // namespace cdmimo

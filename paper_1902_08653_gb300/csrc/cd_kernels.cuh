@@ -499,6 +499,46 @@ __global__ void __maxnreg__(AT > 0 ? CDMIMO_CD_SPECIALIZED_REGS : 128) cd_precod
 // ---------------------------------------------------------------------------------------------
 // Standalone fusion (Sec. III): Xhat[f][n][u] = sum_c lambda_c Xc[f][c][n][u].
 // ---------------------------------------------------------------------------------------------
+// Unnormalized fusion weights (Sec. III) per (subcarrier, cluster), in the true units of H: COLNORM
+// w_c = 1 / sum_u m_{u,c} with m_{u,c} = (||h_{u,c}||^2 + alpha)^{-1} (a user whose denominator is
+// not positive counts as infinite, so w_c = 0, as in the fusing kernels); EQUAL w_c = 1.  One warp
+// per cluster, users over its lanes; grid-stride over subcarriers.  A negative or NaN N0 gives NaN.
+struct ClusterTable {
+    int off[CDMIMO_MAX_CLUSTERS];   // antenna offset o_c
+    int size[CDMIMO_MAX_CLUSTERS];  // B_c
+};
+
+template <int IN>
+__global__ void fusion_weights_kernel(int n_sc, int U, int B, int C, const ClusterTable tab, const void* __restrict__ H,
+                                      const float* __restrict__ N0, const float* __restrict__ h_scale, float inv_Ex,
+                                      int colnorm, float* __restrict__ w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int f = blockIdx.x; f < n_sc; f += gridDim.x) {
+        float alpha = __ldg(N0 + f) * inv_Ex;
+        const bool bad = !(alpha >= 0.f);
+        const float hs2 = IN == CDMIMO_C64 ? 1.f : __ldg(h_scale + f) * __ldg(h_scale + f);
+        for (int c = warp; c < C; c += nw) {
+            float sum = 0.f;
+            if (colnorm) {
+                const int off = tab.off[c], bc = tab.size[c];
+                for (int u = lane; u < U; u += 32) {
+                    const size_t row = ((size_t)f * U + u) * B + off;
+                    float e = 0.f;
+                    for (int b = 0; b < bc; ++b) {
+                        const float2 h = Elem<IN>::load(H, row + b);
+                        e = fmaf(h.x, h.x, fmaf(h.y, h.y, e));
+                    }
+                    const float den = e * hs2 + alpha;
+                    sum += den > 0.f ? 1.f / den : __int_as_float(0x7f800000);
+                }
+                sum = warp_sum(sum);
+            }
+            if (lane == 0) w[(size_t)f * C + c] = bad ? __int_as_float(0x7fc00000) : (colnorm ? 1.f / sum : 1.f);
+        }
+    }
+}
+
 static __global__ void fuse_kernel(int n_sc, int n_sym, int U, int C, const float2* __restrict__ Xc,
                             const float* __restrict__ w, int is_lambda, float2* __restrict__ Xhat)
 {

@@ -1105,6 +1105,38 @@ int cdmimo_fuse(int n_sc, int n_sym, int U, int C, const void* Xc, const float* 
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
+int cdmimo_fusion_weights(const cdmimo_params* p, const void* H, const float* N0, float* w, void* stream)
+{
+    if (int rc = validate(p)) return rc;
+    if (p->fuse == CDMIMO_FUSE_LEARNED) return CDMIMO_ERR_UNSUPPORTED;
+    if (p->n_sc == 0) return CDMIMO_OK;
+    if (!H || !N0 || !w || !aligned(H, elem_bytes(p->in_dtype)) || !aligned(N0, 4) || !aligned(w, 4))
+        return CDMIMO_ERR_INVALID_ARG;
+    if (p->in_dtype != CDMIMO_C64 && (!p->h_scale || !aligned(p->h_scale, 4))) return CDMIMO_ERR_INVALID_ARG;
+    ClusterTable tab{};  // by value in the kernel's parameters: nothing is allocated
+    for (int c = 0, o = 0; c < p->C; o += p->cluster_size[c], ++c) {
+        tab.off[c] = o;
+        tab.size[c] = p->cluster_size[c];
+    }
+    const int colnorm = p->fuse == CDMIMO_FUSE_COLNORM;
+    const int blocks = std::max(1, std::min(p->n_sc, 152 * 8));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (p->in_dtype) {
+    case CDMIMO_C64:
+        fusion_weights_kernel<CDMIMO_C64><<<blocks, 256, 0, s>>>(p->n_sc, p->U, p->B, p->C, tab, H, N0, p->h_scale,
+                                                                1.f / p->Ex, colnorm, w);
+        break;
+    case CDMIMO_C16F:
+        fusion_weights_kernel<CDMIMO_C16F><<<blocks, 256, 0, s>>>(p->n_sc, p->U, p->B, p->C, tab, H, N0, p->h_scale,
+                                                                 1.f / p->Ex, colnorm, w);
+        break;
+    default:
+        fusion_weights_kernel<CDMIMO_C16BF><<<blocks, 256, 0, s>>>(p->n_sc, p->U, p->B, p->C, tab, H, N0,
+                                                                  p->h_scale, 1.f / p->Ex, colnorm, w);
+    }
+    return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
+}
+
 int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
 {
     if (int rc = validate(p)) return rc;

@@ -24,7 +24,9 @@ int dispatch_mode(const CdPlan& pl, const FusedIO& io, cudaStream_t s)
 
 int dispatch_frame_tc(int in_dtype, const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s)
 {
-    if (!pl.learned && !pl.phased) {  // the warp-specialized kernel where it takes the call
+    // the warp-specialized kernel where it takes the call: static schedule only (with the schedule
+    // counters of a workspace the phased kernel's CTAs draw subcarriers from them)
+    if (!pl.learned && !pl.phased && !io.d.sched) {
         const int rc = dispatch_frame_ws(in_dtype, pl, io, op, s);
         if (rc != CDMIMO_ERR_UNSUPPORTED) return rc;
     }

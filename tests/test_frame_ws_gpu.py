@@ -100,9 +100,9 @@ def test_ws_equals_phased_and_matches_oracle(dev, name):
 
 
 def test_ws_full_size_equals_phased(dev):
-    """The benchmark's batch (1200 x 14, B = 256 in 8 x 32, U = 16, K = 3): both kernels, all three
-    modes and both schedules (static; dynamic with the workspace counters, twice in a row so the
-    counters must have reset themselves)."""
+    """The benchmark's batch (1200 x 14, B = 256 in 8 x 32, U = 16, K = 3): both kernels and all
+    three modes; with a schedule workspace (the phased kernel's dynamic schedule, twice in a row so
+    the counters must have reset themselves) the results are the same bits."""
     cs, U, K, n_sc = [32] * 8, 16, 3, 1200
     x = inputs(dev, 20190222, n_sc, 14, cs, U)
     args = (x["H"], x["Y"], x["N0"], x["S"], cs, K)

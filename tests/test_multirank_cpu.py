@@ -61,3 +61,20 @@ def test_reference_arm_prints_on_rank_0_only():
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "vectors/s"
+
+
+def test_strong_scaling_shards_cover_the_batch():
+    """bench.py --scaling strong: every rank loads the same batch and keeps its subcarrier range; the
+    ranges partition the batch and each rank's arrays are exactly its rows."""
+    import bench
+    from paper_1902_08653_gb300 import parallel
+
+    up, dl = bench.make_inputs(bench.rank_seed(0))
+    rows = []
+    for r in range(3):
+        lo, hi = parallel.subcarrier_shard(bench.N_SC, 3, r)
+        su, sd = bench.shard_batch(up, lo, hi), bench.shard_batch(dl, lo, hi)
+        assert su["H"].shape[0] == su["Y"].shape[0] == su["N0"].shape[0] == sd["S"].shape[0] == hi - lo
+        assert np.array_equal(su["H"], up["H"][lo:hi]) and su["M"] == up["M"]
+        rows.append(su["N0"])
+    assert np.array_equal(np.concatenate(rows), up["N0"])
