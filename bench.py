@@ -710,12 +710,11 @@ def mse_vs_mmse_U(up, Xhat, Uc, Mq):
     return mse, ber
 
 
-def run_config4(args, dev):
-    """100 resource blocks x 12 subcarriers x 14 symbols, B in {128,256,512}, clusters {16,32,64}, U in [8,64],
-    K = 3, 16-QAM at 20 dB: one persistent launch per step, replayed from a CUDA graph, autotuned tiles."""
+def config4_items(dev):
+    """The uneven batch's blocks, its detection items (device tensors) and its sweep FLOPs."""
     import torch
 
-    from paper_1902_08653_gb300 import batched, cdmimo
+    from paper_1902_08653_gb300 import batched
     from paper_1902_08653_gb300 import workload as wl
 
     blocks = wl.resource_blocks(20190222, n_rb=100, n_sc=12, n_sym=14)
@@ -729,6 +728,20 @@ def run_config4(args, dev):
                           out=torch.empty((n_sc, 14, Ub), dtype=torch.complex64, device=dev),
                           cluster_size=b["cluster_size"], K=3, fuse="colnorm", Ex=1.0))
         flops += n_sc * 14 * 2 * 3 * Ub * Bb * 8
+    return blocks, items, flops
+
+
+# Tile parameters of the batched kernel under `--profile batched` (the autotuner's usual choice on
+# the uneven batch), fixed so that the captured launches do not depend on timing.
+BATCH_PROFILE_PLAN = dict(P=16, threads=512, group_bytes=96 * 1024, ctas_per_sm=0)
+
+
+def run_config4(args, dev):
+    """100 resource blocks x 12 subcarriers x 14 symbols, B in {128,256,512}, clusters {16,32,64}, U in [8,64],
+    K = 3, 16-QAM at 20 dB: one persistent launch per step, replayed from a CUDA graph, autotuned tiles."""
+    from paper_1902_08653_gb300 import batched, cdmimo
+
+    blocks, items, flops = config4_items(dev)
     bt = batched.Batch(items)
     plan, times = batched.autotune(bt, reps=5)
     bt.capture()
@@ -827,6 +840,17 @@ def run_profile(args):
     from paper_1902_08653_gb300 import workload as wl
 
     dev = torch.device("cuda:0")
+    if args.profile == "batched":  # configuration 4's uneven batch, one persistent launch per call
+        from paper_1902_08653_gb300 import batched
+
+        _, items, _ = config4_items(dev)
+        bt = batched.Batch(items, plan=batched.default_plan(**BATCH_PROFILE_PLAN))
+        for _ in range(3):
+            bt.run()
+        torch.cuda.synchronize()
+        assert cdmimo.device_status(clear=True) == 0
+        print("ok batched", BATCH_PROFILE_PLAN)
+        return
     Up, Mp = (32, 64) if args.profile.startswith("detect_u32") else (U, M)  # configuration 3's users
     up = wl.uplink(20190222, N_SC, N_SYM, B, Up, snr_db=wl.sweep_snr(N_SC), M=Mp)
     t = lambda a: torch.from_numpy(wl.as_c64(a)[0]).to(dev)
@@ -860,10 +884,12 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2 (default): UL detect + DL precode bench line; 1, 3, 4, 5: the other configurations")
     ap.add_argument("--train-channels", type=int, default=1_000_000, help="--config 5: training channels")
-    ap.add_argument("--profile", choices=["detect", "precode", "frame", "frame_f16", "detect_u32", "detect_u32_f16"],
+    ap.add_argument("--profile", choices=["detect", "precode", "frame", "frame_f16", "detect_u32", "detect_u32_f16",
+                                          "batched"],
                     default=None,
                     help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu "
-                         "(detect_u32*: configuration 3's U = 32, 64-QAM batch, K = 3)")
+                         "(detect_u32*: configuration 3's U = 32, 64-QAM batch, K = 3; batched: configuration 4's "
+                         "uneven batch, three persistent launches)")
     ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc", "gram_tc_phased"], default="auto",
                     help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,

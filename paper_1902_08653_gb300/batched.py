@@ -28,6 +28,8 @@ CANDIDATES = [
     dict(P=8, threads=512, group_bytes=96 * 1024, ctas_per_sm=0),
     dict(P=16, threads=512, group_bytes=64 * 1024, ctas_per_sm=0),
     dict(P=32, threads=256, group_bytes=96 * 1024, ctas_per_sm=0),
+    dict(P=16, threads=128, group_bytes=48 * 1024, ctas_per_sm=0),
+    dict(P=16, threads=128, group_bytes=44 * 1024, ctas_per_sm=0),
 ]
 
 

@@ -9,22 +9,25 @@
 // w_c = 1 / sum_u m_{u,c} (COLNORM, the reading of Sec. III) or xhat = sum_c x_c / C (EQUAL).
 #pragma once
 #include "batched.h"
-#include "cd_kernels.cuh"
+#include "cd_kernels_pp.cuh"
 
 namespace cdmimo {
 
-// Lane -> tile mapping of one cluster group (same rules as map_lane).
+// Lane -> tile mapping of one cluster group (same rules as map_lane).  A lane inside no cluster's
+// lane range (the gaps that align packed groups' A classes to warps) is inactive; the warp's mask is
+// the ballot of its active lanes.  Called by every thread of the CTA.
 __device__ __forceinline__ LaneTile map_lane_group(int n_lanes, int Cg, int n_sym, const ClusterTile* tab)
 {
     LaneTile t{};
     const int tid = threadIdx.x;
-    t.active = tid < n_lanes;
+    t.active = false;
     t.c = 0;
     t.A = 1;
-    if (t.active) {
+    if (tid < n_lanes) {
         for (int k = 0; k < Cg; ++k) {
             const int l0 = tab[k].lane0;
             if (tid >= l0 && tid < l0 + n_sym * tab[k].A) {
+                t.active = true;
                 t.c = k;
                 t.A = tab[k].A;
                 t.n = (tid - l0) / t.A;
@@ -32,10 +35,63 @@ __device__ __forceinline__ LaneTile map_lane_group(int n_lanes, int Cg, int n_sy
             }
         }
     }
-    const int n_act = min(32, n_lanes - (tid & ~31));
-    t.mask = n_act >= 32 ? 0xffffffffu : (n_act > 0 ? ((1u << n_act) - 1u) : 0u);
+    t.mask = __ballot_sync(0xffffffffu, t.active);
     t.Awarp = t.active ? (int)__reduce_max_sync(t.mask, (unsigned)t.A) : 1;
     return t;
+}
+
+// Packed-FP32 sweeps of one tile of a packed group (pair-planar channel rows, the lane's AT-strided
+// antenna pairs in registers, tile sums over AT lanes): Algorithm 1 with (m, n) from coef, x per
+// tile in Xs (zero at the start), the running residual r in registers.  Software-pipelined: the
+// rows of step u + 1 are loaded while step u's update consumes the rows of step u (each register
+// is reloaded right after its last use), and the step's (m, n) and old x are read before the
+// correlation, so neither load latency sits on the step's dependency chain.
+template <int AT>
+__device__ __forceinline__ void batched_detect_pp(const float4* hb, int LP, int U, int K, const float2* coef, int Cg,
+                                                  int c, float2* xs, int xstride, float4 (&r)[kPairs], unsigned mask)
+{
+    if (K <= 0 || U <= 0) return;
+    float4 h[kPairs];
+    pp_load_h<AT>(hb, h);
+    int u = 0;
+#pragma unroll 1
+    for (int step = 0; step < K * U; ++step) {
+        const float2 k = coef[u * Cg + c];
+        const float2 xo = xs[u * xstride];
+        float2 g = pp_partial_corr(h, r);
+        g.x = tile_sum_c<AT>(g.x, mask);
+        g.y = tile_sum_c<AT>(g.y, mask);
+        const float2 xn = make_float2(fmaf(k.x, g.x, k.y * xo.x), fmaf(k.x, g.y, k.y * xo.y));
+        xs[u * xstride] = xn;
+        const int un = u + 1 == U ? 0 : u + 1;
+        pp_update_reload<AT>(h, make_float2(xn.x - xo.x, xn.y - xo.y), r, hb + un * LP);
+        u = un;
+    }
+}
+
+// Algorithm 2 on one tile of a packed group (the beamformer x in registers, from zero), p^2 from coef;
+// pipelined like batched_detect_pp.
+template <int AT>
+__device__ __forceinline__ void batched_precode_pp(const float4* hb, int LP, int U, int K, const float2* coef, int Cg,
+                                                   int c, const float2* s, float4 (&x)[kPairs], unsigned mask)
+{
+#pragma unroll
+    for (int i = 0; i < kPairs; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (K <= 0 || U <= 0) return;
+    float4 h[kPairs];
+    pp_load_h<AT>(hb, h);
+    int u = 0;
+#pragma unroll 1
+    for (int step = 0; step < K * U; ++step) {
+        const float q = coef[u * Cg + c].x;
+        const float2 su = s[u];
+        float2 g = pp_partial_corr(h, x);
+        g.x = tile_sum_c<AT>(g.x, mask);
+        g.y = tile_sum_c<AT>(g.y, mask);
+        const int un = u + 1 == U ? 0 : u + 1;
+        pp_update_reload<AT>(h, make_float2(q * (g.x - su.x), q * (g.y - su.y)), x, hb + un * LP);
+        u = un;
+    }
 }
 
 // Body shared by the persistent batched kernel (items popped from `counter`) and the single-block
@@ -158,6 +214,15 @@ __device__ __forceinline__ void batched_body(const unsigned char* __restrict__ t
                 phase ^= 1u;
             }
             if (__syncthreads_or(!ok)) return;
+            const bool packed = P == kPP && G.packed;
+            if (packed) {  // (re0, im0, re1, im1) -> (re0, re1, im0, im1) per 16-byte pair of the group's rows
+                float4* h4 = reinterpret_cast<float4*>(Hs);
+                for (int i = tid; i < G.h_entries / 2; i += blockDim.x) {
+                    const float4 q = h4[i];
+                    h4[i] = make_float4(q.x, q.z, q.y, q.w);
+                }
+                __syncthreads();
+            }
 
             // Preprocessing: column energies, then (m, n) of Algorithm 1 or p^2 of Algorithm 2.
             for (int row = warp; row < U * Cg; row += nwarps) {
@@ -183,7 +248,46 @@ __device__ __forceinline__ void batched_body(const unsigned char* __restrict__ t
                 for (int i = tid; i < U * xs; i += blockDim.x) Xs[i] = make_float2(0.f, 0.f);
             __syncthreads();
 
-            if (lt.active) {
+            if (packed && lt.active) {
+                // Packed FP32 with the tile width fixed at compile time; every active lane of a warp has
+                // the same A (the host aligns each A class of a packed group to a warp).
+                const float4* hb4 = reinterpret_cast<const float4*>(Hs + ct.soff) + lt.a;
+                const int LP = ct.L / 2;
+                float4 w4[kPairs];
+                if (detect) {
+#pragma unroll
+                    for (int i = 0; i < kPairs; ++i)  // the receive vector, pair-planar
+                        w4[i] = make_float4(v[2 * i].x, v[2 * i + 1].x, v[2 * i].y, v[2 * i + 1].y);
+                    float2* xsp = Xs + tile;
+                    switch (lt.Awarp) {
+                    case 1: batched_detect_pp<1>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
+                    case 2: batched_detect_pp<2>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
+                    case 4: batched_detect_pp<4>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
+                    default: batched_detect_pp<8>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
+                    }
+                } else {
+                    const float2* sp = Ss + lt.n * s_stride;
+                    float nr = 0.f;
+                    switch (lt.Awarp) {
+                    case 1: batched_precode_pp<1>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
+                    case 2: batched_precode_pp<2>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
+                    case 4: batched_precode_pp<4>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
+                    default: batched_precode_pp<8>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
+                    }
+#pragma unroll
+                    for (int i = 0; i < kPairs; ++i)
+                        nr = fmaf(w4[i].x, w4[i].x, fmaf(w4[i].y, w4[i].y, fmaf(w4[i].z, w4[i].z, fmaf(w4[i].w, w4[i].w, nr))));
+                    for (int off = 1; off < lt.Awarp; off <<= 1) nr += __shfl_xor_sync(lt.mask, nr, off);
+                    const float sc = nr > 0.f ? D.rho_c * rsqrtf(nr) : 0.f;
+                    float2* out = reinterpret_cast<float2*>(D.out) + ((size_t)f * n_sym + lt.n) * D.B + ct.off;
+#pragma unroll
+                    for (int i = 0; i < kPairs; ++i) {
+                        const int col = 2 * (i * lt.A + lt.a);
+                        if (col < ct.size) out[col] = make_float2(w4[i].x * sc, w4[i].z * sc);
+                        if (col + 1 < ct.size) out[col + 1] = make_float2(w4[i].y * sc, w4[i].w * sc);
+                    }
+                }
+            } else if (lt.active) {
                 const float2* hb = Hs + ct.soff + 2 * lt.a;
                 if (detect) {
                     // Algorithm 1 on this tile.

@@ -199,6 +199,23 @@ __device__ __forceinline__ void pp_update(const float4 (&h)[kPairs], float2 d, f
     }
 }
 
+// pp_update, reloading each h[i] from the next row right after its last use (the loads of the next
+// step issue during this step's update without extra registers).
+template <int AT>
+__device__ __forceinline__ void pp_update_reload(float4 (&h)[kPairs], float2 d, float4 (&v)[kPairs], const float4* next)
+{
+    const float2 ndr = make_float2(-d.x, -d.x), pdi = make_float2(d.y, d.y), ndi = make_float2(-d.y, -d.y);
+#pragma unroll
+    for (int i = 0; i < kPairs; ++i) {
+        float2 re = ffma2(lo2(h[i]), ndr, lo2(v[i]));
+        float2 im = ffma2(lo2(h[i]), ndi, hi2(v[i]));
+        re = ffma2(hi2(h[i]), pdi, re);
+        im = ffma2(hi2(h[i]), ndr, im);
+        v[i] = cat4(re, im);
+        h[i] = next[i * AT];
+    }
+}
+
 // Wait for (bulk) or stage (converting) the channel of subcarrier f in buffer Hb, then permute it to
 // the pair-planar layout.  Returns false on a copy timeout (the whole CTA then stops).
 template <int IN>

@@ -669,8 +669,14 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
         return CDMIMO_ERR_INVALID_ARG;
     unsigned h_max = 0, x_max = 0, uc_max = 0, acc_max = 0, s_max = 0;
     int C_max = 1, items = 0;
-    for (int i = 0; i < n_desc; ++i) {
-        const cdmimo_batch_desc& q = d[i];
+    // Descriptors enter the table in order of decreasing work per item (K U n_sym B, stable), so the
+    // persistent CTAs pop the longest items first and the short ones fill the tail.
+    std::vector<int> ord(n_desc);
+    for (int i = 0; i < n_desc; ++i) ord[i] = i;
+    auto work = [&](int i) { return (double)d[i].K * d[i].U * d[i].n_sym * d[i].B; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work(a) > work(b); });
+    for (int oi = 0; oi < n_desc; ++oi) {
+        const cdmimo_batch_desc& q = d[ord[oi]];
         if (q.op != CDMIMO_OP_DETECT && q.op != CDMIMO_OP_PRECODE) return CDMIMO_ERR_INVALID_ARG;
         if (q.n_sc < 0 || q.n_sym < 1 || q.B < 1 || q.U < 1 || q.C < 1 || q.K < 0) return CDMIMO_ERR_INVALID_ARG;
         if (q.U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
@@ -708,7 +714,20 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
         bd.bulk = (all_even && aligned(q.H, 16)) ? 1 : 0;
         items += q.n_sc;
         const unsigned U = q.U, ns = q.n_sym;
-        // Greedy groups of consecutive clusters.
+        // Greedy groups of consecutive clusters.  With P = 16 a group whose clusters all have A <= 8
+        // runs the packed-FP32 sweeps, which need every warp's active lanes to share one A: each
+        // A class then starts at a warp boundary (the gaps are inactive lanes).
+        auto lane_count = [&](const std::vector<BatchCluster>& cs_, bool align) {
+            std::vector<int> as;
+            for (const BatchCluster& x : cs_) as.push_back(x.A);
+            std::stable_sort(as.begin(), as.end(), [](int a, int b) { return a > b; });
+            unsigned l = 0;
+            for (size_t k2 = 0; k2 < as.size(); ++k2) {
+                if (align && k2 > 0 && as[k2] != as[k2 - 1]) l = (l + 31u) & ~31u;
+                l += ns * (unsigned)as[k2];
+            }
+            return l;
+        };
         int off = 0, c = 0;
         while (c < q.C) {
             BatchGroup g{};
@@ -724,7 +743,11 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
                 if (bc.A > 32) return CDMIMO_ERR_UNSUPPORTED;
                 bc.L = bc.A * P;
                 const unsigned h2 = h + U * (unsigned)bc.L + 2u * (unsigned)bc.A;
-                const unsigned t2 = tiles + ns, l2 = lanes + ns * (unsigned)bc.A, cg2 = (unsigned)cur.size() + 1;
+                std::vector<BatchCluster> trial = cur;
+                trial.push_back(bc);
+                bool pk = P == 16;
+                for (const BatchCluster& x : trial) pk = pk && x.A <= 8;
+                const unsigned t2 = tiles + ns, l2 = lane_count(trial, pk), cg2 = (unsigned)cur.size() + 1;
                 const unsigned bytes = h2 * 8u + U * (t2 | 1u) * 8u + U * cg2 * 12u;
                 if (bytes > (unsigned)plan->group_bytes || l2 > (unsigned)T || cg2 > 64u) {
                     if (cur.empty()) return CDMIMO_ERR_UNSUPPORTED;
@@ -740,12 +763,18 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
                 off += bc.size;
                 ++c;
             }
-            // Lanes: clusters of the group in order of decreasing A (A-aligned lane groups).
+            // Lanes: clusters of the group in order of decreasing A (A-aligned lane groups; packed
+            // groups start each A class at a warp boundary).
+            bool pk = P == 16;
+            for (const BatchCluster& x : cur) pk = pk && x.A <= 8;
+            g.packed = pk ? 1 : 0;
             std::vector<int> order(cur.size());
             for (size_t k2 = 0; k2 < cur.size(); ++k2) order[k2] = (int)k2;
             std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cur[a].A > cur[b].A; });
-            int lane = 0;
+            int lane = 0, prevA = 0;
             for (int k2 : order) {
+                if (pk && prevA && cur[k2].A != prevA) lane = (lane + 31) & ~31;
+                prevA = cur[k2].A;
                 cur[k2].lane0 = lane;
                 lane += (int)ns * cur[k2].A;
             }

@@ -102,6 +102,26 @@ def test_odd_sizes_equal_fusion_and_converting_staging(dev):
     check_against_oracle(blocks, items, K=2, fuse="equal")
 
 
+@pytest.mark.parametrize("P", [16, 32])
+def test_packed_groups_with_every_tile_width(dev, P):
+    """Cluster sizes spanning one to eight (and sixteen) 16-antenna pairs per lane: with P = 16 the
+    groups whose clusters all have A <= 8 run the packed-FP32 sweeps, each A class of a group starting
+    at a warp boundary; A = 16 (B_c = 200) keeps its group on the generic sweeps.  Detection and
+    precoding against the oracle, for both tile sizes."""
+    blocks = []
+    for r, (cs, U) in enumerate([([128, 16, 40, 64, 8, 100], 8), ([200, 32, 16], 5), ([24, 24, 128, 16], 12)]):
+        d = wl.uplink(90 + r, 3, 14, sum(cs), U, snr_db=15.0)
+        d["S"] = wl.downlink(95 + r, 3, 14, sum(cs), U)["S"]
+        d["cluster_size"] = cs
+        blocks.append(d)
+    items = make_items(blocks, dev, with_precode=True)
+    b = batched.Batch(items, plan=batched.default_plan(P=P, threads=512, group_bytes=96 * 1024, ctas_per_sm=0))
+    b.run()
+    torch.cuda.synchronize()
+    check_against_oracle(blocks, items)
+    assert cdmimo.device_status(clear=True) == 0
+
+
 def test_graph_replay_matches_eager(dev):
     blocks = wl.resource_blocks(3, n_rb=10, n_sc=4, n_sym=14, downlink_too=True)
     items = make_items(blocks, dev, with_precode=True)
