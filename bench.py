@@ -733,7 +733,7 @@ def config4_items(dev):
 
 # Tile parameters of the batched kernel under `--profile batched` (the autotuner's usual choice on
 # the uneven batch), fixed so that the captured launches do not depend on timing.
-BATCH_PROFILE_PLAN = dict(P=16, threads=512, group_bytes=96 * 1024, ctas_per_sm=0)
+BATCH_PROFILE_PLAN = dict(P=16, threads=256, group_bytes=84 * 1024, ctas_per_sm=2)
 
 
 def run_config4(args, dev):
@@ -744,6 +744,7 @@ def run_config4(args, dev):
     blocks, items, flops = config4_items(dev)
     bt = batched.Batch(items)
     plan, times = batched.autotune(bt, reps=5)
+    lb = bt.balance()
     bt.capture()
     med, _ = time_device(bt.replay, args.steps, args.warmup, dev)
     n_vec = sum(b["H"].shape[0] * 14 for b in blocks)
@@ -761,6 +762,7 @@ def run_config4(args, dev):
                                "frac": tflops / FP32_PEAK_TFLOPS, "traffic": None},
                      autotune={"chosen": {k: getattr(plan, k) for k in ("P", "threads", "group_bytes", "ctas_per_sm")},
                                "candidates_ms": times},
+                     load_balance=lb,
                      separate_launches={"ms": med_sep, "vectors_per_s": n_vec / (med_sep * 1e-3),
                                         "speedup_of_one_launch": med_sep / med})
 
@@ -820,6 +822,7 @@ def config_summaries(args, dev):
     c4 = run_config4(sub, dev)
     out["4"] = {"workload": c4["config"]["workload"], "ms": c4["ms_per_step"], "vectors_per_s": c4["value"],
                 "fp32_frac": c4["roofline"]["frac"], "autotune_chosen": c4["autotune"]["chosen"],
+                "load_balance": c4["load_balance"],
                 "speedup_over_separate_launches": c4["separate_launches"]["speedup_of_one_launch"]}
     c5 = run_config5(sub, dev)
     v5 = c5["variants"]

@@ -292,7 +292,8 @@ typedef struct {
 typedef struct {
     /* tile parameters (inputs; cdmimo_batch_default_plan gives defaults, an autotuner may change them) */
     int P;            /* antennas per lane: 8, 16 or 32 */
-    int threads;      /* threads per CTA: multiple of 32 in [64, 512]; every cluster group's tiles fit */
+    int threads;      /* threads per CTA: multiple of 32 in [64, 512] ([64, 384] for P = 8); every cluster
+                         group's tiles fit */
     int group_bytes;  /* shared-memory budget of one cluster group (channel rows + per-tile state) */
     int ctas_per_sm;  /* persistent CTAs per SM, 0 = as many as fit */
     /* filled by cdmimo_batch_build */
@@ -321,6 +322,16 @@ int cdmimo_batch_build(const cdmimo_batch_desc* desc, int n_desc, cdmimo_batch_p
  * memory exceeds the device limit.
  */
 int cdmimo_detect_batched(const cdmimo_batch_plan* plan, const void* table_dev, int* counter, void* stream);
+
+/*
+ * cdmimo_detect_batched that also measures the work queue's load balance (an instrumentation aid; the
+ * paper has no counterpart): stats DEVICE unsigned long long[4], 8-byte aligned, reset by this call,
+ * receives {earliest CTA start, latest CTA end, sum of CTA lifetimes, number of CTAs} in global-timer
+ * nanoseconds, so sum / (CTAs x (end - start)) is the fraction of the launch's span the persistent
+ * CTAs spent working.  stats == NULL is cdmimo_detect_batched.  Same errors.
+ */
+int cdmimo_detect_batched_stats(const cdmimo_batch_plan* plan, const void* table_dev, int* counter,
+                                unsigned long long* stats, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- */
 /* Learned deep-unfolded CD (an extension beyond the paper; plain CD is the default).              */

@@ -104,6 +104,7 @@ def lib():
             "cdmimo_batch_default_plan": ([ctypes.POINTER(BatchPlan)], None),
             "cdmimo_batch_build": ([ctypes.POINTER(BatchDesc), I, ctypes.POINTER(BatchPlan), P, S], I),
             "cdmimo_detect_batched": ([ctypes.POINTER(BatchPlan), P, P, P], I),
+            "cdmimo_detect_batched_stats": ([ctypes.POINTER(BatchPlan), P, P, P, P], I),
             "cdmimo_synth_uplink": ([ctypes.c_ulonglong, I, I, I, I, I, P, P, P, P, P, P, P], I),
             "cdmimo_fusion_weights": ([PP, P, P, P, P], I),
             "cdmimo_pipe_probe_sink_floats": ([], S),

@@ -32,7 +32,7 @@ struct BatchGroup {
     int h_entries;      // complex entries of the group's channel region
     int padded;         // 1: some cluster of the group has B_c < A_c P
     int row_bytes;      // bytes of all bulk-copied rows of the group (U * sum B_c * 8)
-    int packed;         // 1: packed-FP32 sweeps (P = 16, every A_c <= 8, each A class warp-aligned)
+    int packed;         // 1: packed-FP32 sweeps (P = 16 or 8, every A_c <= 128 / P, each A class warp-aligned)
 };
 
 // Cluster entry; soff and lane0 are relative to the cluster's group.

@@ -46,12 +46,12 @@ __device__ __forceinline__ LaneTile map_lane_group(int n_lanes, int Cg, int n_sy
 // rows of step u + 1 are loaded while step u's update consumes the rows of step u (each register
 // is reloaded right after its last use), and the step's (m, n) and old x are read before the
 // correlation, so neither load latency sits on the step's dependency chain.
-template <int AT>
+template <int AT, int NP>
 __device__ __forceinline__ void batched_detect_pp(const float4* hb, int LP, int U, int K, const float2* coef, int Cg,
-                                                  int c, float2* xs, int xstride, float4 (&r)[kPairs], unsigned mask)
+                                                  int c, float2* xs, int xstride, float4 (&r)[NP], unsigned mask)
 {
     if (K <= 0 || U <= 0) return;
-    float4 h[kPairs];
+    float4 h[NP];
     pp_load_h<AT>(hb, h);
     int u = 0;
 #pragma unroll 1
@@ -71,14 +71,14 @@ __device__ __forceinline__ void batched_detect_pp(const float4* hb, int LP, int 
 
 // Algorithm 2 on one tile of a packed group (the beamformer x in registers, from zero), p^2 from coef;
 // pipelined like batched_detect_pp.
-template <int AT>
+template <int AT, int NP>
 __device__ __forceinline__ void batched_precode_pp(const float4* hb, int LP, int U, int K, const float2* coef, int Cg,
-                                                   int c, const float2* s, float4 (&x)[kPairs], unsigned mask)
+                                                   int c, const float2* s, float4 (&x)[NP], unsigned mask)
 {
 #pragma unroll
-    for (int i = 0; i < kPairs; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < NP; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (K <= 0 || U <= 0) return;
-    float4 h[kPairs];
+    float4 h[NP];
     pp_load_h<AT>(hb, h);
     int u = 0;
 #pragma unroll 1
@@ -214,7 +214,8 @@ __device__ __forceinline__ void batched_body(const unsigned char* __restrict__ t
                 phase ^= 1u;
             }
             if (__syncthreads_or(!ok)) return;
-            const bool packed = P == kPP && G.packed;
+            constexpr int NP = P / 2;  // antenna pairs per lane
+            const bool packed = (P == 16 || P == 8) && G.packed;
             if (packed) {  // (re0, im0, re1, im1) -> (re0, re1, im0, im1) per 16-byte pair of the group's rows
                 float4* h4 = reinterpret_cast<float4*>(Hs);
                 for (int i = tid; i < G.h_entries / 2; i += blockDim.x) {
@@ -253,17 +254,18 @@ __device__ __forceinline__ void batched_body(const unsigned char* __restrict__ t
                 // the same A (the host aligns each A class of a packed group to a warp).
                 const float4* hb4 = reinterpret_cast<const float4*>(Hs + ct.soff) + lt.a;
                 const int LP = ct.L / 2;
-                float4 w4[kPairs];
+                float4 w4[NP];
                 if (detect) {
 #pragma unroll
-                    for (int i = 0; i < kPairs; ++i)  // the receive vector, pair-planar
+                    for (int i = 0; i < NP; ++i)  // the receive vector, pair-planar
                         w4[i] = make_float4(v[2 * i].x, v[2 * i + 1].x, v[2 * i].y, v[2 * i + 1].y);
                     float2* xsp = Xs + tile;
                     switch (lt.Awarp) {
                     case 1: batched_detect_pp<1>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
                     case 2: batched_detect_pp<2>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
                     case 4: batched_detect_pp<4>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
-                    default: batched_detect_pp<8>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
+                    case 8: batched_detect_pp<8>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
+                    default: batched_detect_pp<16>(hb4, LP, U, D.K, coef, Cg, lt.c, xsp, xs, w4, lt.mask); break;
                     }
                 } else {
                     const float2* sp = Ss + lt.n * s_stride;
@@ -272,16 +274,17 @@ __device__ __forceinline__ void batched_body(const unsigned char* __restrict__ t
                     case 1: batched_precode_pp<1>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
                     case 2: batched_precode_pp<2>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
                     case 4: batched_precode_pp<4>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
-                    default: batched_precode_pp<8>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
+                    case 8: batched_precode_pp<8>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
+                    default: batched_precode_pp<16>(hb4, LP, U, D.K, coef, Cg, lt.c, sp, w4, lt.mask); break;
                     }
 #pragma unroll
-                    for (int i = 0; i < kPairs; ++i)
+                    for (int i = 0; i < NP; ++i)
                         nr = fmaf(w4[i].x, w4[i].x, fmaf(w4[i].y, w4[i].y, fmaf(w4[i].z, w4[i].z, fmaf(w4[i].w, w4[i].w, nr))));
                     for (int off = 1; off < lt.Awarp; off <<= 1) nr += __shfl_xor_sync(lt.mask, nr, off);
                     const float sc = nr > 0.f ? D.rho_c * rsqrtf(nr) : 0.f;
                     float2* out = reinterpret_cast<float2*>(D.out) + ((size_t)f * n_sym + lt.n) * D.B + ct.off;
 #pragma unroll
-                    for (int i = 0; i < kPairs; ++i) {
+                    for (int i = 0; i < NP; ++i) {
                         const int col = 2 * (i * lt.A + lt.a);
                         if (col < ct.size) out[col] = make_float2(w4[i].x * sc, w4[i].z * sc);
                         if (col + 1 < ct.size) out[col + 1] = make_float2(w4[i].y * sc, w4[i].w * sc);
@@ -379,11 +382,23 @@ __device__ __forceinline__ void batched_body(const unsigned char* __restrict__ t
     }
 }
 
+// P = 8 keeps fewer registers per lane (packed: 4 pairs), so two 384-thread CTAs share an SM.  With
+// `stats` non-null every CTA adds its lifetime (global-timer ns) to stats = {earliest start, latest
+// end, sum of lifetimes, CTAs}: the load balance of the work queue.
 template <int P>
-__global__ void __launch_bounds__(512) cd_batched_kernel(const unsigned char* __restrict__ table, const BatchLaunch bl,
-                                                         int* __restrict__ counter)
+__global__ void __launch_bounds__(P == 8 ? 384 : 512, P == 8 ? 2 : 1)
+    cd_batched_kernel(const unsigned char* __restrict__ table, const BatchLaunch bl, int* __restrict__ counter,
+                      unsigned long long* __restrict__ stats)
 {
+    const unsigned long long t0 = stats ? global_ns() : 0ull;
     batched_body<P>(table, bl, counter);
+    if (stats && threadIdx.x == 0) {
+        const unsigned long long t1 = global_ns();
+        atomicMin(&stats[0], t0);
+        atomicMax(&stats[1], t1);
+        atomicAdd(&stats[2], t1 - t0);
+        atomicAdd(&stats[3], 1ull);
+    }
 }
 
 // A one-descriptor table small enough to travel as a kernel parameter (same format as the device

@@ -136,11 +136,11 @@ __device__ __forceinline__ void raw_to_pairs(float4 (&v)[kPairs])
         v[i] = cat4(__fadd2_rn(make_float2(v[i].x, v[i].z), z), __fadd2_rn(make_float2(v[i].y, v[i].w), z));
 }
 
-template <int AT>
-__device__ __forceinline__ void pp_load_h(const float4* hr, float4 (&h)[kPairs])
+template <int AT, int N>
+__device__ __forceinline__ void pp_load_h(const float4* hr, float4 (&h)[N])
 {
 #pragma unroll
-    for (int i = 0; i < kPairs; ++i) h[i] = hr[i * AT];
+    for (int i = 0; i < N; ++i) h[i] = hr[i * AT];
 }
 
 template <int AT>
@@ -151,12 +151,14 @@ __device__ __forceinline__ float tile_sum_c(float v, unsigned mask)
     return v;
 }
 
-// Lane partial of conj(h)^T v over the lane's pairs (two independent accumulator sets).
-__device__ __forceinline__ float2 pp_partial_corr(const float4 (&h)[kPairs], const float4 (&v)[kPairs])
+// Lane partial of conj(h)^T v over the lane's pairs (two independent accumulator sets; N even).
+template <int N>
+__device__ __forceinline__ float2 pp_partial_corr(const float4 (&h)[N], const float4 (&v)[N])
 {
+    static_assert(N % 2 == 0, "pairs per lane must be even");
     float2 R0 = make_float2(0.f, 0.f), I0 = R0, J0 = R0, R1 = R0, I1 = R0, J1 = R0;
 #pragma unroll
-    for (int i = 0; i < kPairs; i += 2) {
+    for (int i = 0; i < N; i += 2) {
         R0 = ffma2(lo2(h[i]), lo2(v[i]), R0);
         I0 = ffma2(lo2(h[i]), hi2(v[i]), I0);
         J0 = ffma2(hi2(h[i]), lo2(v[i]), J0);
@@ -201,12 +203,12 @@ __device__ __forceinline__ void pp_update(const float4 (&h)[kPairs], float2 d, f
 
 // pp_update, reloading each h[i] from the next row right after its last use (the loads of the next
 // step issue during this step's update without extra registers).
-template <int AT>
-__device__ __forceinline__ void pp_update_reload(float4 (&h)[kPairs], float2 d, float4 (&v)[kPairs], const float4* next)
+template <int AT, int N>
+__device__ __forceinline__ void pp_update_reload(float4 (&h)[N], float2 d, float4 (&v)[N], const float4* next)
 {
     const float2 ndr = make_float2(-d.x, -d.x), pdi = make_float2(d.y, d.y), ndi = make_float2(-d.y, -d.y);
 #pragma unroll
-    for (int i = 0; i < kPairs; ++i) {
+    for (int i = 0; i < N; ++i) {
         float2 re = ffma2(lo2(h[i]), ndr, lo2(v[i]));
         float2 im = ffma2(lo2(h[i]), ndi, hi2(v[i]));
         re = ffma2(hi2(h[i]), pdi, re);

@@ -664,8 +664,8 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
 {
     if (!d || n_desc < 1 || !plan) return CDMIMO_ERR_INVALID_ARG;
     const int P = plan->P, T = plan->threads;
-    if ((P != 8 && P != 16 && P != 32) || T < 64 || T > 512 || (T & 31) || plan->group_bytes < 4096 ||
-        plan->ctas_per_sm < 0)
+    if ((P != 8 && P != 16 && P != 32) || T < 64 || T > (P == 8 ? 384 : 512) || (T & 31) ||
+        plan->group_bytes < 4096 || plan->ctas_per_sm < 0)
         return CDMIMO_ERR_INVALID_ARG;
     unsigned h_max = 0, x_max = 0, uc_max = 0, acc_max = 0, s_max = 0;
     int C_max = 1, items = 0;
@@ -714,8 +714,8 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
         bd.bulk = (all_even && aligned(q.H, 16)) ? 1 : 0;
         items += q.n_sc;
         const unsigned U = q.U, ns = q.n_sym;
-        // Greedy groups of consecutive clusters.  With P = 16 a group whose clusters all have A <= 8
-        // runs the packed-FP32 sweeps, which need every warp's active lanes to share one A: each
+        // Greedy groups of consecutive clusters.  With P = 16 (8) a group whose clusters all have
+        // A <= 8 (16) runs the packed-FP32 sweeps, which need every warp's active lanes to share one A: each
         // A class then starts at a warp boundary (the gaps are inactive lanes).
         auto lane_count = [&](const std::vector<BatchCluster>& cs_, bool align) {
             std::vector<int> as;
@@ -733,7 +733,7 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
             BatchGroup g{};
             g.c0 = c;
             g.cl0 = (int)bb->clusters.size();
-            unsigned h = 0, lanes = 0, tiles = 0, rowb = 0;
+            unsigned h = 0, tiles = 0, rowb = 0;
             std::vector<BatchCluster> cur;
             while (c < q.C) {
                 BatchCluster bc{};
@@ -745,8 +745,8 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
                 const unsigned h2 = h + U * (unsigned)bc.L + 2u * (unsigned)bc.A;
                 std::vector<BatchCluster> trial = cur;
                 trial.push_back(bc);
-                bool pk = P == 16;
-                for (const BatchCluster& x : trial) pk = pk && x.A <= 8;
+                bool pk = P == 16 || P == 8;
+                for (const BatchCluster& x : trial) pk = pk && x.A <= 128 / P;
                 const unsigned t2 = tiles + ns, l2 = lane_count(trial, pk), cg2 = (unsigned)cur.size() + 1;
                 const unsigned bytes = h2 * 8u + U * (t2 | 1u) * 8u + U * cg2 * 12u;
                 if (bytes > (unsigned)plan->group_bytes || l2 > (unsigned)T || cg2 > 64u) {
@@ -756,7 +756,6 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
                 bc.soff = (int)h;
                 h = h2;
                 tiles = t2;
-                lanes = l2;
                 rowb += U * (unsigned)bc.size * 8u;
                 if (bc.L != bc.size) g.padded = 1;
                 cur.push_back(bc);
@@ -765,8 +764,8 @@ int batch_split(const cdmimo_batch_desc* d, int n_desc, cdmimo_batch_plan* plan,
             }
             // Lanes: clusters of the group in order of decreasing A (A-aligned lane groups; packed
             // groups start each A class at a warp boundary).
-            bool pk = P == 16;
-            for (const BatchCluster& x : cur) pk = pk && x.A <= 8;
+            bool pk = P == 16 || P == 8;
+            for (const BatchCluster& x : cur) pk = pk && x.A <= 128 / P;
             g.packed = pk ? 1 : 0;
             std::vector<int> order(cur.size());
             for (size_t k2 = 0; k2 < cur.size(); ++k2) order[k2] = (int)k2;
@@ -842,7 +841,8 @@ BatchLaunch launch_from_plan(const cdmimo_batch_plan* plan)
 }
 
 template <int P>
-int launch_batched_t(const cdmimo_batch_plan* plan, const void* table, int* counter, cudaStream_t s)
+int launch_batched_t(const cdmimo_batch_plan* plan, const void* table, int* counter, unsigned long long* stats,
+                     cudaStream_t s)
 {
     auto k = cd_batched_kernel<P>;
     const BatchLaunch bl = launch_from_plan(plan);
@@ -861,7 +861,10 @@ int launch_batched_t(const cdmimo_batch_plan* plan, const void* table, int* coun
     if (plan->ctas_per_sm > 0) per_sm = std::min(per_sm, plan->ctas_per_sm);
     const int grid = std::max(1, std::min(plan->n_items, sms * per_sm));
     if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return CDMIMO_ERR_CUDA;
-    k<<<grid, plan->threads, bl.smem_bytes, s>>>(static_cast<const unsigned char*>(table), bl, counter);
+    if (stats && (cudaMemsetAsync(stats, 0xff, sizeof(unsigned long long), s) != cudaSuccess ||
+                  cudaMemsetAsync(stats + 1, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess))
+        return CDMIMO_ERR_CUDA;
+    k<<<grid, plan->threads, bl.smem_bytes, s>>>(static_cast<const unsigned char*>(table), bl, counter, stats);
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
@@ -1398,15 +1401,23 @@ int cdmimo_batch_build(const cdmimo_batch_desc* desc, int n_desc, cdmimo_batch_p
 
 int cdmimo_detect_batched(const cdmimo_batch_plan* plan, const void* table_dev, int* counter, void* stream)
 {
-    if (!plan || !table_dev || !counter || !aligned(table_dev, 16) || !aligned(counter, 4)) return CDMIMO_ERR_INVALID_ARG;
+    return cdmimo_detect_batched_stats(plan, table_dev, counter, nullptr, stream);
+}
+
+int cdmimo_detect_batched_stats(const cdmimo_batch_plan* plan, const void* table_dev, int* counter,
+                                unsigned long long* stats, void* stream)
+{
+    if (!plan || !table_dev || !counter || !aligned(table_dev, 16) || !aligned(counter, 4) || !aligned(stats, 8))
+        return CDMIMO_ERR_INVALID_ARG;
     if (plan->n_items == 0) return CDMIMO_OK;
-    if (plan->threads < 64 || plan->threads > 512 || (plan->threads & 31) || plan->smem_bytes == 0)
+    if (plan->threads < 64 || plan->threads > (plan->P == 8 ? 384 : 512) || (plan->threads & 31) ||
+        plan->smem_bytes == 0)
         return CDMIMO_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (plan->P) {
-    case 8: return launch_batched_t<8>(plan, table_dev, counter, s);
-    case 16: return launch_batched_t<16>(plan, table_dev, counter, s);
-    case 32: return launch_batched_t<32>(plan, table_dev, counter, s);
+    case 8: return launch_batched_t<8>(plan, table_dev, counter, stats, s);
+    case 16: return launch_batched_t<16>(plan, table_dev, counter, stats, s);
+    case 32: return launch_batched_t<32>(plan, table_dev, counter, stats, s);
     }
     return CDMIMO_ERR_INVALID_ARG;
 }

@@ -102,20 +102,21 @@ def test_odd_sizes_equal_fusion_and_converting_staging(dev):
     check_against_oracle(blocks, items, K=2, fuse="equal")
 
 
-@pytest.mark.parametrize("P", [16, 32])
-def test_packed_groups_with_every_tile_width(dev, P):
-    """Cluster sizes spanning one to eight (and sixteen) 16-antenna pairs per lane: with P = 16 the
-    groups whose clusters all have A <= 8 run the packed-FP32 sweeps, each A class of a group starting
-    at a warp boundary; A = 16 (B_c = 200) keeps its group on the generic sweeps.  Detection and
-    precoding against the oracle, for both tile sizes."""
+@pytest.mark.parametrize("P,threads", [(16, 512), (32, 512), (8, 384)])
+def test_packed_groups_with_every_tile_width(dev, P, threads):
+    """Cluster sizes spanning one to eight (and sixteen) lanes per tile: with P = 16 (8) the groups
+    whose clusters all have A <= 8 (16) run the packed-FP32 sweeps, each A class of a group starting
+    at a warp boundary; B_c = 200 (A = 16, or 32 at P = 8) keeps its group on the generic sweeps.
+    Detection and precoding against the oracle, for every tile size."""
     blocks = []
-    for r, (cs, U) in enumerate([([128, 16, 40, 64, 8, 100], 8), ([200, 32, 16], 5), ([24, 24, 128, 16], 12)]):
+    wide = [200, 32, 16] if P != 8 else [120, 32, 16]  # 200 antennas at P = 8 need 32 lanes x 14 symbols > 384
+    for r, (cs, U) in enumerate([([128, 16, 40, 64, 8, 100], 8), (wide, 5), ([24, 24, 128, 16], 12)]):
         d = wl.uplink(90 + r, 3, 14, sum(cs), U, snr_db=15.0)
         d["S"] = wl.downlink(95 + r, 3, 14, sum(cs), U)["S"]
         d["cluster_size"] = cs
         blocks.append(d)
     items = make_items(blocks, dev, with_precode=True)
-    b = batched.Batch(items, plan=batched.default_plan(P=P, threads=512, group_bytes=96 * 1024, ctas_per_sm=0))
+    b = batched.Batch(items, plan=batched.default_plan(P=P, threads=threads, group_bytes=96 * 1024, ctas_per_sm=0))
     b.run()
     torch.cuda.synchronize()
     check_against_oracle(blocks, items)
@@ -154,6 +155,12 @@ def test_autotune_and_full_size_sample(dev):
     torch.cuda.synchronize()
     check_against_oracle(blocks, items, sample=2)
     assert cdmimo.device_status(clear=True) == 0
+    # the instrumented launch: same outputs, and a load balance in (0, 1]
+    ref = [it["out"].clone() for it in items]
+    lb = b.balance()
+    torch.cuda.synchronize()
+    assert all(torch.equal(r, it["out"]) for r, it in zip(ref, items))
+    assert 0 < lb["efficiency"] <= 1.0 and lb["ctas"] >= 152 and lb["mean_cta_us"] <= lb["span_us"]
 
 
 def test_single_block_streaming_path(dev):

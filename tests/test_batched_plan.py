@@ -87,3 +87,94 @@ def test_table_buffer_too_small():
     off = (-buf.ctypes.data) % 16
     assert L.cdmimo_batch_build(arr, 1, ctypes.byref(plan), ctypes.c_void_p(buf.ctypes.data + off),
                                 plan.table_bytes - 16) == cdmimo.ERR_WORKSPACE
+
+
+DESC_DT = np.dtype([("H", "<u8"), ("V", "<u8"), ("N0", "<u8"), ("out", "<u8"), ("op", "<i4"), ("n_sc", "<i4"),
+                    ("n_sym", "<i4"), ("B", "<i4"), ("U", "<i4"), ("C", "<i4"), ("K", "<i4"), ("fuse", "<i4"),
+                    ("inv_Ex", "<f4"), ("rho_c", "<f4"), ("item0", "<i4"), ("group0", "<i4"), ("n_groups", "<i4"),
+                    ("bulk", "<i4")])
+GROUP_DT = np.dtype([(k, "<i4") for k in ("c0", "c1", "cl0", "n_lanes", "h_entries", "padded", "row_bytes",
+                                          "packed")])
+CLUSTER_DT = np.dtype([(k, "<i4") for k in ("off", "size", "A", "L", "soff", "lane0")])
+
+
+def parse_table(table):
+    hdr = np.frombuffer(table[:32].tobytes(), dtype=np.int32)
+    n_desc, n_items, n_groups, n_clusters = hdr[:4]
+    off_desc, off_group, off_cluster = hdr[4:7].view(np.uint32)
+    descs = np.frombuffer(table[off_desc:off_desc + n_desc * DESC_DT.itemsize].tobytes(), DESC_DT)
+    groups = np.frombuffer(table[off_group:off_group + n_groups * GROUP_DT.itemsize].tobytes(), GROUP_DT)
+    clus = np.frombuffer(table[off_cluster:off_cluster + n_clusters * CLUSTER_DT.itemsize].tobytes(), CLUSTER_DT)
+    return descs, groups, clus
+
+
+@pytest.mark.parametrize("P,T", [(16, 512), (16, 256), (8, 384), (32, 256)])
+def test_table_order_and_packed_lane_layout(P, T):
+    """Descriptors enter the table longest item first (K U n_sym B, stable); in packed groups (P = 16
+    or 8, every A <= 128 / P) each tile width starts at a warp boundary, lanes of different clusters
+    are disjoint and every group's lanes fit the CTA."""
+    g = np.random.default_rng(5)
+    blocks = []
+    for _ in range(40):
+        B = int(g.choice([128, 256, 512]))
+        cs = wl.random_partition(g, B)
+        if g.random() < 0.2:
+            cs = [128] + cs[:-1] if sum(cs[:-1]) + 128 == B else cs
+        blocks.append({"B": B, "U": int(g.integers(8, 65)), "cluster_size": cs})
+    arr, keep = descs_for(blocks)
+    rc, table = build(arr, len(blocks), batched.default_plan(P=P, threads=T, group_bytes=96 * 1024))
+    assert rc == cdmimo.OK
+    descs, groups, clus = parse_table(table)
+    work = descs["K"].astype(np.int64) * descs["U"] * descs["n_sym"] * descs["B"]
+    assert np.all(np.diff(work) <= 0)
+    assert sorted(descs["H"].tolist()) == sorted(arr[i].H for i in range(len(blocks)))
+    assert np.all(np.diff(descs["item0"]) == descs["n_sc"][:-1])
+    n_packed = 0
+    for d in descs:
+        for gi in range(d["group0"], d["group0"] + d["n_groups"]):
+            gr = groups[gi]
+            cl = clus[gr["cl0"]:gr["cl0"] + gr["c1"] - gr["c0"]]
+            assert gr["n_lanes"] <= T
+            spans = sorted((c["lane0"], c["lane0"] + d["n_sym"] * c["A"], c["A"]) for c in cl)
+            assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+            assert max(s[1] for s in spans) == gr["n_lanes"]
+            packed = P in (8, 16) and all(c["A"] <= 128 // P for c in cl)
+            assert gr["packed"] == int(packed)
+            if packed:
+                n_packed += 1
+                for a, b in zip(spans, spans[1:]):
+                    assert a[2] >= b[2]
+                    if a[2] != b[2]:
+                        assert b[0] % 32 == 0
+    assert (n_packed > 0) == (P in (8, 16))
+
+
+def test_p8_thread_limit():
+    arr, keep = descs_for([{"B": 64, "U": 8, "cluster_size": [32, 32]}])
+    assert build(arr, 1, batched.default_plan(P=8, threads=512))[0] == cdmimo.ERR_INVALID_ARG
+    assert build(arr, 1, batched.default_plan(P=8, threads=384))[0] == cdmimo.OK
+
+
+def test_occupancy_candidates_fill_the_sm():
+    """Each derived candidate's plan fits its CTAs per SM in shared memory, and one budget step more
+    would not (or would not build); shapes whose CTAs cannot hold a U = 64, 64-antenna cluster are
+    left out."""
+    g = np.random.default_rng(9)
+    blocks = []
+    for _ in range(60):
+        B = int(g.choice([128, 256, 512]))
+        blocks.append({"B": B, "U": int(g.integers(8, 65)), "cluster_size": wl.random_partition(g, B)})
+    arr, keep = descs_for(blocks)
+
+    class Stub:  # what the planner reads of a Batch
+        descs, items = arr, blocks
+
+    cands = batched.occupancy_candidates(Stub)
+    shapes = {(c["P"], c["threads"], c["ctas_per_sm"]) for c in cands}
+    assert shapes <= set(batched.OCCUPANCY_SHAPES) and (16, 512, 1) in shapes and (8, 384, 2) in shapes
+    for c in cands:
+        limit = batched.SMEM_PER_SM // c["ctas_per_sm"] - batched.SMEM_RESERVED_PER_CTA
+        sm = batched.plan_smem(Stub, batched.default_plan(**c))
+        assert sm is not None and sm <= limit
+        more = batched.plan_smem(Stub, batched.default_plan(**dict(c, group_bytes=c["group_bytes"] + 4096)))
+        assert more is None or more > limit or c["group_bytes"] + 4096 > limit
