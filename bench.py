@@ -48,16 +48,17 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 #   subcarrier for the Hermitian G_c, shared by the n_sym symbols (and by both directions of a frame).
 GRAM_G = C * (U * (U + 1) // 2) * (B // C) / N_SYM
 FLOP_PER_VEC = {"residual": 2 * K * U * B * 8, "gram": 8 * (K * C * U * U + U * B + GRAM_G)}
-FLOP_PER_VEC["gram_tc"] = FLOP_PER_VEC["gram_tc_phased"] = FLOP_PER_VEC["gram"]  # the same algorithm; its contractions run on the tensor cores
+FLOP_PER_VEC["gram_tc"] = FLOP_PER_VEC["gram_tc_phased"] = FLOP_PER_VEC["gram_tc_umma"] = FLOP_PER_VEC["gram"]  # the same algorithm; its contractions run on the tensor cores
 FRAME_FLOP_PER_VEC = {"residual": 2 * FLOP_PER_VEC["residual"], "gram": 8 * (2 * K * C * U * U + 2 * U * B + GRAM_G)}
 KERNELS = {"residual": ("cd_detect_pp_kernel", "cd_precode_pp_kernel"),
            "gram": ("cd_detect_gram_kernel", "cd_precode_gram_kernel"),
            "gram_tc": ("cd_frame_ws_kernel<uplink>", "cd_frame_ws_kernel<downlink>"),
-           "gram_tc_phased": ("cd_frame_tc_kernel<uplink>", "cd_frame_tc_kernel<downlink>")}
+           "gram_tc_phased": ("cd_frame_tc_kernel<uplink>", "cd_frame_tc_kernel<downlink>"),
+           "gram_tc_umma": ("cd_frame_ws_kernel<uplink>", "cd_frame_ws_kernel<downlink>")}
 # One-kernel TDD frames by form: FP32 Gram form, and Gram form with z, G_c and x_c = H_c w on the
 # tensor cores (split-TF32 MMAs; the sweeps, K C U^2 of the flops above, stay on the FP32 pipes).
 FRAME_KERNELS = {"gram": "cd_frame_gram_kernel", "gram_tc": "cd_frame_ws_kernel",
-                 "gram_tc_phased": "cd_frame_tc_kernel"}
+                 "gram_tc_phased": "cd_frame_tc_kernel", "gram_tc_umma": "cd_frame_ws_kernel"}
 # Per-pipe work of the one-kernel frame (Gram form on the tensor cores), per frame vector:
 #   FP32 pipes: the Gauss-Seidel sweeps, K U^2 complex MACs per cluster and direction;
 #   tensor pipes: z = H_c^H y_c, G_c = H_c^H H_c and x_c = H_c w, algorithmically the rest of
@@ -893,7 +894,8 @@ def main():
                     help="untimed: three cdmimo_detect / cdmimo_precode / cdmimo_detect_precode calls, for ncu "
                          "(detect_u32*: configuration 3's U = 32, 64-QAM batch, K = 3; batched: configuration 4's "
                          "uneven batch, three persistent launches)")
-    ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc", "gram_tc_phased"], default="auto",
+    ap.add_argument("--form", choices=["auto", "residual", "gram", "gram_tc", "gram_tc_phased", "gram_tc_umma"],
+                    default="auto",
                     help="CD evaluation form")
     ap.add_argument("--e2e-chunks", type=int, default=0,
                     help="chunks of the pipelined host-buffer frame in the e2e leg (0: the library's default)")

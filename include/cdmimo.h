@@ -93,6 +93,10 @@ typedef enum { CDMIMO_FUSE_EQUAL = 0, CDMIMO_FUSE_COLNORM = 1, CDMIMO_FUSE_LEARN
  *             current one; its results equal the phased kernel's bit for bit.
  *   GRAM_TC_PHASED  GRAM_TC always on the phased kernel (the phases of a subcarrier one after the
  *             other, two CTAs per SM), e.g. to compare the two kernels.
+ *   GRAM_TC_UMMA  GRAM_TC with G_c and z of the warp-specialized kernel formed on the tcgen05 tensor
+ *             cores (c64 storage, C <= 8; one thread issues the MMAs, accumulators in tensor
+ *             memory): the same split-TF32 products summed in another order, so results agree with
+ *             GRAM_TC to rounding; elsewhere it is GRAM_TC.
  *   AUTO      GRAM where it applies, every B_c >= 2 U (so G_c + (N0/Ex) I stays well conditioned
  *             in FP32) and it needs fewer complex MACs, on the tensor cores where GRAM_TC's kernel
  *             takes the call; else RESIDUAL.
@@ -102,7 +106,8 @@ typedef enum {
     CDMIMO_FORM_RESIDUAL = 1,
     CDMIMO_FORM_GRAM = 2,
     CDMIMO_FORM_GRAM_TC = 3,
-    CDMIMO_FORM_GRAM_TC_PHASED = 4
+    CDMIMO_FORM_GRAM_TC_PHASED = 4,
+    CDMIMO_FORM_GRAM_TC_UMMA = 5
 } cdmimo_form;
 
 /*

@@ -33,7 +33,7 @@ LEARNED_BLOCK_BYTES = 4 * 4 + 16 * 4 * 2 + 64 * 4 + 4 * 4 + 64 * 65 * 2 + 64 * 2
 
 C64, C16F, C16BF = 0, 1, 2
 FUSE = {"equal": 0, "colnorm": 1, "learned": 2}
-FORM = {"auto": 0, "residual": 1, "gram": 2, "gram_tc": 3, "gram_tc_phased": 4}
+FORM = {"auto": 0, "residual": 1, "gram": 2, "gram_tc": 3, "gram_tc_phased": 4, "gram_tc_umma": 5}
 OP_DETECT, OP_PRECODE, OP_FRAME = 0, 1, 2
 
 

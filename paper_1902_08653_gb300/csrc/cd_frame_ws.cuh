@@ -26,6 +26,7 @@
 // timed-out wait leave the loop on all MMA warps together.
 #pragma once
 #include "cd_frame_tc.cuh"
+#include "umma.cuh"
 
 namespace cdmimo {
 
@@ -43,7 +44,10 @@ struct WsLayout {
     unsigned off_S, st_S;      // [U][n_sym] float2: s of the subcarrier, transposed (downlink)
     unsigned off_lam, st_lam;  // [C] floats: fusion weights 1 / sum_u m_u
     unsigned off_tab, off_bar, smem_bytes;  // off_bar: [8] mbarriers, then [2] floats: the uplink output
-                                            // scale of the subcarrier in each z / x buffer
+                                            // scale of the subcarrier in each z / x buffer, then (T5) the
+                                            // MMA-completion mbarrier and the tensor-memory base address
+    unsigned off_op;    // T5: [6][16][2 BC] words of tcgen05 operands (t5_phase_a)
+    unsigned tmem_cols; // T5: tensor-memory columns allocated (64 per cluster, a power of two)
     int sweep_warps;  // warps of the sweep role (a multiple of four)
     int slot;         // sweep lanes per cluster (8 or 16, >= n_sym): a cluster's tiles fill a quarter or
                       // half warp, so that no quarter warp reads two clusters' Gram rows
@@ -84,13 +88,176 @@ __device__ __forceinline__ bool mma_group_and(bool ok)
     return r != 0;
 }
 
-template <int BC, int MODE, int IN>
+// Phase A on the 5th-generation tensor cores (c64 storage, clusters of BC = 16 or 32, C <= 8): for
+// each cluster the MMA warps write six K-major operand blocks of 16 rows x 2 BC FP32 words into `op`
+// (the real and imaginary parts of an antenna side by side along K), in this order:
+//     0 Y_lo  1 Y_hi  2 H_lo  3 H_hi  4 rot(H)_lo  5 rot(H)_hi
+// with H_u the channel row of user u, Y_n the receive samples of symbol n, rot(h) = (Im h, -Re h) per
+// antenna, and hi / lo the split-TF32 halves of cd_frame_tc.cuh.  One thread then issues, into
+// tensor-memory columns 64 c .. 64 c + 63, the M = 64, N = 64 product D = A B^T with A = blocks 0..3
+// and B = blocks 2..5: every pairing of a hi or lo half with a hi or lo half in one instruction per
+// 8 words of K (an M = 64, N = 64 tf32 MMA costs the device what an N = 32 one does).  Row by row,
+// P_re[v] = D[., v] + D[., 16 + v] and P_im[v] = D[., 32 + v] + D[., 48 + v] sum over B's halves, and
+// the sum over A's halves pairs two lane quarters:
+//     Re G_uv = P_re(H_lo u) + P_re(H_hi u),  Im G_uv = P_im(H_lo u) + P_im(H_hi u),
+//     Re z_vn = P_re(Y_lo n) + P_re(Y_hi n),  Im z_vn = -(P_im(Y_lo n) + P_im(Y_hi n))
+// (G_c = H_c^H H_c, z = H_c^H y_c; Sec. III-A).  An M = 64 accumulator keeps A's rows 16 q .. 16 q + 15
+// in lanes 32 q .. 32 q + 15, so warps of quarters 1 and 3 (Y_hi, H_hi) pass their partial rows
+// through shared memory (the operand buffer, free once the MMAs are done) to the warps of quarters 0
+// and 2, which write z and the pair-planar G rows, m_u, p_u^2 and the fusion weight exactly as
+// tc_phase_a does.  The operand buffer is reused per cluster (each cluster's MMAs are waited for
+// before the next is written).  yq holds this thread's receive samples of every cluster (row tid mod
+// 16, words 4 (tid / 16) .. + 3 of the cluster's span).  Returns false, on every MMA thread, when a
+// completion wait timed out.
+template <int BC, bool UL>
+__device__ __forceinline__ bool t5_phase_a(const CdPlan& pl, const ClusterTile* tab, const float* Hj, int srow,
+                                           float* op, uint64_t* barT, uint32_t& tpar, uint32_t tbase, float alpha,
+                                           float4* Gj, float* Dmj, float* Dpj, float2* Zj, uint32_t xs, float* Lj,
+                                           const float4 (&yq)[8])
+{
+    constexpr int UT = kTcUT, BLK = 32 * BC;             // words per operand block (16 rows x 2 BC)
+    constexpr uint32_t LBO = 128u, SBO = 64u * BC;       // bytes: next 4 words of K / next 8 rows
+    constexpr uint32_t idesc = umma_idesc_tf32(64, 64);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = tid & 15, kc = tid >> 4;                // this thread's chunk: row r, words 4 kc .. 4 kc + 3
+    const bool mine = kc < BC / 2;
+    const int U = pl.U, C = pl.C, n_sym = pl.n_sym;
+    const int cofs = (r >> 3) * (SBO / 4) + kc * 32 + (r & 7) * 4;  // word offset of the chunk in a block
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {  // unrolled: yq[c] stays in registers
+        if (c >= C) break;
+        if (c > 0) ok = mbar_wait_bounded(barT, (tpar++) & 1u);  // the MMAs of cluster c - 1 read op
+        if (mine) {
+            const float4 h = *reinterpret_cast<const float4*>(Hj + r * srow + 2 * tab[c].off + 4 * kc);
+            const float4 y = yq[c];
+            uint32_t hh[4], hl[4], yh[4], yl[4];
+            tf32_split(h.x, hh[0], hl[0]);
+            tf32_split(h.y, hh[1], hl[1]);
+            tf32_split(h.z, hh[2], hl[2]);
+            tf32_split(h.w, hh[3], hl[3]);
+            tf32_split(y.x, yh[0], yl[0]);
+            tf32_split(y.y, yh[1], yl[1]);
+            tf32_split(y.z, yh[2], yl[2]);
+            tf32_split(y.w, yh[3], yl[3]);
+            auto st = [&](int b, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3) {
+                *reinterpret_cast<uint4*>(op + b * BLK + cofs) = make_uint4(a0, a1, a2, a3);
+            };
+            st(0, yl[0], yl[1], yl[2], yl[3]);
+            st(1, yh[0], yh[1], yh[2], yh[3]);
+            st(2, hl[0], hl[1], hl[2], hl[3]);
+            st(3, hh[0], hh[1], hh[2], hh[3]);
+            st(4, hl[1], neg_bits(hl[0]), hl[3], neg_bits(hl[2]));
+            st(5, hh[1], neg_bits(hh[0]), hh[3], neg_bits(hh[2]));
+        }
+        fence_proxy_async_smem();
+        ok = mma_group_and(ok);
+        if (!ok) return false;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t dcol = tbase + 64u * (uint32_t)c;
+            // descriptors of k-step 0; k-step ks starts 2 core matrices (256 bytes, 16 address units) on
+            const uint64_t da = umma_desc(op, LBO, SBO), db = umma_desc(op + 2 * BLK, LBO, SBO);
+#pragma unroll
+            for (int ks = 0; ks < BC / 4; ++ks) umma_tf32(dcol, da + 16u * ks, db + 16u * ks, idesc, ks > 0 ? 1u : 0u);
+            umma_commit(barT);
+        }
+        __syncwarp();  // lanes 1..31 of warp 0 wait here, not in a sleeping poll interleaved with the issue
+    }
+    ok = mma_group_and(mbar_wait_bounded(barT, (tpar++) & 1u));
+    if (!ok) return false;
+    tc_fence_after();
+    // Epilogue, two rounds of four clusters: the warps of each half of the MMA warps take alternate
+    // clusters; quarter 3 (H_hi) and 1 (Y_hi) hand their partial rows over in op, quarters 2 and 0
+    // finish G and z.
+    const int q = warp & 3, half = warp >> 2;
+    float* scr = op;  // [4][16][32] G partials, then [4][16][32] z partials
+    for (int round = 0; round * 4 < C; ++round) {
+        float pr[UT], pi[UT];
+        int cs[2];
+        cs[0] = 4 * round + half;
+        cs[1] = 4 * round + 2 + half;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int c = cs[t];
+            if (c < C && (q == 1 || q == 3)) {
+                float v[32], w[32];
+                const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)c;
+                tmem_ld32(ta, v);
+                tmem_ld32(ta + 32u, w);
+                float* dst = scr + ((q == 3 ? 0 : 4) + (c & 3)) * 16 * 32 + (lane & 15) * 32;
+                if (lane < 16) {
+#pragma unroll
+                    for (int i = 0; i < UT; i += 4) {
+                        *reinterpret_cast<float4*>(dst + i) =
+                            make_float4(v[i] + v[16 + i], v[i + 1] + v[17 + i], v[i + 2] + v[18 + i], v[i + 3] + v[19 + i]);
+                        *reinterpret_cast<float4*>(dst + 16 + i) =
+                            make_float4(w[i] + w[16 + i], w[i + 1] + w[17 + i], w[i + 2] + w[18 + i], w[i + 3] + w[19 + i]);
+                    }
+                }
+            }
+        }
+        mma_group_and(true);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int c = cs[t];
+            if (c >= C || (q != 0 && q != 2)) continue;
+            float v[32], w[32];
+            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)c;
+            tmem_ld32(ta, v);
+            tmem_ld32(ta + 32u, w);
+            const float* src = scr + ((q == 2 ? 0 : 4) + (c & 3)) * 16 * 32 + (lane & 15) * 32;
+#pragma unroll
+            for (int i = 0; i < UT; ++i) {
+                pr[i] = v[i] + v[16 + i] + src[i];
+                pi[i] = w[i] + w[16 + i] + src[16 + i];
+            }
+            if (q == 2) {
+                const int u = lane;
+                float mu = 0.f;
+                if (u < UT) {
+                    float e = 0.f;  // Re G_uu, selected without a dynamic register index
+#pragma unroll
+                    for (int i = 0; i < UT; ++i) e = i == u ? pr[i] : e;
+                    const float den = e + alpha;
+                    mu = (u < U && den > 0.f) ? __fdividef(1.f, den) : 0.f;
+                    Dmj[c * UT + u] = mu;
+                    Dpj[c * UT + u] = (u < U && e > 0.f) ? __fdividef(1.f, e) : 0.f;
+                    float4* Gr = Gj + (size_t)c * UT * (UT / 2) + u * (UT / 2);
+#pragma unroll
+                    for (int i = 0; i < UT / 2; ++i) {
+                        float g0 = pr[2 * i], g1 = pr[2 * i + 1], i0 = pi[2 * i], i1 = pi[2 * i + 1];
+                        if (2 * i == u) g0 = i0 = 0.f;
+                        if (2 * i + 1 == u) g1 = i1 = 0.f;
+                        Gr[i] = make_float4(g0, g1, i0, i1);
+                    }
+                }
+                // fusion weight 1 / sum_u m_u (a skipped column counts as infinite)
+                float ms = (lane < U) ? (mu > 0.f ? mu : __int_as_float(0x7f800000)) : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ms += __shfl_xor_sync(0xffffffffu, ms, o);
+                if (lane == 0) Lj[c] = 1.f / ms;
+            } else if (UL && lane < n_sym) {
+                float2* z = Zj + c * n_sym + lane;
+#pragma unroll
+                for (int u = 0; u < UT; ++u)
+                    if (u < U) z[u * xs] = make_float2(pr[u], -pi[u]);
+            }
+        }
+        mma_group_and(true);  // the scratch is read before the next round (or the next cluster's operands) reuse it
+    }
+    tc_fence_before();
+    return true;
+}
+
+template <int BC, int MODE, int IN, bool T5 = false>
 __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdPlan pl, const WsLayout wl,
                                                                        const FusedIO io)
 {
     constexpr bool UL = MODE != kTcPrecode, DL = MODE != kTcDetect;
     static_assert(MODE == kTcFrame || MODE == kTcDetect || MODE == kTcPrecode, "plain modes only");
     static_assert(BC == 16 || BC == 32, "cluster size 16 or 32");
+    static_assert(!T5 || IN == CDMIMO_C64, "tcgen05 phase A: c64 storage");
     constexpr int UT = kTcUT;
     const int SROW = wl.srow;
     constexpr uint32_t eb = IN == CDMIMO_C64 ? 8u : 4u;  // bytes per stored complex entry
@@ -102,6 +269,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
     uint64_t* barH = reinterpret_cast<uint64_t*>(smem + wl.off_bar);  // [3] channel copies landed
     uint64_t* barA = barH + 3;                                         // [2] phase A done
     uint64_t* barS = barH + 5;                                         // [2] sweeps done
+    uint64_t* barT = barH + 9;                                         // tcgen05 MMAs done (T5)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(barH + 10);          // tensor-memory base (T5)
     auto Hb = [&](int s) { return reinterpret_cast<float*>(smem + wl.off_H + (unsigned)(s % 3) * wl.st_H); };
     auto Gb = [&](int s) { return reinterpret_cast<float4*>(smem + wl.off_G + (unsigned)(s & 1) * wl.st_G); };
     auto Dmb = [&](int s) { return reinterpret_cast<float*>(smem + wl.off_D + (unsigned)(s & 1) * wl.st_D); };
@@ -128,13 +297,18 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
             mbar_init(&barA[i], (uint32_t)kMmaThreads);
             mbar_init(&barS[i], (uint32_t)n_sw);
         }
+        if (T5) mbar_init(barT, 1u);
         fence_proxy_async_smem();
     }
+    if (T5 && warp == 0) tmem_alloc(tslot, wl.tmem_cols);  // one CTA per SM: the columns are free
     for (int j = 0; j < 3; ++j) {
         float* hb = Hb(j) + U * SROW;
         for (int i = tid; i < (UT - U) * SROW; i += blockDim.x) hb[i] = 0.f;
     }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = T5 ? *tslot : 0u;
 
     if (warp < kWsMmaWarps) {
         // ------------------------------------------------------------------ MMA role
@@ -161,6 +335,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
             }
         };
         const int gid = lane >> 2, tig = lane & 3;
+        uint32_t tpar = 0;           // T5: completions of barT waited for
         int issued = 0, landed = 0;  // channel copies issued / waited for (subcarriers 0 .. issued - 1)
         if (n_mine > 0) issue_copy(issued++);
         bool ok = true;
@@ -187,6 +362,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                     }
             };
             float2 sv = make_float2(0.f, 0.f);
+            float4 yq[8];  // T5: this thread's receive samples of every cluster (t5_phase_a)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) yq[c] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (do_a) {
                 if constexpr (UL) {
                     n0 = __ldg(d.N0 + fa);
@@ -194,7 +372,16 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                         hs = __ldg(d.h_scale + fa);
                         ys = __ldg(d.y_scale + fa);
                     }
-                    if (warp < C) load_yv(0, KP);
+                    if constexpr (T5) {
+                        const int r = tid & 15, kc = tid >> 4;
+                        const float* Yf = static_cast<const float*>(d.Y) + (size_t)fa * n_sym * pl.B * 2;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (c < C && r < n_sym && kc < BC / 2)
+                                yq[c] = __ldg(reinterpret_cast<const float4*>(Yf + ((size_t)r * pl.B + tab[c].off) * 2 + 4 * kc));
+                    } else if (warp < C) {
+                        load_yv(0, KP);
+                    }
                 }
                 if (DL && tid < n_s) sv = __ldg(io.S + (size_t)fa * n_s + tid);
             }
@@ -232,8 +419,15 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                 ok = mma_group_and(mbar_wait_bounded(&barH[j % 3], (uint32_t)(j / 3) & 1u));
                 if (!ok) break;
                 ++landed;
-                if (UL && warp < C) load_yv(KP, KA);
-                for (int c = warp; c < C; c += kWsMmaWarps) {
+                if constexpr (T5) {
+                    if (!t5_phase_a<BC, UL>(pl, tab, Hb(j), SROW, reinterpret_cast<float*>(smem + wl.off_op), barT, tpar,
+                                        tbase, alpha, Gb(j), Dmb(j), Dpb(j), Zb(j), xs, Lb(j), yq)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!T5 && UL && warp < C) load_yv(KP, KA);
+                for (int c = warp; !T5 && c < C; c += kWsMmaWarps) {
                     const ClusterTile ct = tab[c];
                     float* Dm = Dmb(j) + c * UT;
                     tc_phase_a<BC, IN, UL, false>(pl, Hb(j) + ct.off * ew, SROW, d.Y, (size_t)fa * n_sym * pl.B + ct.off,
@@ -259,8 +453,11 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
             }
         }
         // A copy still in flight (the loop left early): wait for it (bounded) before the CTA exits.
-        if (!ok && tid == 0)
+        if (!ok && tid == 0) {
             for (int s = landed; s < issued; ++s) mbar_wait_bounded(&barH[s % 3], (uint32_t)(s / 3) & 1u, 100000000ull);
+            // and MMAs (their commit not yet waited for) before the tensor memory is freed
+            if (T5) mbar_wait_bounded(barT, tpar & 1u, 100000000ull);
+        }
     } else {
         // ------------------------------------------------------------------ sweep role
         // One lane per (cluster, symbol) tile: the uplink x (right-hand side z) and the downlink w
@@ -294,7 +491,12 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
             mbar_arrive(&barS[s & 1]);
         }
     }
+    tc_fence_before();
     __syncthreads();
+    if (T5 && warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, wl.tmem_cols);
+    }
 }
 
 }  // namespace cdmimo

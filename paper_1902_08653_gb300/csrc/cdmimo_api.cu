@@ -65,7 +65,7 @@ int validate(const cdmimo_params* p)
     if (p->fuse != CDMIMO_FUSE_EQUAL && p->fuse != CDMIMO_FUSE_COLNORM && p->fuse != CDMIMO_FUSE_LEARNED)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_RESIDUAL && p->form != CDMIMO_FORM_GRAM &&
-        p->form != CDMIMO_FORM_GRAM_TC && p->form != CDMIMO_FORM_GRAM_TC_PHASED)
+        p->form != CDMIMO_FORM_GRAM_TC && p->form != CDMIMO_FORM_GRAM_TC_PHASED && p->form != CDMIMO_FORM_GRAM_TC_UMMA)
         return CDMIMO_ERR_INVALID_ARG;
     if (p->U > CDMIMO_MAX_USERS) return CDMIMO_ERR_UNSUPPORTED;
     if (!p->cluster_size || p->C > CDMIMO_MAX_CLUSTERS) return CDMIMO_ERR_BAD_PARTITION;
@@ -298,7 +298,8 @@ constexpr unsigned kTcTwoCtaSmem = (228u * 1024u - 2u * 1024u) / 2u;
 // GRAM and GRAM_TC ask for the Gram form (UNSUPPORTED where it does not apply).
 bool is_forced_gram(const cdmimo_params* p)
 {
-    return p->form == CDMIMO_FORM_GRAM || p->form == CDMIMO_FORM_GRAM_TC || p->form == CDMIMO_FORM_GRAM_TC_PHASED;
+    return p->form == CDMIMO_FORM_GRAM || p->form == CDMIMO_FORM_GRAM_TC || p->form == CDMIMO_FORM_GRAM_TC_PHASED ||
+           p->form == CDMIMO_FORM_GRAM_TC_UMMA;
 }
 
 // Tensor-core plan (any mode of cd_frame_tc_kernel): the Gram frame plan's cluster table and
@@ -309,7 +310,8 @@ bool is_forced_gram(const cdmimo_params* p)
 // form's own rules hold.  p->form must be AUTO or GRAM_TC.
 int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
 {
-    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC && p->form != CDMIMO_FORM_GRAM_TC_PHASED)
+    if (p->form != CDMIMO_FORM_AUTO && p->form != CDMIMO_FORM_GRAM_TC && p->form != CDMIMO_FORM_GRAM_TC_PHASED &&
+        p->form != CDMIMO_FORM_GRAM_TC_UMMA)
         return CDMIMO_ERR_UNSUPPORTED;
     if (p->in_dtype != CDMIMO_C64 && p->learned) return CDMIMO_ERR_UNSUPPORTED;
     if (op != CDMIMO_OP_DETECT && (p->learned || p->fuse == CDMIMO_FUSE_LEARNED)) return CDMIMO_ERR_UNSUPPORTED;
@@ -353,6 +355,7 @@ int build_tc_plan(const cdmimo_params* p, const void* H, int op, CdPlan* pl)
     pl->threads = 256;
     pl->UT = 16;
     pl->phased = p->form == CDMIMO_FORM_GRAM_TC_PHASED;
+    pl->umma = p->form == CDMIMO_FORM_GRAM_TC_UMMA;
     return CDMIMO_OK;
 }
 
@@ -1175,7 +1178,8 @@ int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H)
     if (op != CDMIMO_OP_DETECT && op != CDMIMO_OP_PRECODE && op != CDMIMO_OP_FRAME) return CDMIMO_ERR_INVALID_ARG;
     CdPlan pl;
     if (build_tc_plan(p, H, op, &pl) == CDMIMO_OK)
-        return p->form == CDMIMO_FORM_GRAM_TC_PHASED ? CDMIMO_FORM_GRAM_TC_PHASED : CDMIMO_FORM_GRAM_TC;
+        return (p->form == CDMIMO_FORM_GRAM_TC_PHASED || p->form == CDMIMO_FORM_GRAM_TC_UMMA) ? p->form
+                                                                                            : CDMIMO_FORM_GRAM_TC;
     if ((op == CDMIMO_OP_DETECT || op == CDMIMO_OP_FRAME) && build_tc32_plan(p, H, &pl) == CDMIMO_OK)
         return CDMIMO_FORM_GRAM_TC;  // the frame then runs as two calls, the uplink's on this kernel
     if (op == CDMIMO_OP_FRAME) {

@@ -44,6 +44,8 @@ struct CdPlan {
     int learned;      // 1: learned sweeps (and possibly learned fusion) from a cdmimo_learned block
     int phased;       // tensor-core plans: 1 = the phased kernel (cd_frame_tc_kernel) even where the
                       // warp-specialized one (cd_frame_ws_kernel) would take the call
+    int umma;         // tensor-core plans: 1 = the warp-specialized kernel forms G_c and z on the tcgen05
+                      // tensor cores where it can (c64, C <= 8), 0 = with mma.sync
     float inv_Ex;
     float rho_c;      // downlink per-cluster norm rho / sqrt(C)
     // byte offsets of the shared-memory regions (channel blocks start at 0; the packed kernels keep

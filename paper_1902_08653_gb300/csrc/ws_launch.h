@@ -16,7 +16,7 @@ inline unsigned ws_align(unsigned v, unsigned a) { return (v + a - 1u) / a * a; 
 // The kernel's layout for plan pl (built by build_tc_plan) and op; UNSUPPORTED where the kernel does
 // not take the call: a learned plan, more sweep lanes (C n_sym) than four warps hold, or a layout
 // above the device's shared memory per block.
-inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl)
+inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl, bool t5 = false)
 {
     if (pl.learned || pl.phased) return CDMIMO_ERR_UNSUPPORTED;
     if (pl.n_sym > 16) return CDMIMO_ERR_UNSUPPORTED;
@@ -34,6 +34,10 @@ inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl)
         o += (unsigned)n * st;
     };
     region(wl->off_H, wl->st_H, hbytes, 128u, 3);
+    const unsigned bc = (unsigned)pl.cl[0].size, blk = 16u * 2u * bc * 4u;  // T5 operand block bytes
+    unsigned st_op = 0;
+    wl->off_op = 0;
+    if (t5) region(wl->off_op, st_op, std::max(6u * blk, 16384u), 128u, 1);  // also the epilogue's scratch
     region(wl->off_G, wl->st_G, C * UT * (UT / 2) * 16u, 128u, 2);
     region(wl->off_D, wl->st_D, 2u * C * UT * 4u, 16u, 2);
     region(wl->off_Z, wl->st_Z, ul ? UT * xs * 8u : 0u, 16u, 2);
@@ -43,8 +47,10 @@ inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl)
     wl->off_tab = o;
     o = ws_align(o + C * (unsigned)sizeof(ClusterTile), 16u);
     wl->off_bar = o;
-    o = ws_align(o + 8u * 8u + 2u * 4u, 16u);
+    o = ws_align(o + 8u * 8u + 2u * 4u + 16u, 16u);
     wl->smem_bytes = o;
+    wl->tmem_cols = 32u;
+    while (t5 && wl->tmem_cols < 64u * C) wl->tmem_cols *= 2u;
     wl->sweep_warps = warps;
     wl->slot = slot;
     wl->srow = (int)srow;
@@ -55,10 +61,10 @@ inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl)
     return (int)wl->smem_bytes <= optin ? CDMIMO_OK : CDMIMO_ERR_UNSUPPORTED;
 }
 
-template <int BC, int MODE, int IN>
+template <int BC, int MODE, int IN, bool T5 = false>
 int ws_launch(const CdPlan& pl, const WsLayout& wl, const FusedIO& io, cudaStream_t s)
 {
-    auto k = cd_frame_ws_kernel<BC, MODE, IN>;
+    auto k = cd_frame_ws_kernel<BC, MODE, IN, T5>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.smem_bytes) != cudaSuccess)
         return CDMIMO_ERR_CUDA;
     const int threads = 32 * (kWsMmaWarps + wl.sweep_warps);
@@ -72,16 +78,40 @@ int ws_launch(const CdPlan& pl, const WsLayout& wl, const FusedIO& io, cudaStrea
     return cudaGetLastError() == cudaSuccess ? CDMIMO_OK : CDMIMO_ERR_CUDA;
 }
 
+// Whether the call runs phase A on the tcgen05 tensor cores: c64 storage, at most 8 clusters, the
+// plan asks for it, and (uplink) 16-byte aligned receive samples (read as float4).
+template <int IN>
+bool ws_use_t5(const CdPlan& pl, const FusedIO& io, int op)
+{
+    if (IN != CDMIMO_C64 || !pl.umma || pl.C > 8) return false;
+    return op == CDMIMO_OP_PRECODE || (reinterpret_cast<uintptr_t>(io.d.Y) & 15u) == 0u;
+}
+
 // CDMIMO_ERR_UNSUPPORTED (nothing launched) where the kernel does not take the call; op DETECT also
 // needs no per-cluster outputs (io.d.Xc, io.d.lam).
 template <int IN>
 int ws_dispatch_op(const CdPlan& pl, const FusedIO& io, int op, cudaStream_t s)
 {
-    WsLayout wl{};
-    if (int rc = build_ws_layout(pl, IN, op, &wl)) return rc;
-    if (op == CDMIMO_OP_DETECT && (io.d.Xc || io.d.lam)) return CDMIMO_ERR_UNSUPPORTED;
     const int bc = pl.cl[0].size;
     if (bc != 16 && bc != 32) return CDMIMO_ERR_UNSUPPORTED;
+    if (op == CDMIMO_OP_DETECT && (io.d.Xc || io.d.lam)) return CDMIMO_ERR_UNSUPPORTED;
+    WsLayout wl{};
+    if constexpr (IN == CDMIMO_C64) {
+        if (ws_use_t5<IN>(pl, io, op) && build_ws_layout(pl, IN, op, &wl, true) == CDMIMO_OK) {
+            switch (op) {
+            case CDMIMO_OP_FRAME:
+                return bc == 16 ? ws_launch<16, kTcFrame, IN, true>(pl, wl, io, s)
+                                : ws_launch<32, kTcFrame, IN, true>(pl, wl, io, s);
+            case CDMIMO_OP_DETECT:
+                return bc == 16 ? ws_launch<16, kTcDetect, IN, true>(pl, wl, io, s)
+                                : ws_launch<32, kTcDetect, IN, true>(pl, wl, io, s);
+            case CDMIMO_OP_PRECODE:
+                return bc == 16 ? ws_launch<16, kTcPrecode, IN, true>(pl, wl, io, s)
+                                : ws_launch<32, kTcPrecode, IN, true>(pl, wl, io, s);
+            }
+        }
+    }
+    if (int rc = build_ws_layout(pl, IN, op, &wl)) return rc;
     switch (op) {
     case CDMIMO_OP_FRAME:
         return bc == 16 ? ws_launch<16, kTcFrame, IN>(pl, wl, io, s) : ws_launch<32, kTcFrame, IN>(pl, wl, io, s);

@@ -2,12 +2,15 @@
 form on the tensor cores (form GRAM_TC, and AUTO where it applies) with the phases of consecutive
 subcarriers overlapped in one CTA per SM.
 
-It evaluates exactly the operations of the phased kernel (cd_frame_tc_kernel, form
-GRAM_TC_PHASED) in the same order, only scheduled differently, so the two must agree bit for bit;
-each case is also held to the FP64 oracle at 1e-4 relative L2 per vector.  The shapes cover the
-pipeline's edges: CTAs with zero, one, two and three subcarriers (the fill and drain of a
-three-stage pipeline), users below the 16-row tiles, one symbol, K = 1 and K = 5, clusters of 16
-and 32 antennas, and 16-bit storage.
+With its contractions on mma.sync (form GRAM_TC) it evaluates exactly the operations of the phased
+kernel (cd_frame_tc_kernel, form GRAM_TC_PHASED) in the same order, only scheduled differently, so
+the two must agree bit for bit.  With G_c and z formed on the tcgen05 tensor cores (form
+GRAM_TC_UMMA with c64 storage) the same split-TF32 products are summed in another order: those
+results must stay within 1e-5 of the mma.sync ones.  Each case is also held to the FP64
+oracle at 1e-4 relative L2 per vector.  The shapes cover the pipeline's edges: CTAs with zero, one,
+two and three subcarriers (the fill and drain of a three-stage pipeline), users below the 16-row
+tiles, one symbol, K = 1 and K = 5, clusters of 16 and 32 antennas, fewer than eight clusters, and
+16-bit storage.
 """
 import numpy as np
 import pytest
@@ -68,7 +71,18 @@ CASES = {
     "K5_one_symbol": (170, 1, [32] * 4, 16, 5, "colnorm", "c64"),
     "Bc16_C8_U12_n_sym9": (160, 9, [16] * 8, 12, 3, "colnorm", "c64"),
     "Bc16_C6_bf16_odd": (99, 5, [16] * 6, 13, 2, "colnorm", "bf16"),
+    "Bc32_C3_U11_n_sym7": (240, 7, [32] * 3, 11, 3, "colnorm", "c64"),
+    "Bc16_C1_U10": (153, 14, [16], 10, 2, "colnorm", "c64"),
 }
+
+
+def run_three(x, cs, K, fuse, form):
+    args = (x["H"], x["Y"], x["N0"], x["S"], cs, K)
+    X, P = cdmimo.detect_precode(*args, fuse=fuse, form=form, **x["sc"])
+    D = cdmimo.detect(x["H"], x["Y"], x["N0"], cs, K, fuse=fuse, form=form, **x["sc"])
+    Q = cdmimo.precode(x["H"], x["S"], cs, K, form=form)
+    torch.cuda.synchronize()
+    return X, P, D, Q
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -77,44 +91,49 @@ def test_ws_equals_phased_and_matches_oracle(dev, name):
     x = inputs(dev, 700 + len(name), n_sc, n_sym, cs, U, kind)
     code = KINDS[kind][1]
     B = sum(cs)
-    assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, K, in_dtype=code, H=x["H"],
-                                form="gram_tc") == "gram_tc"
-    assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, K, in_dtype=code, H=x["H"],
-                                form="gram_tc_phased") == "gram_tc_phased"
-    args = (x["H"], x["Y"], x["N0"], x["S"], cs, K)
-    Xw, Pw = cdmimo.detect_precode(*args, fuse=fuse, form="gram_tc", **x["sc"])
-    Xp, Pp = cdmimo.detect_precode(*args, fuse=fuse, form="gram_tc_phased", **x["sc"])
-    Dw = cdmimo.detect(x["H"], x["Y"], x["N0"], cs, K, fuse=fuse, form="gram_tc", **x["sc"])
-    Dp = cdmimo.detect(x["H"], x["Y"], x["N0"], cs, K, fuse=fuse, form="gram_tc_phased", **x["sc"])
-    Qw = cdmimo.precode(x["H"], x["S"], cs, K, form="gram_tc")
-    Qp = cdmimo.precode(x["H"], x["S"], cs, K, form="gram_tc_phased")
-    torch.cuda.synchronize()
-    assert torch.equal(Xw, Xp) and torch.equal(Pw, Pp), "frame: warp-specialized != phased"
-    assert torch.equal(Dw, Dp), "detect: warp-specialized != phased"
-    assert torch.equal(Qw, Qp), "precode: warp-specialized != phased"
+    for form in ("gram_tc", "gram_tc_phased", "gram_tc_umma"):
+        assert cdmimo.selected_form(cdmimo.OP_FRAME, n_sc, n_sym, B, U, cs, K, in_dtype=code, H=x["H"],
+                                    form=form) == form
+    sync = run_three(x, cs, K, fuse, "gram_tc")
+    phased = run_three(x, cs, K, fuse, "gram_tc_phased")
+    for a, b, what in zip(sync, phased, ("frame Xhat", "frame Xdl", "detect", "precode")):
+        assert torch.equal(a, b), f"{what}: warp-specialized (mma.sync) != phased"
+    t5 = run_three(x, cs, K, fuse, "gram_tc_umma")
     Xo, _, _ = orc.detect(x["H64"], x["Y64"], x["N064"], cs, K, fuse=fuse, threads=8)
     Po = orc.precode(x["H64"], x["S64"], cs, K, threads=8)
-    for got, ref, what in ((Xw, Xo, "frame Xhat"), (Pw, Po, "frame Xdl"), (Dw, Xo, "detect"), (Qw, Po, "precode")):
+    for got, ref, what in zip(t5, (Xo, Po, Xo, Po), ("frame Xhat", "frame Xdl", "detect", "precode")):
         assert_vectors_close(got.cpu().numpy(), ref, TOL, f"ws {what}")
+    for a, b, what in zip(t5, sync, ("frame Xhat", "frame Xdl", "detect", "precode")):
+        if kind == "c64":  # tcgen05 contractions: the same products in another order
+            assert_vectors_close(a.cpu().numpy(), b.cpu().numpy(), 1e-5, f"tcgen05 vs mma.sync {what}")
+        else:
+            assert torch.equal(a, b), f"{what}: 16-bit storage runs the mma.sync kernel"
     assert cdmimo.device_status(clear=True) == 0
 
 
 def test_ws_full_size_equals_phased(dev):
-    """The benchmark's batch (1200 x 14, B = 256 in 8 x 32, U = 16, K = 3): both kernels and all
-    three modes; with a schedule workspace (the phased kernel's dynamic schedule, twice in a row so
-    the counters must have reset themselves) the results are the same bits."""
+    """The benchmark's batch (1200 x 14, B = 256 in 8 x 32, U = 16, K = 3): the mma.sync kernel (the
+    default) and all three modes equal the phased kernel bit for bit, also with a schedule workspace
+    (the phased kernel's dynamic schedule, twice in a row so the counters must have reset
+    themselves); the tcgen05 variant stays within 1e-5 of them, and repeats its own bits."""
     cs, U, K, n_sc = [32] * 8, 16, 3, 1200
     x = inputs(dev, 20190222, n_sc, 14, cs, U)
     args = (x["H"], x["Y"], x["N0"], x["S"], cs, K)
     ref = cdmimo.detect_precode(*args, form="gram_tc_phased")
-    for ws in (None, True, True):
-        got = cdmimo.detect_precode(*args, workspace=ws)
+    for ws, form in ((None, "auto"), (True, "auto"), (True, "auto")):
+        got = cdmimo.detect_precode(*args, workspace=ws, form=form)
         torch.cuda.synchronize()
         assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
     assert torch.equal(cdmimo.detect(x["H"], x["Y"], x["N0"], cs, K),
                        cdmimo.detect(x["H"], x["Y"], x["N0"], cs, K, form="gram_tc_phased"))
     assert torch.equal(cdmimo.precode(x["H"], x["S"], cs, K),
                        cdmimo.precode(x["H"], x["S"], cs, K, form="gram_tc_phased"))
+    t5 = cdmimo.detect_precode(*args, form="gram_tc_umma")
+    t5b = cdmimo.detect_precode(*args, form="gram_tc_umma")
+    torch.cuda.synchronize()
+    assert torch.equal(t5[0], t5b[0]) and torch.equal(t5[1], t5b[1])
+    for a, b in zip(t5, ref):
+        assert_vectors_close(a.cpu().numpy(), b.cpu().numpy(), 1e-5, "tcgen05 vs mma.sync, full size")
     assert cdmimo.device_status(clear=True) == 0
 
 
