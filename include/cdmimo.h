@@ -485,6 +485,21 @@ int cdmimo_selected_form(const cdmimo_params* p, int op, const void* H);
 size_t cdmimo_pipe_probe_sink_floats(void);
 int cdmimo_pipe_probe(int kind, int iters, float* sink, size_t sink_floats, double* flops, void* stream);
 
+/*
+ * Probes of the tcgen05 tensor cores behind form GRAM_TC_UMMA (measurement aids; the paper has no
+ * counterpart).
+ * cdmimo_umma_layout_probe: one CTA forms D = A B^T (tf32 in, FP32 accumulate; M = 64 or 128 rows,
+ *   N = 32, K = 32) with the library's operand layout and MMA issue, and copies all 128 tensor-memory
+ *   lanes x 32 columns to D.  A DEVICE float[M][32], B DEVICE float[32][32], row-major; D DEVICE
+ *   float[128][32] (lane-major; lanes no row maps to keep whatever the accumulator held).
+ * cdmimo_umma_rate_probe: one thread issues n (1..4096) back-to-back M x N x 8 tf32 MMAs (M 64 or 128,
+ *   N a multiple of 16 in [16, 256]) into one accumulator, commits and waits; *cycles (DEVICE long
+ *   long) receives the best of five runs in SM clock cycles, or -1 if a wait timed out.
+ * Both enqueue one launch on `stream`.  Errors: INVALID_ARG, CUDA_ERROR.
+ */
+int cdmimo_umma_layout_probe(int M, const float* A, const float* B, float* D, void* stream);
+int cdmimo_umma_rate_probe(int M, int N, int n, long long* cycles, void* stream);
+
 /* Static name of a status code. */
 const char* cdmimo_status_string(int status);
 

@@ -105,6 +105,8 @@ def lib():
             "cdmimo_batch_build": ([ctypes.POINTER(BatchDesc), I, ctypes.POINTER(BatchPlan), P, S], I),
             "cdmimo_detect_batched": ([ctypes.POINTER(BatchPlan), P, P, P], I),
             "cdmimo_detect_batched_stats": ([ctypes.POINTER(BatchPlan), P, P, P, P], I),
+            "cdmimo_umma_layout_probe": ([I, P, P, P, P], I),
+            "cdmimo_umma_rate_probe": ([I, I, I, P, P], I),
             "cdmimo_synth_uplink": ([ctypes.c_ulonglong, I, I, I, I, I, P, P, P, P, P, P, P], I),
             "cdmimo_fusion_weights": ([PP, P, P, P, P], I),
             "cdmimo_pipe_probe_sink_floats": ([], S),
@@ -503,6 +505,27 @@ def pipe_probe(kind, iters, sink, stream=None):
 
 def pipe_probe_sink_floats():
     return int(lib().cdmimo_pipe_probe_sink_floats())
+
+
+def umma_layout_probe(M, A, B, stream=None):
+    """cdmimo_umma_layout_probe: D = A B^T on the tcgen05 tensor cores (A [M, 32], B [32, 32] float32
+    device tensors, M 64 or 128); returns all 128 tensor-memory lanes x 32 columns as a [128, 32]
+    tensor (lane-major)."""
+    _need(A, "A")
+    _need(B, "B")
+    D = torch.full((128, 32), float("nan"), dtype=torch.float32, device=A.device)
+    _check("cdmimo_umma_layout_probe", lib().cdmimo_umma_layout_probe(int(M), _ptr(A), _ptr(B), _ptr(D),
+                                                                      _stream(stream)))
+    return D
+
+
+def umma_rate_probe(M, N, n, stream=None):
+    """cdmimo_umma_rate_probe: SM cycles of n back-to-back M x N x 8 tf32 tcgen05 MMAs from one thread
+    (best of five, commit and wait included); -1 if a wait timed out."""
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check("cdmimo_umma_rate_probe", lib().cdmimo_umma_rate_probe(int(M), int(N), int(n), _ptr(out),
+                                                                  _stream(stream)))
+    return int(out.item())
 
 
 def fusion_weights(H, N0, cluster_size, *, Ex=1.0, fuse="colnorm", h_scale=None, out=None, stream=None):
