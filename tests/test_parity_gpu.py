@@ -244,3 +244,34 @@ def test_low_precision_staging_paths(dev, cs, U):
         Xd = cdmimo.precode(torch.from_numpy(qHd.view(np.int16)).to(dev).view(tdt), to_dev(S32, dev), cs,
                             3).cpu().numpy()
         assert_vectors_close(Xd, orc.precode(dHd, S64, cs, 3), TOL, f"{kind} precode {cs}")
+
+
+@pytest.mark.parametrize("kind", ["c64", "f16", "bf16"])
+@pytest.mark.parametrize("U", [24, 32, 48, 64])
+def test_user_counts_every_storage(dev, U, kind):
+    """Detection and precoding at U = 24, 32, 48 and 64 users (B = 256 in clusters of 32, so U > B_c
+    for the last two) in every storage format, on whatever form AUTO picks (the tensor-core kernel
+    for U <= 32, the residual kernels above): parity with the oracle on the values the GPU receives
+    (dequantized for 16-bit storage)."""
+    n_sc, n_sym, cs, K = 40, 14, [32] * 8, 3
+    d = wl.uplink(500 + U, n_sc, n_sym, sum(cs), U, snr_db=wl.sweep_snr(n_sc), M=16)
+    N0 = d["N0"].astype(np.float32)
+    if kind == "c64":
+        Ht, dH = to_dev(wl.as_c64(d["H"])[0], dev), wl.as_c64(d["H"])[1]
+        Yt, dY = to_dev(wl.as_c64(d["Y"])[0], dev), wl.as_c64(d["Y"])[1]
+        sc = {}
+    else:
+        tdt = torch.float16 if kind == "f16" else torch.bfloat16
+        qH, sH, dH = wl.quantize_c16(d["H"], kind)
+        qY, sY, dY = wl.quantize_c16(d["Y"], kind)
+        Ht = torch.from_numpy(qH.view(np.int16)).to(dev).view(tdt)
+        Yt = torch.from_numpy(qY.view(np.int16)).to(dev).view(tdt)
+        sc = dict(h_scale=to_dev(sH, dev), y_scale=to_dev(sY, dev))
+    Xg = cdmimo.detect(Ht, Yt, to_dev(N0, dev), cs, K, **sc).cpu().numpy()
+    Xo, _, _ = orc.detect(dH, dY, N0.astype(np.float64), cs, K, threads=8)
+    assert_vectors_close(Xg, Xo, TOL, f"detect U={U} {kind}")
+    if kind == "c64":
+        S32, S64 = wl.as_c64(d["X"])
+        Pg = cdmimo.precode(Ht, to_dev(S32, dev), cs, K).cpu().numpy()
+        assert_vectors_close(Pg, orc.precode(dH, S64, cs, K, threads=8), TOL, f"precode U={U}")
+    assert cdmimo.device_status(clear=True) == 0
