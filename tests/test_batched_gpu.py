@@ -182,3 +182,25 @@ def test_single_block_streaming_path(dev):
         cdmimo.detect(t(d["H"]), t(d["Y"]), N0, cs, 3,
                       Xc=torch.zeros((3, 8, 14, 64), dtype=torch.complex64, device=dev))
     assert e.value.status == cdmimo.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("P,threads", [(16, 256), (8, 384)])
+def test_packed_groups_edge_cases(dev, P, threads):
+    """Packed groups at the edges: one user, one symbol, K = 0 (zero estimates and beamformers),
+    K = 1, and a block whose clusters all take one lane per tile; detection and precoding against
+    the oracle."""
+    specs = [([16, 16, 32], 1, 1, 3), ([64, 16], 5, 14, 0), ([32] * 4, 9, 3, 1), ([16] * 6, 12, 14, 2)]
+    for P_ in (P,):
+        for r, (cs, U, n_sym, K) in enumerate(specs):
+            d = wl.uplink(300 + r, 3, n_sym, sum(cs), U, snr_db=12.0)
+            d["S"] = wl.downlink(310 + r, 3, n_sym, sum(cs), U)["S"]
+            d["cluster_size"] = cs
+            items = make_items([d], dev, K=K, with_precode=True)
+            b = batched.Batch(items, plan=batched.default_plan(P=P_, threads=threads, group_bytes=64 * 1024,
+                                                               ctas_per_sm=0))
+            b.run()
+            torch.cuda.synchronize()
+            check_against_oracle([d], items, K=K)
+            if K == 0:
+                assert not items[0]["out"].abs().any() and not items[1]["out"].abs().any()
+    assert cdmimo.device_status(clear=True) == 0
