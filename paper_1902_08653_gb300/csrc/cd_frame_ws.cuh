@@ -305,9 +305,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         float* hb = Hb(j) + U * SROW;
         for (int i = tid; i < (UT - U) * SROW; i += blockDim.x) hb[i] = 0.f;
     }
-    tc_fence_before();
+    if (T5) tc_fence_before();
     __syncthreads();
-    tc_fence_after();
+    if (T5) tc_fence_after();
     const uint32_t tbase = T5 ? *tslot : 0u;
 
     if (warp < kWsMmaWarps) {
@@ -363,8 +363,10 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
             };
             float2 sv = make_float2(0.f, 0.f);
             float4 yq[8];  // T5: this thread's receive samples of every cluster (t5_phase_a)
+            if constexpr (T5) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) yq[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int c = 0; c < 8; ++c) yq[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             if (do_a) {
                 if constexpr (UL) {
                     n0 = __ldg(d.N0 + fa);
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
             mbar_arrive(&barS[s & 1]);
         }
     }
-    tc_fence_before();
+    if (T5) tc_fence_before();
     __syncthreads();
     if (T5 && warp == 0) {
         tc_fence_after();
