@@ -31,7 +31,8 @@
 namespace cdmimo {
 
 constexpr int kWsMmaWarps = 8;
-constexpr int kWsMaxThreads = 32 * kWsMmaWarps + 128;  // 8 MMA warps + up to 4 sweep warps
+constexpr int kWsSweepGroups = 2;  // sweep groups of four warps, taking alternate subcarriers
+constexpr int kWsMaxThreads = 32 * kWsMmaWarps + kWsSweepGroups * 128;  // 512 threads, 128 registers each
 
 // Shared-memory layout of cd_frame_ws_kernel (byte offsets), built on the host.  Buffer i of a
 // region starts at off + i * stride (three channel buffers, two of everything else).
@@ -48,7 +49,7 @@ struct WsLayout {
                                             // MMA-completion mbarrier and the tensor-memory base address
     unsigned off_op;    // T5: [6][16][2 BC] words of tcgen05 operands (t5_phase_a)
     unsigned tmem_cols; // T5: tensor-memory columns allocated (64 per cluster, a power of two)
-    int sweep_warps;  // warps of the sweep role (a multiple of four)
+    int sweep_warps;  // warps of one sweep group (four); kWsSweepGroups groups run
     int slot;         // sweep lanes per cluster (8 or 16, >= n_sym): a cluster's tiles fill a quarter or
                       // half warp, so that no quarter warp reads two clusters' Gram rows
     int srow;         // 32-bit words per channel row (ws_row_words)
@@ -312,7 +313,6 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
 
     if (warp < kWsMmaWarps) {
         // ------------------------------------------------------------------ MMA role
-        constexpr int KA = BC / 4;
         float* osc = reinterpret_cast<float*>(barH + 8);  // [2] uplink output scale per z / x buffer
         // Copies of subcarrier s's channel rows into buffer s mod 3: warp w copies users w, w + 8, ...
         // (whole rows of B entries); its lane 0 announces their bytes on the buffer's barrier (one
@@ -334,33 +334,19 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                 }
             }
         };
-        const int gid = lane >> 2, tig = lane & 3;
         uint32_t tpar = 0;           // T5: completions of barT waited for
         int issued = 0, landed = 0;  // channel copies issued / waited for (subcarriers 0 .. issued - 1)
         if (n_mine > 0) issue_copy(issued++);
         bool ok = true;
         for (int j = 0; ok && j < n_mine + 2; ++j) {
             // Loads for phase A of j, issued before phase C and the fusion of j - 2 so that their
-            // latency is spent there: N0 (and scales), the downlink symbols, and the receive samples
-            // of the warp's first cluster for the first KP k-steps, in MMA fragment order (the rest
-            // are loaded as phase A starts; holding all of them through phase C costs registers).
-            constexpr int KP = KA / 2;
+            // latency is spent there: N0 (and scales) and the downlink symbols.  Phase A loads its
+            // receive samples itself, two k-steps ahead (they are in L2 since the channel copy of j
+            // was issued); holding them in registers through phase C would not fit the 128
+            // registers a thread has with two sweep groups.
             const bool do_a = j < n_mine;
             const int fa = do_a ? fof(j) : 0;
             float n0 = 0.f, hs = 1.f, ys = 1.f;
-            float2 yv[UL ? 2 * KA : 1];
-            const size_t ybase0 = (size_t)fa * n_sym * pl.B + (warp < C ? tab[warp].off : 0);
-            auto load_yv = [&](int k0, int k1) {
-#pragma unroll
-                for (int ks = 0; ks < KA; ++ks)
-#pragma unroll
-                    for (int jj = 0; jj < 2; ++jj) {
-                        const int n = 8 * jj + gid;
-                        if (ks >= k0 && ks < k1)
-                            yv[2 * ks + jj] = n < n_sym ? Elem<IN>::load(d.Y, ybase0 + (size_t)n * pl.B + 4 * ks + tig)
-                                                        : make_float2(0.f, 0.f);
-                    }
-            };
             float2 sv = make_float2(0.f, 0.f);
             float4 yq[8];  // T5: this thread's receive samples of every cluster (t5_phase_a)
             if constexpr (T5) {
@@ -381,8 +367,6 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                         for (int c = 0; c < 8; ++c)
                             if (c < C && r < n_sym && kc < BC / 2)
                                 yq[c] = __ldg(reinterpret_cast<const float4*>(Yf + ((size_t)r * pl.B + tab[c].off) * 2 + 4 * kc));
-                    } else if (warp < C) {
-                        load_yv(0, KP);
                     }
                 }
                 if (DL && tid < n_s) sv = __ldg(io.S + (size_t)fa * n_s + tid);
@@ -428,14 +412,12 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                         break;
                     }
                 }
-                if (!T5 && UL && warp < C) load_yv(KP, KA);
                 for (int c = warp; !T5 && c < C; c += kWsMmaWarps) {
                     const ClusterTile ct = tab[c];
                     float* Dm = Dmb(j) + c * UT;
                     tc_phase_a<BC, IN, UL, false>(pl, Hb(j) + ct.off * ew, SROW, d.Y, (size_t)fa * n_sym * pl.B + ct.off,
                                                   alpha, Gb(j) + (size_t)c * UT * (UT / 2), Dm, Dpb(j) + c * UT,
-                                                  Zb(j) + c * n_sym, xs, nullptr, nullptr,
-                                                  (UL && c == warp) ? yv : nullptr);
+                                                  Zb(j) + c * n_sym, xs, nullptr, nullptr);
                     if constexpr (UL) {
                         __syncwarp();
                         if (lane == 0) {  // fusion weight 1 / sum_u m_u (a skipped column counts as infinite)
@@ -462,14 +444,18 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         }
     } else {
         // ------------------------------------------------------------------ sweep role
-        // One lane per (cluster, symbol) tile: the uplink x (right-hand side z) and the downlink w
-        // (right-hand side s) side by side in the frame, reading the same rows of G_c.  Cluster
-        // sc = 32 / slot clusters per warp, each in its own quarter or half warp.
-        const int sw = warp - kWsMmaWarps, cpw = 32 / wl.slot;
+        // Two groups of four warps take alternate subcarriers (group g sweeps s = g, g + 2, ...; the
+        // double-buffered G_c, z / x, w and s of s are group g's), so the sweeps of consecutive
+        // subcarriers overlap and each sub-partition holds two sweep warps.  One lane per (cluster,
+        // symbol) tile: the uplink x (right-hand side z) and the downlink w (right-hand side s) side
+        // by side in the frame, reading the same rows of G_c.  Cluster sc = 32 / slot clusters per
+        // warp, each in its own quarter or half warp.
+        const int grp = (warp - kWsMmaWarps) / wl.sweep_warps, sw = (warp - kWsMmaWarps) % wl.sweep_warps;
+        const int cpw = 32 / wl.slot;
         const int sc = sw * cpw + lane / wl.slot, n_b = lane % wl.slot;
         const bool active = sc < C && n_b < n_sym;
         const int tile = sc * n_sym + n_b;
-        for (int s = 0; s < n_mine; ++s) {
+        for (int s = grp; s < n_mine; s += kWsSweepGroups) {
             if (!mbar_wait_bounded(&barA[s & 1], (uint32_t)(s >> 1) & 1u)) break;
             if (active) {
                 float4 x[UT / 2], w[UT / 2];

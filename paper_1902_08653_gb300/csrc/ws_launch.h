@@ -21,8 +21,8 @@ inline int build_ws_layout(const CdPlan& pl, int in_dtype, int op, WsLayout* wl,
     if (pl.learned || pl.phased) return CDMIMO_ERR_UNSUPPORTED;
     if (pl.n_sym > 16) return CDMIMO_ERR_UNSUPPORTED;
     const int slot = ws_slot(pl.n_sym), cpw = 32 / slot;           // sweep lanes per cluster, clusters per warp
-    const int warps = ((pl.C + cpw - 1) / cpw + 3) / 4 * 4;         // sweep warps, a multiple of four
-    if (warps * 32 + 32 * kWsMmaWarps > kWsMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
+    const int warps = ((pl.C + cpw - 1) / cpw + 3) / 4 * 4;         // warps of a sweep group: four
+    if (kWsSweepGroups * warps * 32 + 32 * kWsMmaWarps != kWsMaxThreads) return CDMIMO_ERR_UNSUPPORTED;
     const bool ul = op != CDMIMO_OP_PRECODE, dl = op != CDMIMO_OP_DETECT;
     const unsigned C = pl.C, U = pl.U, UT = kTcUT, n_sym = pl.n_sym, xs = tc_x_stride(pl.n_tiles);
     const unsigned srow = ws_row_words(pl.B, in_dtype);
@@ -67,7 +67,7 @@ int ws_launch(const CdPlan& pl, const WsLayout& wl, const FusedIO& io, cudaStrea
     auto k = cd_frame_ws_kernel<BC, MODE, IN, T5>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.smem_bytes) != cudaSuccess)
         return CDMIMO_ERR_CUDA;
-    const int threads = 32 * (kWsMmaWarps + wl.sweep_warps);
+    const int threads = 32 * (kWsMmaWarps + kWsSweepGroups * wl.sweep_warps);
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return CDMIMO_ERR_CUDA;
