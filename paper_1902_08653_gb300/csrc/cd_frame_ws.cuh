@@ -6,24 +6,25 @@
 // subcarriers overlapped inside one CTA per SM instead of run one after the other.
 //
 // Roles.  Eight "MMA" warps own the clusters (warp c takes clusters c, c + 8, ...): for its clusters
-// a warp forms G_c and z of subcarrier s + 1 (phase A), and x_c = H_c w of subcarrier s - 1
-// (phase C), while the "sweep" warps (one lane per (cluster, symbol) tile, 4 warps at C n_sym = 112)
-// run the K sweeps of subcarrier s.  The MMA warps also fuse the uplink estimates of s - 1 and stage
-// the downlink symbols of s + 1.  A subcarrier then costs the longer of the two roles' work, not
-// their sum, and the sweep warps (the FP32 pipes) and the MMA warps (the tensor pipes) issue on the
-// same SM sub-partitions at the same time.
+// a warp forms G_c and z of subcarrier s + 1 (phase A) and x_c = H_c w of subcarrier s - 1 (phase C),
+// and the MMA warps stage the downlink symbols.  Two groups of four "sweep" warps (one lane per
+// (cluster, symbol) tile, 4 warps at C n_sym = 112) take alternate subcarriers: a group runs the K
+// sweeps of its subcarrier and then fuses that subcarrier's uplink estimates, so the sweeps of two
+// consecutive subcarriers overlap.  A subcarrier then costs about the longest role's work, not the
+// sum, with the sweep warps (the FP32 pipes) and the MMA warps (the tensor pipes) issuing on the
+// same SM sub-partitions at the same time.  512 threads of 128 registers fill the register file.
 //
 // Pipeline, for the CTA's subcarriers s = 0, 1, ... (f = blockIdx.x + s gridDim.x, a static schedule;
 // calls with schedule counters run the phased kernel):
-//   MMA stage j:    [j >= 2] wait sweeps(j - 2); phase C and fusion of j - 2; copy the channel of j + 1
-//                   into the buffer j - 2 used;  [j < n] wait channel(j); phase A of j; signal A(j).
-//   sweep stage j:  wait A(j); sweeps of j; signal sweeps(j).
+//   MMA stage j:    [j >= 2] wait done(j - 2); phase C of j - 2; copy the channel of j + 1 into the
+//                   buffer j - 2 used;  [j < n] wait channel(j); phase A of j; signal A(j).
+//   sweep group g:  for s = g, g + 2, ...: wait A(s); sweeps of s; fusion of s; signal done(s).
 // Buffers: the channel rows of subcarrier s live from phase A(s) to phase C(s), two stages later, so
 // there are three (s mod 3); G_c, m_u, p_u^2, z / x, w, s and the fusion weights are double
-// buffered (s mod 2).  The hand-overs between roles are mbarriers (release / acquire), each with a
-// bounded wait; within the MMA warps a named barrier separates the fusion of j - 2 (which reads every
-// cluster's x) from phase A of j (which overwrites those rows with z), and its reduction makes a
-// timed-out wait leave the loop on all MMA warps together.
+// buffered (s mod 2, the buffers of sweep group s mod 2).  The hand-overs between roles are
+// mbarriers (release / acquire), each with a bounded wait; named barriers with reductions (1: the
+// MMA warps, 2 and 3: the sweep groups) order the steps within a role and make a timed-out wait leave
+// the loop on all of its warps together.
 #pragma once
 #include "cd_frame_tc.cuh"
 #include "umma.cuh"
@@ -72,6 +73,21 @@ __host__ __device__ constexpr int ws_slot(int n_sym) { return n_sym <= 8 ? 8 : 1
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier `id` over `n` threads, returning the AND of every participant's `ok`.
+__device__ __forceinline__ bool group_and(bool ok, uint32_t id, uint32_t n)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
 }
 
 // Named barrier 1 over the MMA warps, returning the AND of every participant's `ok`.
@@ -310,10 +326,10 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
     __syncthreads();
     if (T5) tc_fence_after();
     const uint32_t tbase = T5 ? *tslot : 0u;
+    float* osc = reinterpret_cast<float*>(barH + 8);  // [2] uplink output scale per z / x buffer
 
     if (warp < kWsMmaWarps) {
         // ------------------------------------------------------------------ MMA role
-        float* osc = reinterpret_cast<float*>(barH + 8);  // [2] uplink output scale per z / x buffer
         // Copies of subcarrier s's channel rows into buffer s mod 3: warp w copies users w, w + 8, ...
         // (whole rows of B entries); its lane 0 announces their bytes on the buffer's barrier (one
         // arrival per MMA warp).
@@ -380,7 +396,6 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                         tc_phase_c<BC, IN>(pl, Hb(s) + tab[c].off * ew, SROW, Wb(s) + c * n_sym, xs,
                                            io.Xdl + (size_t)f * n_sym * pl.B + tab[c].off);
                 }
-                if constexpr (UL) fuse_range(pl, d, f, Lb(s), Zb(s), xs, osc[s & 1], 0, kMmaThreads);
             }
             __syncwarp();
             if (j + 1 < n_mine) issue_copy(issued++);  // into the buffer that phase C of j - 2 released
@@ -455,8 +470,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
         const int sc = sw * cpw + lane / wl.slot, n_b = lane % wl.slot;
         const bool active = sc < C && n_b < n_sym;
         const int tile = sc * n_sym + n_b;
+        const uint32_t gbar = 2u + (uint32_t)grp, gthreads = 32u * (uint32_t)wl.sweep_warps;  // group barrier
         for (int s = grp; s < n_mine; s += kWsSweepGroups) {
-            if (!mbar_wait_bounded(&barA[s & 1], (uint32_t)(s >> 1) & 1u)) break;
+            if (!group_and(mbar_wait_bounded(&barA[s & 1], (uint32_t)(s >> 1) & 1u), gbar, gthreads)) break;
             if (active) {
                 float4 x[UT / 2], w[UT / 2];
                 const float4* Gc = Gb(s) + (size_t)sc * UT * (UT / 2);
@@ -475,6 +491,11 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) cd_frame_ws_kernel(const CdP
                         if constexpr (DL) Wb(s)[tile + u * xs] = slice_entry<UT, 1>(w, u);
                     }
                 }
+            }
+            if constexpr (UL) {  // the fusion of s (Sec. III), on this group once every tile's x is written
+                asm volatile("bar.sync %0, %1;" ::"r"(gbar), "r"(gthreads) : "memory");
+                fuse_range(pl, d, fof(s), Lb(s), Zb(s), xs, osc[s & 1], kMmaThreads + grp * (int)gthreads,
+                           (int)gthreads);
             }
             mbar_arrive(&barS[s & 1]);
         }
