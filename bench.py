@@ -82,7 +82,7 @@ FRAME_BYTES_PER_VEC = U * B * 8 / N_SYM + B * 8 + U * 8 + U * 8 + B * 8
 NCU_TRAFFIC = {"cd_detect_gram_kernel": 73.806592e6 + 0.621568e6,
                "cd_precode_gram_kernel": 41.539072e6 + 0.377088e6,
                "cd_frame_gram_kernel": 76.144896e6 + 4.834560e6,
-               "cd_frame_ws_kernel": 75.993344e6 + 4.826112e6}
+               "cd_frame_ws_kernel": 75.990016e6 + 5.112064e6}
 
 WORKLOAD = ("TDD frame: UL CD detect + fusion and DL CD ZF precode + normalization on the same channel; "
             "B=256 (C=8 x 32), U=16, K=3, 1200 subcarriers x 14 OFDM symbols, i.i.d. CN(0,1), 16-QAM, "
@@ -529,7 +529,7 @@ def precision_variants(up, dl, dev, stream, steps, e2e_chunks):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / n_e2e
-        out[kind] = {"kernel": "cd_frame_tc_kernel", "ms": ms, "vectors_per_s": N_SC * N_SYM / (ms * 1e-3),
+        out[kind] = {"kernel": FRAME_KERNELS["gram_tc"], "ms": ms, "vectors_per_s": N_SC * N_SYM / (ms * 1e-3),
                      "mse_vs_mmse_mean": float(np.mean(list(mse.values()))),
                      "e2e": {"vectors_per_s": N_SC * N_SYM / (e2e_ms * 1e-3), "ms_per_step": e2e_ms,
                              "h2d_bytes_per_step": int(Hh.numel() * 2 + Yh.numel() * 2 + N0h.numel() * 4 +
