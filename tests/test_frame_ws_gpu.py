@@ -73,6 +73,7 @@ CASES = {
     "Bc16_C6_bf16_odd": (99, 5, [16] * 6, 13, 2, "colnorm", "bf16"),
     "Bc32_C3_U11_n_sym7": (240, 7, [32] * 3, 11, 3, "colnorm", "c64"),
     "Bc16_C1_U10": (153, 14, [16], 10, 2, "colnorm", "c64"),
+    "Bc16_C16_n_sym8": (311, 8, [16] * 16, 12, 3, "colnorm", "c64"),  # four clusters per sweep warp
 }
 
 
