@@ -407,14 +407,13 @@ size_t cdmimo_learned_workspace_size(const cdmimo_params* p, int hidden);
  *   - Limit: n_sc * (cdmimo_learned_param_count(p->K, p->U, hidden) + 1, rounded up to a multiple
  *     of 4) * 4 bytes must not exceed CDMIMO_NOALLOC_SCRATCH_BYTES; larger batches return
  *     CDMIMO_ERR_WORKSPACE (use cdmimo_learned_grad with a workspace, or split the batch).
- *   - The first call on a device looks up the array's device address with that device current;
- *     make that first call before any stream capture.
+ *   - Every call looks up the array's device address for the current device and context (so the
+ *     entry point stays usable after cudaDeviceReset()); the first call on a device also loads the
+ *     module there: make that first call before any stream capture.
  *   - All calls share the one array and it keeps the last call's contents (nothing in it has to
  *     start at zero).  Calls that overlap on the GPU (other streams, other host threads) race on
  *     it: serialize them.
  *   - It allocates nothing and frees nothing.
- *   - The looked-up address is kept per device for the life of the process: do not use this entry
- *     point on a device after cudaDeviceReset() has been called on it.
  *   - A block that does not match (p->K, p->U, hidden) is flagged as in cdmimo_learned_grad.
  */
 #define CDMIMO_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)

@@ -632,23 +632,18 @@ int launch_grad_t(const CdPlan& pl, const GradLayout& gl, const GradIO& io, cuda
 
 // Scratch of cdmimo_learned_grad_noalloc: a fixed device array owned by the library, for callers
 // that cannot allocate device memory.  Host code only ever sees its address through
-// cudaGetSymbolAddress (the symbol itself is a host-side stand-in); the address is looked up once
-// per device, with that device current, on the first call made on it.
+// cudaGetSymbolAddress (the symbol itself is a host-side stand-in); the address is looked up on every
+// call, for the current device and context, so it stays valid across a device or context reset
+// (which reloads the module) and needs no shared cache between host threads.
 static __device__ __align__(256) float g_noalloc_scratch[CDMIMO_NOALLOC_SCRATCH_BYTES / sizeof(float)];
 
 namespace {
 
 float* noalloc_scratch_address()
 {
-    static float* addr[kMaxDevices] = {nullptr};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    if (!addr[dev]) {
-        void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return nullptr;
-        addr[dev] = static_cast<float*>(ptr);
-    }
-    return addr[dev];
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    return static_cast<float*>(ptr);
 }
 
 }  // namespace
