@@ -65,15 +65,17 @@ __device__ __forceinline__ void corr2(const float4* hr, const float4 (&v0)[kPair
 
 // Data fusion (Sec. III) of one subcarrier on the CTA's threads [t0, t0 + nt): lam holds
 // w_c = 1 / sum_u m_{u,c}; lambda_c = w_c / sum w (COLNORM) or 1 / C (EQUAL, or no positive weight).
+// final_lam: lam already holds lambda_c (the learned fusion's softmax), used as it is.
 __device__ __forceinline__ void fuse_range(const CdPlan& pl, const DetectIO& io, int f, const float* lam,
-                                           const float2* Xs, uint32_t xs_stride, float out_scale, int t0, int nt)
+                                           const float2* Xs, uint32_t xs_stride, float out_scale, int t0, int nt,
+                                           bool final_lam = false)
 {
     const int r = (int)threadIdx.x - t0, C = pl.C, U = pl.U, n_sym = pl.n_sym;
     if (r < 0 || r >= nt) return;
     float tot = 0.f;
-    for (int c = 0; c < C; ++c) tot += lam[c];
-    const bool equal = pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f);
-    const float inv = equal ? 1.f / (float)C : 1.f / tot;
+    for (int c = 0; c < C && !final_lam; ++c) tot += lam[c];
+    const bool equal = !final_lam && (pl.fuse == CDMIMO_FUSE_EQUAL || !(tot > 0.f));
+    const float inv = final_lam ? 1.f : equal ? 1.f / (float)C : 1.f / tot;
     for (int i = r; i < n_sym * U; i += nt) {  // symbols fastest: a warp's loads of x hit distinct banks
         const int u = i / n_sym, n = i - u * n_sym;
         float2 acc = make_float2(0.f, 0.f);

@@ -705,7 +705,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) cd_frame_tc_kernel(const CdPlan
                     tc_learned_lambda<UT>(pl, blk, learned_ok, alpha, tab, Dp, mlp, lam, 0, kTcThreads / 32);
                     __syncthreads();
                 }
-                fuse_subcarrier<true>(pl, d, f, lam, Zs, xs, out_scale);
+                // (symbols fastest, as for the plain rules: this kernel takes no per-cluster outputs)
+                fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads, true);
             } else {
                 fuse_range(pl, d, f, lam, Zs, xs, out_scale, 0, kTcThreads);
             }
