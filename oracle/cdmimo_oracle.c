@@ -29,6 +29,14 @@
  *   - per-cluster power: rho_c = rho / sqrt(C) (Sec. IV-B, rho_c^2 = rho^2 / C), also for uneven B_c.
  *   - the garbled transposes of Alg. 2 are read as Eq. (4): x <- x - (hbar_u^H x - sbar_u) hbar_u,
  *     and sbar carries the cluster index: sbar_{u,c} = p_{u,c} s_u.
+ *
+ * Pins (the CPU tests check these functions against what the paper and the mathematics fix, not
+ * against themselves): the sweeps against Gauss-Seidel / dual Gauss-Seidel splittings and their
+ * limits (local L-MMSE and local ZF by Cholesky), closed forms (one user, orthogonal columns, K = 0,
+ * one cluster), exhaustive ML on tiny QPSK cases; the learned sweeps and fusion against hand-computed
+ * values.  Parity unpinned: the COLNORM fusion weights' agreement with the paper's sigma_c^2, which
+ * the paper does not state (only the reading above and its invariants are pinned: weights summing
+ * to one, equal weights for identical clusters, the closed form for a scaled cluster).
  */
 #include <complex.h>
 #include <math.h>
